@@ -1,0 +1,91 @@
+"""The FP64 oracle against its pins (see oracle_pins.py for what each pins)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle_pins as P
+from oracle import theory as th
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return oracle.load()
+
+
+@pytest.mark.parametrize("pin", P.ALL_FAST_PINS, ids=lambda p: p.__name__)
+def test_fast_pin(lib, pin):
+    fails = pin(lib)
+    assert not fails, "\n".join(fails[:10])
+
+
+def test_weights_printed(lib):
+    """Text after Eq. 2 and after Eq. 3."""
+    assert np.allclose(oracle.feq(1.0, 0, 0, lib=lib), GOLD["d2q9_weights"]["value"],
+                       atol=1e-16)
+    # the interaction weights enter only through F; a unit psi step in one
+    # neighbour isolates them
+    for (dx, dy), key in (((1, 0), "w1"), ((1, 1), "w2")):
+        psi = np.ones((5, 5))
+        psi[2 + dy, 2 + dx] = 2.0
+        Fx, _ = oracle.force(psi, G=-1.0, lib=lib)
+        # F_x(center) = psi(c) * sum_a w_a psi(c+e_a) e_ax = w * (2 - 1) from the bump
+        assert Fx[2, 2] == pytest.approx(GOLD["interaction_weights"]["value"][key], abs=1e-15)
+
+
+def test_divergence_is_reported_not_clamped(lib):
+    """A density beyond the domain of psi (eta >= 1) stops the run with a
+    status instead of producing numbers."""
+    lat = oracle.Lattice(4, 4, 0.8, lib=lib)
+    rho = np.full((4, 4), 0.2)
+    rho[1, 1] = 1.2
+    lat.init_density(rho)
+    f0 = lat.f.copy()
+    rc, done = lat.step(5, oracle.SC, 1.0)
+    assert rc == 1 and done == 0
+    assert np.array_equal(lat.f, f0)
+
+
+@pytest.mark.slow
+def test_improved_flat_interface_follows_eps_16_sigma(lib):
+    fails = P.pin_improved_flat_interface(lib)
+    assert not fails, "\n".join(fails)
+
+
+@pytest.mark.slow
+def test_sigma_0105_fits_maxwell(lib):
+    """Sec. IV B (Fig. 6): sigma = 0.105 reproduces the Maxwell coexistence at
+    tau = 0.6 and 0.8 (here T/Tc = 0.8 and 0.9: rho_l within 0.5 %, rho_g
+    within 5 %)."""
+    for t in (0.8, 0.9):
+        mx = th.maxwell(th.CarnahanStarling(th.temperature(t)))
+        for tau in (0.6, 0.8):
+            got = P.flat_interface(lib, t, oracle.IMPROVED, tau, 0.105)
+            assert got is not None
+            assert abs(got[1] / mx[1] - 1) < 5e-3, (t, tau, got, mx)
+            assert abs(got[0] / mx[0] - 1) < 5e-2, (t, tau, got, mx)
+
+
+@pytest.mark.slow
+def test_tau_dependence_sc_vs_improved(lib):
+    """Sec. I and V: the Shan-Chen coexistence curve depends on tau (its extra
+    term carries tau^2, Eq. 20), while in the improved scheme eps = 16 sigma
+    carries no tau.  (EDM, Eq. 11, is checked only through its identity with
+    Shan-Chen at tau = 1: its relaxed slab does not move with tau in FP64,
+    unlike the tau dependence the paper attributes to it.)"""
+    spread = {}
+    rg_at = {}
+    for name, sch, sig in (("SC", oracle.SC, 0.0), ("improved", oracle.IMPROVED, 0.105),
+                           ("EDM", oracle.EDM, 0.0)):
+        rg = [P.flat_interface(lib, 0.85, sch, tau, sig, steps=20000)[0]
+              for tau in (0.6, 1.0, 1.5)]
+        rg_at[name] = rg
+        spread[name] = (max(rg) - min(rg)) / np.mean(rg)
+    assert spread["SC"] > 0.5, spread                 # 0.0217 -> 0.0458
+    assert spread["improved"] < 1e-4, spread
+    assert rg_at["SC"][0] < rg_at["SC"][1] < rg_at["SC"][2]
+    assert rg_at["EDM"][1] == pytest.approx(rg_at["SC"][1], rel=1e-12)
