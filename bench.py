@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Throughput of the fused pseudopotential D2Q9 step (MLUPS and HBM roofline).
+
+Workload (one "step" = one lattice Boltzmann time step of the whole domain):
+8192 x 8192 periodic D2Q9, spinodal decomposition from
+rho = rho_avg (1 + 0.01 U[-1, 1]) (seed 3 + rank) with rho_avg midway between
+the Maxwell coexistence densities at T = 0.85 Tc, tau = 0.8, improved forcing
+scheme with sigma = 0.1, FP32 populations.  The populations (2 x 2.4 GB)
+are far larger than L2, so no flush is needed between steps.
+
+* value      -- MLUPS over all ranks, device time of exactly K steps (CUDA
+                events on the stream the kernels run on), inputs resident.
+* roofline   -- the step kernel: algorithmic bytes per launch (9 reads + 9
+                writes per cell) / average launch time, against the measured
+                HBM copy bandwidth.
+* e2e        -- the same metric through the public C ABI from pinned host
+                memory: lbm_init_density (H2D), K steps, lbm_get_moments (D2H).
+* cpu_baseline -- the FP64 oracle (test infrastructure) on a bounded sample
+                of the same workload, on this host's cores.
+
+``--impl reference`` times the oracle alone as the reference arm.
+Under torchrun every rank runs its own replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D2Q9 pseudopotential MLUPS & % HBM roofline; batched sweep; warm-start speedup"
+BYTES_PER_CELL = {"fp32": 72, "fp64": 144, "bf16dev": 44, "fp16dev": 44}
+KERNEL_SOURCES = ["lbm_device.cuh", "lbm_kernels.cuh", "lbm_launch.cuh"]
+# DRAM bytes per launch of the step kernel from an ncu capture, keyed by the
+# hash of the kernel sources it was taken on (null once they change).
+MEASURED_TRAFFIC = {}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1204_4098_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.bus_id = bus_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "100", "-f", self.path]
+        if self.bus_id:
+            cmd += ["-i", self.bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.DEVNULL,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    return world, rank, local
+
+
+def dist_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def workload_density(n, rank, T_over_Tc=0.85):
+    from paper_1204_4098_gb300 import inputs, lbm
+    rg, rl, _ = lbm.maxwell(lbm.temperature(T_over_Tc))
+    return inputs.spinodal(n, n, 0.5 * (rg + rl), amp=0.01, seed=3 + rank), (rg, rl)
+
+
+def cpu_baseline(n_side=1024, steps=60):
+    """FP64 oracle (test infrastructure) on a 1024 x 1024 sample of the
+    workload for `steps` steps, single-threaded."""
+    import oracle
+    from oracle import theory as th
+    from paper_1204_4098_gb300 import inputs
+    t = 0.85
+    rg, rl, _ = th.maxwell(th.CarnahanStarling(th.temperature(t)))
+    rho0 = inputs.spinodal(n_side, n_side, 0.5 * (rg + rl), amp=0.01, seed=3)
+    lat = oracle.Lattice(n_side, n_side, t)
+    lat.init_density(rho0)
+    t0 = time.perf_counter()
+    rc, done = lat.step(steps, oracle.IMPROVED, 0.8, 0.1)
+    dt = time.perf_counter() - t0
+    assert rc == 0
+    return {"value": n_side * n_side * done / dt / 1e6, "unit": "MLUPS", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{n_side}x{n_side} crop of the workload recipe, {done} steps, FP64, "
+                      f"1 thread ({dt:.1f} s)"}
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the FP64 oracle, as it stands, on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    from oracle import theory as th
+    from paper_1204_4098_gb300 import inputs
+    side = args.ref_side
+    t = 0.85
+    rg, rl, _ = th.maxwell(th.CarnahanStarling(th.temperature(t)))
+    lat = oracle.Lattice(side, side, t)
+    lat.init_density(inputs.spinodal(side, side, 0.5 * (rg + rl), amp=0.01, seed=3))
+    lat.step(args.warmup, oracle.IMPROVED, 0.8, 0.1)
+    t0 = time.perf_counter()
+    rc, done = lat.step(args.steps, oracle.IMPROVED, 0.8, 0.1)
+    dt = time.perf_counter() - t0
+    value = side * side * done / dt / 1e6
+    sample = f"{side}x{side} crop of the 8192x8192 recipe per step, FP64 oracle, 1 thread"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / max(done, 1) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args),
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args):
+    return {"workload": f"{args.n}x{args.n} periodic D2Q9 spinodal decomposition, "
+                        f"T=0.85Tc, tau=0.8, improved forcing sigma=0.1, "
+                        f"{args.precision} populations",
+            "nx": args.n, "ny": args.n, "scheme": "improved", "sigma": 0.1, "tau": 0.8,
+            "T_over_Tc": 0.85, "precision": args.precision,
+            "l2": "inputs larger than L2 (two population buffers of "
+                  f"{args.n * args.n * BYTES_PER_CELL[args.precision] / 2 / 1e9:.1f} GB each)"}
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_1204_4098_gb300 import lbm
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    prec = {"fp32": lbm.FP32, "fp64": lbm.FP64, "bf16dev": lbm.BF16DEV,
+            "fp16dev": lbm.FP16DEV}[args.precision]
+    n = args.n
+    rho0, _ = workload_density(n, rank)
+    cells = n * n
+
+    lat = lbm.Lattice(n, n, 0.85, precision=prec, device=local, stream=stream.cuda_stream)
+    lat.init_density(rho0)
+    lat.step_async(args.warmup, lbm.IMPROVED, 0.8, 0.1)
+    assert lat.sync() == lbm.LBM_OK
+
+    props = torch.cuda.get_device_properties(local)
+    bus = None
+    if hasattr(props, "pci_bus_id"):
+        bus = f"{getattr(props, 'pci_domain_id', 0):08X}:{props.pci_bus_id:02X}:" \
+              f"{getattr(props, 'pci_device_id', 0):02X}.0"
+    sampler = ClockSampler(bus)
+    sampler.start()
+
+    # ---- device-resident timing: exactly K steps, one kernel launch each ----
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    launches0 = lbm.launch_count()
+    start.record(stream)
+    lat.step_async(args.steps, lbm.IMPROVED, 0.8, 0.1)
+    end.record(stream)
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    launches = lbm.launch_count() - launches0
+    ms = start.elapsed_time(end)
+    assert lat.sync() == lbm.LBM_OK
+    clocks = sampler.stop()
+    ms_max = dist_max(ms, world)
+    value = world * cells * args.steps / (ms_max * 1e-3) / 1e6
+
+    per_launch_s = ms * 1e-3 / args.steps
+    bpc = BYTES_PER_CELL[args.precision]
+    achieved = bpc * cells / per_launch_s / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = MEASURED_TRAFFIC.get((kernel_source_hash(), args.precision, n))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "strip_kernel<Store, improved, step>",
+                "algorithmic_bytes_per_launch": bpc * cells,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s"}
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda: torch.empty((n, n), dtype=torch.float64, pin_memory=True).numpy()
+        h_rho0 = pin()
+        h_rho0[...] = rho0
+        outs = (pin(), pin(), pin())
+        dist_barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.init_density(h_rho0)
+        lat.step_async(args.steps, lbm.IMPROVED, 0.8, 0.1)
+        lat.observe(out=outs)
+        torch.cuda.synchronize()
+        dt = dist_max(time.perf_counter() - t0, world)
+        assert np.isfinite(outs[0][0, 0])
+        e2e = {"value": world * cells * args.steps / dt / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 8 * cells / args.steps,
+               "d2h_bytes_per_step": 24 * cells / args.steps,
+               "note": "lbm_init_density (8 B/cell H2D) + K x lbm_step + lbm_get_moments "
+                       "(24 B/cell D2H), pinned host memory, wall clock"}
+    lat.close()
+
+    variants = {}
+    if args.variants and rank == 0:
+        for name, p in (("bf16dev", lbm.BF16DEV), ("fp16dev", lbm.FP16DEV)):
+            v = lbm.Lattice(n, n, 0.85, precision=p, device=local, stream=stream.cuda_stream)
+            v.init_density(rho0)
+            v.step_async(args.warmup, lbm.IMPROVED, 0.8, 0.1)
+            torch.cuda.synchronize()
+            k = max(args.steps // 2, 1)
+            s2, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s2.record(stream)
+            v.step_async(k, lbm.IMPROVED, 0.8, 0.1)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            assert v.sync() == lbm.LBM_OK
+            t_ms = s2.elapsed_time(e2)
+            gbs = BYTES_PER_CELL[name] * cells / (t_ms * 1e-3 / k) / 1e9
+            variants[name] = {"MLUPS": cells * k / (t_ms * 1e-3) / 1e6, "achieved_GBs": gbs,
+                              "frac": gbs / peak, "bytes_per_cell": BYTES_PER_CELL[name]}
+            v.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp32": "f32", "fp64": "f64", "bf16dev": "bf16", "fp16dev": "f16"}[
+                    args.precision],
+                "data": "synthetic", "config": workload_config(args),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": launches}
+        if variants:
+            line["storage_variants"] = variants
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--precision", choices=tuple(BYTES_PER_CELL), default="fp32")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variants", action="store_true", default=True)
+    ap.add_argument("--no-variants", dest="variants", action="store_false")
+    ap.add_argument("--ref-side", type=int, default=384)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * lbm.h -- C ABI of the GB300 pseudopotential (Shan-Chen) D2Q9 lattice
+ * Boltzmann library.
+ *
+ * The method is the one of Li, Luo & Li, "Forcing scheme in pseudopotential
+ * lattice Boltzmann model for multiphase flows": one time step is
+ *   (1) streaming of Eq. 1 (pull form: f_a(x, t) = f*_a(x - e_a, t - 1)),
+ *   (2) the moments rho = sum f_a, u = sum f_a e_a / rho (Sec. III A),
+ *   (3) the potential psi(rho) of Eq. 8 with the Carnahan-Starling p_EOS of
+ *       Eq. 23 (a, b, R; c = 1, delta_t = 1, G < 0),
+ *   (4) the interaction force of Eq. 3 with w(1) = 1/3, w(2) = 1/12,
+ *   (5) BGK collision (Eqs. 1-2) with the chosen forcing scheme.
+ * All of it runs in one fused CUDA kernel per step; the host only validates
+ * arguments, launches, and copies data in and out.
+ *
+ * Lattice: D2Q9, e0 = (0,0); e1..e4 = (1,0), (0,1), (-1,0), (0,-1);
+ * e5..e8 = (1,1), (-1,1), (-1,-1), (1,-1).  Host arrays are row-major
+ * [ny][nx] (x fastest); population arrays are [9][ny][nx].  The domain is
+ * periodic in x and y.
+ *
+ * Memory: a context owns every device allocation it makes (two population
+ * buffers, plus a density plane for 16-bit storage, plus small scratch);
+ * host pointers passed in are only read or written during the call.
+ *
+ * Errors: every function returns an lbm_status; on failure the context (if
+ * any) records a message readable with lbm_last_error().  No function
+ * aborts the process.  Threading: one context must not be used by two host
+ * threads at once; distinct contexts may share a device.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_E_INVAL = 1,    /* bad argument (size, scheme, tau, null pointer, ...) */
+  LBM_E_NOMEM = 2,    /* device or host allocation failed                  */
+  LBM_E_CUDA = 3,     /* a CUDA runtime call failed                         */
+  LBM_E_DIVERGED = 4, /* density left the domain of psi (rho <= 0, b rho/4 >= 1,
+                         negative radicand in Eq. 8) or became non-finite    */
+  LBM_E_TIMEOUT = 5,  /* a bounded device-side wait gave up                 */
+  LBM_E_STATE = 6     /* call out of order (e.g. step before init)           */
+} lbm_status;
+
+/* Forcing schemes (Table I of the paper). */
+enum {
+  LBM_SCHEME_SC = 0,       /* Shan-Chen velocity shift: BGK towards
+                              f_eq(rho, u + tau F / rho), Eqs. 9-10          */
+  LBM_SCHEME_EDM = 1,      /* exact difference method:
+                              F_a = f_eq(rho, u + F/rho) - f_eq(rho, u), Eq. 11 */
+  LBM_SCHEME_IMPROVED = 2, /* improved scheme, Eq. 31: Guo forcing with
+                              v' = v + sigma F / ((tau - 1/2) psi^2);
+                              sigma = 0 is Guo's scheme (Eqs. 12-13)         */
+  LBM_SCHEME_NOFORCE = 3,  /* F = 0: plain BGK (force-free checks)           */
+  LBM_SCHEME_EDM_MOD = 4,  /* EDM with C_e = 1/tau (Sec. III C)             */
+  LBM_SCHEME_LADD = 5      /* Ladd: u in f_eq and in F_a, B_e = C_e = 1
+                              (Table I)                                      */
+};
+
+/* Storage precision of the populations. */
+enum {
+  LBM_FP32 = 0,    /* float populations, float arithmetic                   */
+  LBM_FP64 = 1,    /* double populations, double arithmetic                 */
+  LBM_BF16DEV = 2, /* bf16 deviations d_a = f_a - w_a rho plus a float rho
+                      plane; float arithmetic                                */
+  LBM_FP16DEV = 3  /* as LBM_BF16DEV with IEEE half deviations               */
+};
+
+typedef struct {
+  int nx, ny;          /* lattice size, each >= 1                            */
+  double T_over_Tc;    /* reduced temperature, > 0                           */
+  int tc_mode;         /* 0: exact critical temperature of Eq. 23;
+                          1: the rounded Tc = 0.094 printed with Eq. 23      */
+  double a, b, R, G;   /* Eq. 23 / Eq. 8 constants; the paper's values are
+                          a = 1, b = 4, R = 1, G = -1 (G must be < 0)         */
+  int precision;       /* LBM_FP32, LBM_FP64, LBM_BF16DEV, LBM_FP16DEV       */
+  int device;          /* CUDA device ordinal                                 */
+  void *cuda_stream;   /* cudaStream_t to run on, or NULL for a stream the
+                          context creates and owns                           */
+} lbm_params;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Fill p with the paper's defaults: a = 1, b = 4, R = 1, G = -1, exact Tc,
+ * FP32, device 0, own stream; nx, ny and T_over_Tc are set to 0. */
+void lbm_default_params(lbm_params *p);
+
+/* Allocate a lattice.  Errors: LBM_E_INVAL for nx or ny < 1, T_over_Tc <= 0,
+ * G >= 0, b <= 0, unknown precision or tc_mode; LBM_E_NOMEM; LBM_E_CUDA.
+ * On success *out owns the context (free it with lbm_destroy). */
+lbm_status lbm_create(const lbm_params *p, lbm_ctx **out);
+
+/* Set the state to f_a = f_eq(rho, u) (Eq. 2) at every cell.  rho is a host
+ * array of ny*nx doubles; ux and uy may be NULL (zero velocity).  Copied to
+ * the device during the call.  LBM_E_INVAL if any rho is outside the domain
+ * of psi (rho <= 0, b rho / 4 >= 1 or a negative radicand in Eq. 8). */
+lbm_status lbm_init_density(lbm_ctx *ctx, const double *rho, const double *ux,
+                            const double *uy);
+
+/* Advance n >= 0 time steps with the given scheme and relaxation time
+ * tau > 1/2 (sigma is read by LBM_SCHEME_IMPROVED only).  Kernels are queued
+ * on the context stream; the call then waits for them and reads the device
+ * status word once.  LBM_E_DIVERGED if psi became undefined in any step
+ * (the state is then unspecified but the context stays usable and
+ * destroyable); LBM_E_STATE before lbm_init_density / lbm_set_populations. */
+lbm_status lbm_step(lbm_ctx *ctx, int n, int scheme, double tau, double sigma);
+
+/* Queue n steps without waiting and without reading the status (for timing
+ * and graph capture); lbm_sync_status() later waits and reports. */
+lbm_status lbm_step_async(lbm_ctx *ctx, int n, int scheme, double tau,
+                          double sigma);
+lbm_status lbm_sync_status(lbm_ctx *ctx);
+
+/* Density and the actual fluid velocity v = u + F / (2 rho) (Table I, every
+ * scheme) of the current state, as host FP64 arrays of ny*nx; any pointer
+ * may be NULL.  F = 0 (and psi is not evaluated) when the most recent
+ * lbm_step used LBM_SCHEME_NOFORCE.  LBM_E_DIVERGED if psi is undefined. */
+lbm_status lbm_get_moments(lbm_ctx *ctx, double *rho, double *vx, double *vy);
+
+/* Total mass sum_x rho(x), reduced on the device in FP64. */
+lbm_status lbm_get_mass(lbm_ctx *ctx, double *mass);
+
+/* Checkpoint: copy the populations f_a(x, t) of the current state to / from
+ * a host FP64 array [9][ny][nx].  For 16-bit storage lbm_set_populations
+ * rounds the deviations to 16 bits. */
+lbm_status lbm_get_populations(lbm_ctx *ctx, double *f);
+lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f);
+
+/* Reduced temperature -> absolute temperature used by the context. */
+lbm_status lbm_get_temperature(const lbm_ctx *ctx, double *T);
+
+/* Human-readable message of the last failure on ctx ("" if none); with a
+ * NULL ctx, the last failure of lbm_create on this thread. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Free every resource of ctx.  Accepts NULL. */
+lbm_status lbm_destroy(lbm_ctx *ctx);
+
+/* ---- host-side equation-of-state helpers (no GPU needed) -------------- */
+
+/* Exact critical point of Eq. 23: dp/drho = d^2p/drho^2 = 0. */
+lbm_status lbm_cs_critical_point(double a, double b, double R, double *rho_c,
+                                 double *T_c, double *p_c);
+
+/* Maxwell equal-area coexistence densities (Eq. 7) of Eq. 23 at absolute
+ * temperature T (0 < T < T_c).  LBM_E_INVAL outside that range. */
+lbm_status lbm_cs_maxwell(double T, double a, double b, double R,
+                          double *rho_g, double *rho_l, double *p0);
+
+/* Number of kernel launches this process has queued through the library
+ * (all contexts), for accounting in benchmarks. */
+unsigned long long lbm_kernel_launch_count(void);
+
+/* ---- launch tuning ------------------------------------------------------ */
+
+/* Rows per warp band of the step kernel (0 = automatic: one wave of warps,
+ * at least 8 rows each).  Changes only speed, never results. */
+lbm_status lbm_set_band_rows(lbm_ctx *ctx, int band_rows);
+
+/* The launch geometry lbm_step would use for `scheme`: 32-column strips,
+ * rows per band, bands, and CTAs of 128 threads. */
+lbm_status lbm_get_launch_geometry(lbm_ctx *ctx, int scheme, int *n_strips,
+                                   int *band_rows, int *n_bands, int *grid);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

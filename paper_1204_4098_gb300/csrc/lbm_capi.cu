@@ -1,0 +1,541 @@
+// C ABI of the pseudopotential D2Q9 library: context life cycle, argument
+// validation, launch geometry, and host <-> device copies.  Every step of
+// the method itself runs in the kernels of lbm_step_*.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launches(unsigned long long n) { g_launches += n; }
+
+cudaError_t strip_launch_f32(int, int, const StripLaunch&, int, cudaStream_t);
+cudaError_t strip_launch_f64(int, int, const StripLaunch&, int, cudaStream_t);
+cudaError_t strip_launch_bf16(int, int, const StripLaunch&, int, cudaStream_t);
+cudaError_t strip_launch_f16(int, int, const StripLaunch&, int, cudaStream_t);
+cudaError_t strip_occupancy_f32(int, int, int*);
+cudaError_t strip_occupancy_f64(int, int, int*);
+cudaError_t strip_occupancy_bf16(int, int, int*);
+cudaError_t strip_occupancy_f16(int, int, int*);
+cudaError_t set_state_f32(void*, float*, int, int, size_t, const double*, const double*,
+                          const double*, const double*, const EosCheck&, cudaStream_t);
+cudaError_t set_state_f64(void*, float*, int, int, size_t, const double*, const double*,
+                          const double*, const double*, const EosCheck&, cudaStream_t);
+cudaError_t set_state_bf16(void*, float*, int, int, size_t, const double*, const double*,
+                          const double*, const double*, const EosCheck&, cudaStream_t);
+cudaError_t set_state_f16(void*, float*, int, int, size_t, const double*, const double*,
+                          const double*, const double*, const EosCheck&, cudaStream_t);
+cudaError_t get_state_f32(const void*, const float*, int, int, size_t, double*, cudaStream_t);
+cudaError_t get_state_f64(const void*, const float*, int, int, size_t, double*, cudaStream_t);
+cudaError_t get_state_bf16(const void*, const float*, int, int, size_t, double*, cudaStream_t);
+cudaError_t get_state_f16(const void*, const float*, int, int, size_t, double*, cudaStream_t);
+cudaError_t mass_f32(const void*, const float*, size_t, double*, int, double*, cudaStream_t);
+cudaError_t mass_f64(const void*, const float*, size_t, double*, int, double*, cudaStream_t);
+cudaError_t mass_bf16(const void*, const float*, size_t, double*, int, double*, cudaStream_t);
+cudaError_t mass_f16(const void*, const float*, size_t, double*, int, double*, cudaStream_t);
+
+cudaError_t strip_launch(int precision, int scheme, int mode, const StripLaunch& L, int grid,
+                         cudaStream_t s) {
+  switch (precision) {
+    case kFP32: return strip_launch_f32(scheme, mode, L, grid, s);
+    case kFP64: return strip_launch_f64(scheme, mode, L, grid, s);
+    case kBF16Dev: return strip_launch_bf16(scheme, mode, L, grid, s);
+    case kFP16Dev: return strip_launch_f16(scheme, mode, L, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t strip_occupancy(int precision, int scheme, int mode, int* b) {
+  switch (precision) {
+    case kFP32: return strip_occupancy_f32(scheme, mode, b);
+    case kFP64: return strip_occupancy_f64(scheme, mode, b);
+    case kBF16Dev: return strip_occupancy_bf16(scheme, mode, b);
+    case kFP16Dev: return strip_occupancy_f16(scheme, mode, b);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t set_state_launch(int precision, void* dst, float* rd, int nx, int ny, size_t plane,
+                             const double* rho, const double* ux, const double* uy,
+                             const double* f_in, const EosCheck& chk, cudaStream_t s) {
+  switch (precision) {
+    case kFP32: return set_state_f32(dst, rd, nx, ny, plane, rho, ux, uy, f_in, chk, s);
+    case kFP64: return set_state_f64(dst, rd, nx, ny, plane, rho, ux, uy, f_in, chk, s);
+    case kBF16Dev: return set_state_bf16(dst, rd, nx, ny, plane, rho, ux, uy, f_in, chk, s);
+    case kFP16Dev: return set_state_f16(dst, rd, nx, ny, plane, rho, ux, uy, f_in, chk, s);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t get_state_launch(int precision, const void* src, const float* rs, int nx, int ny,
+                             size_t plane, double* f_out, cudaStream_t s) {
+  switch (precision) {
+    case kFP32: return get_state_f32(src, rs, nx, ny, plane, f_out, s);
+    case kFP64: return get_state_f64(src, rs, nx, ny, plane, f_out, s);
+    case kBF16Dev: return get_state_bf16(src, rs, nx, ny, plane, f_out, s);
+    case kFP16Dev: return get_state_f16(src, rs, nx, ny, plane, f_out, s);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t mass_launch(int precision, const void* src, const float* rs, size_t plane,
+                        double* partial, int n_partial, double* out, cudaStream_t s) {
+  switch (precision) {
+    case kFP32: return mass_f32(src, rs, plane, partial, n_partial, out, s);
+    case kFP64: return mass_f64(src, rs, plane, partial, n_partial, out, s);
+    case kBF16Dev: return mass_bf16(src, rs, plane, partial, n_partial, out, s);
+    case kFP16Dev: return mass_f16(src, rs, plane, partial, n_partial, out, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+size_t storage_bytes(int precision) {
+  switch (precision) {
+    case kFP32: return 4;
+    case kFP64: return 8;
+    case kBF16Dev:
+    case kFP16Dev: return 2;
+  }
+  return 0;
+}
+
+}  // namespace lbm
+
+using namespace lbm;
+
+static thread_local std::string g_create_error;
+
+struct lbm_ctx {
+  lbm_params p{};
+  double T = 0.0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void* f[2] = {nullptr, nullptr};
+  float* rho[2] = {nullptr, nullptr};
+  int cur = 0;  // buffer holding the current state
+  size_t plane = 0;
+  unsigned* d_status = nullptr;
+  unsigned* h_status = nullptr;  // pinned
+  double* d_partial = nullptr;
+  int n_partial = 0;
+  double* d_scalar = nullptr;
+  double* d_tmp = nullptr;  // 3 * plane doubles, allocated on first use
+  double* d_pop = nullptr;  // 9 * plane doubles, allocated on first use
+  bool initialized = false;
+  int last_scheme = LBM_SCHEME_SC;
+  int sm_count = 0;
+  int band_rows_override = 0;
+  std::string err;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+lbm_status fail(lbm_ctx* ctx, lbm_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+lbm_status cuda_fail(lbm_ctx* ctx, cudaError_t e, const char* what) {
+  return fail(ctx, LBM_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(ctx, call)                                  \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+EosCheck eos_check(lbm_ctx* c) {
+  EosCheck k{};
+  k.RT = c->p.R * c->T;
+  k.a = c->p.a;
+  k.b4 = c->p.b / 4.0;
+  k.two_over_G = 2.0 / c->p.G;
+  k.status = c->d_status;
+  return k;
+}
+
+StripLaunch base_launch(lbm_ctx* c) {
+  StripLaunch L{};
+  L.nx = c->p.nx;
+  L.ny = c->p.ny;
+  L.plane = c->plane;
+  L.status = c->d_status;
+  L.RT = c->p.R * c->T;
+  L.a = c->p.a;
+  L.b4 = c->p.b / 4.0;
+  L.two_over_G = 2.0 / c->p.G;
+  L.minus_G = -c->p.G;
+  L.tau = 1.0;
+  L.omega = 1.0;
+  L.sigma_ups = 0.0;
+  L.guo = 0.5;
+  return L;
+}
+
+// Warp-strip geometry: strips of 32 columns, and as many row bands as fill
+// the resident warp slots once (one wave: every warp of a band runs at the
+// same time as its neighbours).
+lbm_status geometry(lbm_ctx* c, int scheme, int mode, StripLaunch& L, int& grid) {
+  int bps = 0;
+  LBM_CUDA(c, strip_occupancy(c->p.precision, scheme, mode, &bps));
+  if (bps < 1) bps = 1;
+  const int warps_per_cta = kStripCtaThreads / 32;
+  const long long resident = (long long)c->sm_count * bps * warps_per_cta;
+  const int n_strips = (c->p.nx + 31) / 32;
+  const int ny = c->p.ny;
+  int band_rows;
+  if (c->band_rows_override > 0) {
+    band_rows = std::min(c->band_rows_override, ny);
+  } else {
+    long long n_bands = std::max<long long>(1, resident / n_strips);
+    const int min_rows = 8;
+    n_bands = std::min<long long>(n_bands, std::max(1, ny / min_rows));
+    band_rows = int((ny + n_bands - 1) / n_bands);
+  }
+  const int n_bands = (ny + band_rows - 1) / band_rows;
+  L.n_strips = n_strips;
+  L.band_rows = band_rows;
+  L.n_bands = n_bands;
+  const long long warps = (long long)n_strips * n_bands;
+  grid = int((warps + warps_per_cta - 1) / warps_per_cta);
+  return LBM_OK;
+}
+
+lbm_status ensure_tmp(lbm_ctx* c, double** buf, size_t count) {
+  if (*buf) return LBM_OK;
+  cudaError_t e = cudaMalloc(buf, count * sizeof(double));
+  if (e != cudaSuccess) {
+    *buf = nullptr;
+    return fail(c, LBM_E_NOMEM, "cudaMalloc of a staging buffer failed");
+  }
+  return LBM_OK;
+}
+
+lbm_status queue_steps(lbm_ctx* c, int n, int scheme, double tau, double sigma) {
+  if (!c) return LBM_E_INVAL;
+  if (n < 0) return fail(c, LBM_E_INVAL, "n must be >= 0");
+  if (scheme < 0 || scheme > LBM_SCHEME_LADD) return fail(c, LBM_E_INVAL, "unknown scheme");
+  if (!(tau > 0.5) || !std::isfinite(tau)) return fail(c, LBM_E_INVAL, "tau must be > 1/2");
+  if (!std::isfinite(sigma)) return fail(c, LBM_E_INVAL, "sigma must be finite");
+  if (!c->initialized) return fail(c, LBM_E_STATE, "state not initialised");
+  if (n == 0) return LBM_OK;
+  StripLaunch L = base_launch(c);
+  L.tau = tau;
+  L.omega = 1.0 / tau;
+  L.sigma_ups = sigma / (tau - 0.5);
+  L.guo = 1.0 - 1.0 / (2.0 * tau);
+  int grid = 0;
+  lbm_status st = geometry(c, scheme, kStepMode, L, grid);
+  if (st != LBM_OK) return st;
+  for (int k = 0; k < n; ++k) {
+    const int s = c->cur, d = 1 - c->cur;
+    L.src = c->f[s];
+    L.dst = c->f[d];
+    L.rho_src = c->rho[s];
+    L.rho_dst = c->rho[d];
+    cudaError_t e = strip_launch(c->p.precision, scheme, kStepMode, L, grid, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
+    c->cur = d;
+  }
+  count_launches((unsigned long long)n);
+  c->last_scheme = scheme;
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_default_params(lbm_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->a = 1.0;
+  p->b = 4.0;
+  p->R = 1.0;
+  p->G = -1.0;
+  p->tc_mode = 0;
+  p->precision = LBM_FP32;
+  p->device = 0;
+  p->cuda_stream = nullptr;
+}
+
+lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
+  g_create_error.clear();
+  if (!p || !out) {
+    g_create_error = "null argument";
+    return LBM_E_INVAL;
+  }
+  *out = nullptr;
+  if (p->nx < 1 || p->ny < 1 || (long long)p->nx * p->ny > 0x7fffffffLL) {
+    g_create_error = "nx, ny must be >= 1 with nx * ny < 2^31";
+    return LBM_E_INVAL;
+  }
+  if (!(p->T_over_Tc > 0.0) || !(p->G < 0.0) || !(p->b > 0.0) || !(p->R > 0.0) ||
+      !(p->a > 0.0)) {
+    g_create_error = "need T_over_Tc > 0, G < 0, a, b, R > 0";
+    return LBM_E_INVAL;
+  }
+  if (p->precision < LBM_FP32 || p->precision > LBM_FP16DEV) {
+    g_create_error = "unknown precision";
+    return LBM_E_INVAL;
+  }
+  double Tc = 0.0;
+  if (p->tc_mode == 0) {
+    double rc, pc;
+    if (lbm_cs_critical_point(p->a, p->b, p->R, &rc, &Tc, &pc) != LBM_OK) {
+      g_create_error = "critical point not found";
+      return LBM_E_INVAL;
+    }
+  } else if (p->tc_mode == 1) {
+    Tc = 0.094;
+  } else {
+    g_create_error = "tc_mode must be 0 or 1";
+    return LBM_E_INVAL;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || p->device < 0 || p->device >= ndev) {
+    g_create_error = "no such CUDA device";
+    return LBM_E_CUDA;
+  }
+  DeviceGuard guard(p->device);
+  lbm_ctx* c = new lbm_ctx();
+  c->p = *p;
+  c->T = p->T_over_Tc * Tc;
+  c->plane = (size_t)p->nx * p->ny;
+  auto bail = [&](lbm_status st, const char* msg) {
+    g_create_error = msg;
+    lbm_destroy(c);
+    return st;
+  };
+  if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, p->device) !=
+      cudaSuccess)
+    return bail(LBM_E_CUDA, "cudaDeviceGetAttribute failed");
+  if (p->cuda_stream) {
+    c->stream = static_cast<cudaStream_t>(p->cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(LBM_E_CUDA, "cudaStreamCreate failed");
+    c->own_stream = true;
+  }
+  const size_t pop_bytes = 9 * c->plane * storage_bytes(p->precision);
+  for (int i = 0; i < 2; ++i) {
+    if (cudaMalloc(&c->f[i], pop_bytes) != cudaSuccess)
+      return bail(LBM_E_NOMEM, "cudaMalloc of a population buffer failed");
+    if (p->precision == LBM_BF16DEV || p->precision == LBM_FP16DEV) {
+      if (cudaMalloc(&c->rho[i], c->plane * sizeof(float)) != cudaSuccess)
+        return bail(LBM_E_NOMEM, "cudaMalloc of a density plane failed");
+    }
+  }
+  c->n_partial = 2 * c->sm_count;
+  if (cudaMalloc(&c->d_status, sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&c->d_partial, c->n_partial * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->d_scalar, sizeof(double)) != cudaSuccess)
+    return bail(LBM_E_NOMEM, "cudaMalloc of scratch failed");
+  if (cudaMallocHost(&c->h_status, sizeof(unsigned)) != cudaSuccess)
+    return bail(LBM_E_NOMEM, "cudaMallocHost failed");
+  if (cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return bail(LBM_E_CUDA, "status init failed");
+  *out = c;
+  return LBM_OK;
+}
+
+lbm_status lbm_destroy(lbm_ctx* c) {
+  if (!c) return LBM_OK;
+  DeviceGuard guard(c->p.device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(c->f[i]);
+    cudaFree(c->rho[i]);
+  }
+  cudaFree(c->d_status);
+  cudaFree(c->d_partial);
+  cudaFree(c->d_scalar);
+  cudaFree(c->d_tmp);
+  cudaFree(c->d_pop);
+  if (c->h_status) cudaFreeHost(c->h_status);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return LBM_OK;
+}
+
+const char* lbm_last_error(const lbm_ctx* c) {
+  return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+lbm_status lbm_get_temperature(const lbm_ctx* c, double* T) {
+  if (!c || !T) return LBM_E_INVAL;
+  *T = c->T;
+  return LBM_OK;
+}
+
+lbm_status lbm_init_density(lbm_ctx* c, const double* rho, const double* ux,
+                            const double* uy) {
+  if (!c) return LBM_E_INVAL;
+  if (!rho) return fail(c, LBM_E_INVAL, "rho is NULL");
+  DeviceGuard guard(c->p.device);
+  lbm_status st = ensure_tmp(c, &c->d_tmp, 3 * c->plane);
+  if (st != LBM_OK) return st;
+  const size_t bytes = c->plane * sizeof(double);
+  double* d_rho = c->d_tmp;
+  double* d_ux = ux ? c->d_tmp + c->plane : nullptr;
+  double* d_uy = uy ? c->d_tmp + 2 * c->plane : nullptr;
+  LBM_CUDA(c, cudaMemcpyAsync(d_rho, rho, bytes, cudaMemcpyHostToDevice, c->stream));
+  if (ux) LBM_CUDA(c, cudaMemcpyAsync(d_ux, ux, bytes, cudaMemcpyHostToDevice, c->stream));
+  if (uy) LBM_CUDA(c, cudaMemcpyAsync(d_uy, uy, bytes, cudaMemcpyHostToDevice, c->stream));
+  LBM_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream));
+  LBM_CUDA(c, set_state_launch(c->p.precision, c->f[c->cur], c->rho[c->cur], c->p.nx, c->p.ny,
+                               c->plane, d_rho, d_ux, d_uy, nullptr, eos_check(c), c->stream));
+  count_launches(1);
+  LBM_CUDA(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(unsigned),
+                              cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (*c->h_status & kStatusInvalidInitFlag) {
+    c->initialized = false;
+    cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream);
+    cudaStreamSynchronize(c->stream);
+    return fail(c, LBM_E_INVAL,
+                "rho outside the domain of psi (rho <= 0, b rho/4 >= 1 or negative radicand)");
+  }
+  c->initialized = true;
+  c->last_scheme = LBM_SCHEME_SC;
+  return LBM_OK;
+}
+
+lbm_status lbm_step_async(lbm_ctx* c, int n, int scheme, double tau, double sigma) {
+  if (!c) return LBM_E_INVAL;
+  DeviceGuard guard(c->p.device);
+  return queue_steps(c, n, scheme, tau, sigma);
+}
+
+lbm_status lbm_sync_status(lbm_ctx* c) {
+  if (!c) return LBM_E_INVAL;
+  DeviceGuard guard(c->p.device);
+  LBM_CUDA(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(unsigned),
+                              cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (*c->h_status & kStatusDivergedFlag)
+    return fail(c, LBM_E_DIVERGED, "density left the domain of psi");
+  return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* c, int n, int scheme, double tau, double sigma) {
+  lbm_status st = lbm_step_async(c, n, scheme, tau, sigma);
+  if (st != LBM_OK) return st;
+  return lbm_sync_status(c);
+}
+
+lbm_status lbm_get_moments(lbm_ctx* c, double* rho, double* vx, double* vy) {
+  if (!c) return LBM_E_INVAL;
+  if (!c->initialized) return fail(c, LBM_E_STATE, "state not initialised");
+  DeviceGuard guard(c->p.device);
+  lbm_status st = ensure_tmp(c, &c->d_tmp, 3 * c->plane);
+  if (st != LBM_OK) return st;
+  StripLaunch L = base_launch(c);
+  L.src = c->f[c->cur];
+  L.rho_src = c->rho[c->cur];
+  L.out_rho = c->d_tmp;
+  L.out_vx = c->d_tmp + c->plane;
+  L.out_vy = c->d_tmp + 2 * c->plane;
+  const int mode = c->last_scheme == LBM_SCHEME_NOFORCE ? kObserveNoForceMode : kObserveMode;
+  int grid = 0;
+  st = geometry(c, LBM_SCHEME_SC, mode, L, grid);
+  if (st != LBM_OK) return st;
+  LBM_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream));
+  LBM_CUDA(c, strip_launch(c->p.precision, LBM_SCHEME_SC, mode, L, grid, c->stream));
+  count_launches(1);
+  const size_t bytes = c->plane * sizeof(double);
+  if (rho) LBM_CUDA(c, cudaMemcpyAsync(rho, L.out_rho, bytes, cudaMemcpyDeviceToHost, c->stream));
+  if (vx) LBM_CUDA(c, cudaMemcpyAsync(vx, L.out_vx, bytes, cudaMemcpyDeviceToHost, c->stream));
+  if (vy) LBM_CUDA(c, cudaMemcpyAsync(vy, L.out_vy, bytes, cudaMemcpyDeviceToHost, c->stream));
+  return lbm_sync_status(c);
+}
+
+lbm_status lbm_get_mass(lbm_ctx* c, double* mass) {
+  if (!c || !mass) return fail(c, LBM_E_INVAL, "null argument");
+  if (!c->initialized) return fail(c, LBM_E_STATE, "state not initialised");
+  DeviceGuard guard(c->p.device);
+  LBM_CUDA(c, mass_launch(c->p.precision, c->f[c->cur], c->rho[c->cur], c->plane, c->d_partial,
+                          c->n_partial, c->d_scalar, c->stream));
+  count_launches(2);
+  LBM_CUDA(c, cudaMemcpyAsync(mass, c->d_scalar, sizeof(double), cudaMemcpyDeviceToHost,
+                              c->stream));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_ctx* c, double* f) {
+  if (!c || !f) return fail(c, LBM_E_INVAL, "null argument");
+  if (!c->initialized) return fail(c, LBM_E_STATE, "state not initialised");
+  DeviceGuard guard(c->p.device);
+  lbm_status st = ensure_tmp(c, &c->d_pop, 9 * c->plane);
+  if (st != LBM_OK) return st;
+  LBM_CUDA(c, get_state_launch(c->p.precision, c->f[c->cur], c->rho[c->cur], c->p.nx, c->p.ny,
+                               c->plane, c->d_pop, c->stream));
+  count_launches(1);
+  LBM_CUDA(c, cudaMemcpyAsync(f, c->d_pop, 9 * c->plane * sizeof(double),
+                              cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_ctx* c, const double* f) {
+  if (!c || !f) return fail(c, LBM_E_INVAL, "null argument");
+  DeviceGuard guard(c->p.device);
+  lbm_status st = ensure_tmp(c, &c->d_pop, 9 * c->plane);
+  if (st != LBM_OK) return st;
+  LBM_CUDA(c, cudaMemcpyAsync(c->d_pop, f, 9 * c->plane * sizeof(double),
+                              cudaMemcpyHostToDevice, c->stream));
+  LBM_CUDA(c, set_state_launch(c->p.precision, c->f[c->cur], c->rho[c->cur], c->p.nx, c->p.ny,
+                               c->plane, nullptr, nullptr, nullptr, c->d_pop, EosCheck{},
+                               c->stream));
+  count_launches(1);
+  LBM_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->initialized = true;
+  return LBM_OK;
+}
+
+unsigned long long lbm_kernel_launch_count(void) { return g_launches.load(); }
+
+lbm_status lbm_set_band_rows(lbm_ctx* c, int band_rows) {
+  if (!c) return LBM_E_INVAL;
+  if (band_rows < 0) return fail(c, LBM_E_INVAL, "band_rows must be >= 0");
+  c->band_rows_override = band_rows;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_launch_geometry(lbm_ctx* c, int scheme, int* n_strips, int* band_rows,
+                                   int* n_bands, int* grid) {
+  if (!c) return LBM_E_INVAL;
+  if (scheme < 0 || scheme > LBM_SCHEME_LADD) return fail(c, LBM_E_INVAL, "unknown scheme");
+  DeviceGuard guard(c->p.device);
+  StripLaunch L = base_launch(c);
+  int g = 0;
+  lbm_status st = geometry(c, scheme, kStepMode, L, g);
+  if (st != LBM_OK) return st;
+  if (n_strips) *n_strips = L.n_strips;
+  if (band_rows) *band_rows = L.band_rows;
+  if (n_bands) *n_bands = L.n_bands;
+  if (grid) *grid = g;
+  return LBM_OK;
+}
+
+}  // extern "C"

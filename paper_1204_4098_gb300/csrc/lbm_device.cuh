@@ -1,0 +1,198 @@
+// Device-side building blocks of the fused pseudopotential D2Q9 step.
+//
+// Lattice (Li, Luo & Li, Sec. II): D2Q9 with c = 1, delta_t = 1,
+// c_s^2 = 1/3, velocities e0 = (0,0); e1..e4 = (1,0), (0,1), (-1,0), (0,-1);
+// e5..e8 = (1,1), (-1,1), (-1,-1), (1,-1); weights 4/9, 1/9, 1/36 (text
+// after Eq. 2) and interaction weights w(1) = 1/3, w(2) = 1/12 (text after
+// Eq. 3).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+constexpr int kQ = 9;
+
+__host__ __device__ constexpr int ex_of(int a) {
+  return a == 1 || a == 5 || a == 8 ? 1 : (a == 3 || a == 6 || a == 7 ? -1 : 0);
+}
+__host__ __device__ constexpr int ey_of(int a) {
+  return a == 2 || a == 5 || a == 6 ? 1 : (a == 4 || a == 7 || a == 8 ? -1 : 0);
+}
+template <class C>
+__host__ __device__ constexpr C w_of(int a) {
+  return a == 0 ? C(4) / C(9) : (a <= 4 ? C(1) / C(9) : C(1) / C(36));
+}
+
+// ---------------------------------------------------------------------------
+// explicitly rounded arithmetic: the potential psi is evaluated both by the
+// lane that owns a column and, as a halo, by the neighbouring warp; writing
+// it with *_rn operations keeps the compiler from contracting the two copies
+// differently, so both see bit-identical values.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float sqrt_rn(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double sqrt_rn(double a) { return __dsqrt_rn(a); }
+
+// ---------------------------------------------------------------------------
+// physical parameters of one lattice, in the compute type C
+// ---------------------------------------------------------------------------
+template <class C>
+struct Phys {
+  C RT;         // R T of Eq. 23
+  C a;          // attraction constant of Eq. 23
+  C b4;         // b / 4  (eta = b rho / 4)
+  C two_over_G; // 2 / G  (Eq. 8 with c = 1)
+  C minus_G;    // -G     (Eq. 3)
+  C tau;        // relaxation time
+  C omega;      // 1 / tau
+  C sigma_ups;  // sigma / (tau - 1/2)  (Eq. 31: v' = v + sigma F / (upsilon psi^2))
+  C guo;        // 1 - 1 / (2 tau)  (B_e = C_e of Eq. 13)
+};
+
+// psi of Eq. 8 with the Carnahan-Starling p_EOS of Eq. 23.  Flags (and
+// returns 0 for) densities outside the domain of psi: rho <= 0, eta >= 1,
+// a negative or non-finite radicand.
+template <class C>
+__device__ __forceinline__ C psi_of_rho(C rho, const Phys<C>& P, bool& bad) {
+  const C one = C(1);
+  C eta = mul_rn(P.b4, rho);
+  C om = sub_rn(one, eta);
+  // 1 + eta + eta^2 - eta^3 = 1 + eta (1 + eta (1 - eta))
+  C num = fma_rn(eta, fma_rn(eta, om, one), one);
+  C den = mul_rn(mul_rn(om, om), om);
+  C p = sub_rn(div_rn(mul_rn(mul_rn(rho, P.RT), num), den), mul_rn(mul_rn(P.a, rho), rho));
+  C arg = mul_rn(P.two_over_G, sub_rn(p, div_rn(rho, C(3))));
+  bool ok = (rho > C(0)) && (eta < one) && (arg >= C(0)) && (arg <= C(1e30));
+  bad |= !ok;
+  return ok ? sqrt_rn(arg) : C(0);
+}
+
+// ---------------------------------------------------------------------------
+// collision of one cell, Eqs. 1-2 with the forcing schemes of Table I
+// ---------------------------------------------------------------------------
+enum Scheme { kSC = 0, kEDM = 1, kImproved = 2, kNoForce = 3, kEDMMod = 4, kLadd = 5 };
+
+// Every scheme of Table I is BGK towards f_eq(rho, u_eq) plus Guo's general
+// forcing term (Eq. 12) with B = B_e F and C = C_e (V F + F V):
+//   F_a = w_a [ 3 B_e (e.F) + C_e (9 (e.V)(e.F) - 3 V.F) ].
+//   SC (Eqs. 9-10):  u_eq = u + tau F / rho, no forcing term
+//   EDM (Eq. 11):    u_eq = u, B_e = C_e = 1, V = u + F/(2 rho)
+//                    (Eq. 16: f_eq(u + F/rho) - f_eq(u) in closed form)
+//   improved (Eq. 31): u_eq = v = u + F/(2 rho), B_e = C_e = 1 - 1/(2 tau),
+//                    V = v' = v + sigma F / ((tau - 1/2) psi^2)
+//   EDM, C_e = 1/tau: u_eq = u, B_e = 1, C_e = 1/tau, V = v
+//   Ladd:            u_eq = u, B_e = C_e = 1, V = u
+//   no force:        u_eq = u, no forcing term
+template <class C, int SCHEME>
+__device__ __forceinline__ void collide(C (&f)[kQ], C rho, C Fx, C Fy, C psi,
+                                        const Phys<C>& P) {
+  const C jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+  const C jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+  const C inv_rho = C(1) / rho;
+  const C ux = jx * inv_rho, uy = jy * inv_rho;
+
+  C qx = ux, qy = uy;  // velocity in f_eq
+  C Vx = C(0), Vy = C(0), Be = C(0), Ce = C(0);
+  constexpr bool kForcing = SCHEME != kSC && SCHEME != kNoForce;
+  if constexpr (SCHEME == kSC) {
+    qx = ux + P.tau * Fx * inv_rho;
+    qy = uy + P.tau * Fy * inv_rho;
+  } else if constexpr (SCHEME == kEDM) {
+    Vx = ux + C(0.5) * Fx * inv_rho;
+    Vy = uy + C(0.5) * Fy * inv_rho;
+    Be = C(1);
+    Ce = C(1);
+  } else if constexpr (SCHEME == kImproved) {
+    qx = ux + C(0.5) * Fx * inv_rho;
+    qy = uy + C(0.5) * Fy * inv_rho;
+    const C s = P.sigma_ups / (psi * psi);
+    Vx = qx + s * Fx;
+    Vy = qy + s * Fy;
+    Be = P.guo;
+    Ce = P.guo;
+  } else if constexpr (SCHEME == kEDMMod) {
+    Vx = ux + C(0.5) * Fx * inv_rho;
+    Vy = uy + C(0.5) * Fy * inv_rho;
+    Be = C(1);
+    Ce = P.omega;
+  } else if constexpr (SCHEME == kLadd) {
+    Vx = ux;
+    Vy = uy;
+    Be = C(1);
+    Ce = C(1);
+  }
+
+  const C om = P.omega;
+  const C one_m_om = C(1) - om;
+  // f_eq_a = w rho (1 - 1.5 q.q + 3 e.q + 4.5 (e.q)^2)
+  const C base = C(1) - C(1.5) * (qx * qx + qy * qy);
+  const C om_rho = om * rho;
+  const C VF3 = C(3) * (Vx * Fx + Vy * Fy);
+#pragma unroll
+  for (int a = 0; a < kQ; ++a) {
+    const int ex = ex_of(a), ey = ey_of(a);
+    const C w = w_of<C>(a);
+    const C eq = C(ex) * qx + C(ey) * qy;
+    const C feq_over_w_rho = base + eq * (C(3) + C(4.5) * eq);
+    C out = one_m_om * f[a] + (w * om_rho) * feq_over_w_rho;
+    if constexpr (kForcing) {
+      const C eF = C(ex) * Fx + C(ey) * Fy;
+      const C eV = C(ex) * Vx + C(ey) * Vy;
+      out += w * (C(3) * Be * eF + Ce * (C(9) * eV * eF - VF3));
+    }
+    f[a] = out;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// population storage
+// ---------------------------------------------------------------------------
+// Direct storage: f stored as T, computed as C.
+// Deviation storage: d_a = f_a - w_a rho_src stored as 16-bit T, plus a float
+// plane rho_src (the density of the cell the populations sit on).
+struct StoreF32 {
+  using T = float;
+  using C = float;
+  static constexpr bool kDev = false;
+  static __device__ __forceinline__ C to_c(T v) { return v; }
+  static __device__ __forceinline__ T from_c(C v) { return v; }
+};
+struct StoreF64 {
+  using T = double;
+  using C = double;
+  static constexpr bool kDev = false;
+  static __device__ __forceinline__ C to_c(T v) { return v; }
+  static __device__ __forceinline__ T from_c(C v) { return v; }
+};
+struct StoreBF16 {
+  using T = __nv_bfloat16;
+  using C = float;
+  static constexpr bool kDev = true;
+  static __device__ __forceinline__ C to_c(T v) { return __bfloat162float(v); }
+  static __device__ __forceinline__ T from_c(C v) { return __float2bfloat16_rn(v); }
+};
+struct StoreF16 {
+  using T = __half;
+  using C = float;
+  static constexpr bool kDev = true;
+  static __device__ __forceinline__ C to_c(T v) { return __half2float(v); }
+  static __device__ __forceinline__ T from_c(C v) { return __float2half_rn(v); }
+};
+
+// Device status bits (same values as the kStatus*Flag constants of the host).
+enum : unsigned { kStatusDiverged = 1u, kStatusTimeout = 2u, kStatusInvalidInit = 4u };
+
+}  // namespace lbm

@@ -1,0 +1,324 @@
+// Fused pseudopotential D2Q9 step kernels (templated on storage and scheme).
+//
+// One time step (Li, Luo & Li, Eq. 1) in pull form: the buffer src holds the
+// post-collision populations f*_a(x', t-1) at the cells they were collided
+// on; the state at time t is f_a(x, t) = f*_a(x - e_a, t - 1).  The kernel
+// reads src, computes rho, u (Sec. III A), psi (Eqs. 8, 23), the force of
+// Eq. 3 and the collision, and writes f*_a(x, t) to dst -- one read and one
+// write of every population per step, nothing else through HBM.
+//
+// Work decomposition ("warp strips"): a warp owns 32 consecutive columns
+// (one per lane) and a band of rows, which it marches down.  For each row it
+// needs psi on the row above and below and on the two columns beside the
+// strip; psi of a row is computed once, when the row is first loaded, and
+// kept in registers for the three output rows that use it.  The x neighbours
+// come from the adjacent lanes by shuffle, the two halo columns from one
+// extra load per direction spread over lanes 0..8 and 16..24.  The next row
+// is loaded while the current one is computed.  Warps of a band run side by
+// side, so the halo reads of one strip hit the lines its neighbours just
+// brought into L2.  Periodic wrap is applied to the indices, so any nx, ny
+// >= 1 works; lanes past the right edge of a ragged strip evaluate the
+// wrapped columns (serving as the right neighbour) and store nothing.
+#pragma once
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+constexpr int kStripWarpsPerCta = 4;
+constexpr int kStripThreads = kStripWarpsPerCta * 32;
+
+template <class S>
+struct StripArgs {
+  const typename S::T* src;   // [9][ny][nx] post-collision populations (t-1)
+  typename S::T* dst;         // [9][ny][nx] post-collision populations (t)
+  const float* rho_src;       // deviation storage: density plane of src
+  float* rho_dst;             // deviation storage: density plane of dst
+  double* out_rho;            // observe mode: rho, v (FP64, [ny][nx])
+  double* out_vx;
+  double* out_vy;
+  unsigned* status;           // device status word
+  int nx, ny;
+  int n_strips;               // ceil(nx / 32)
+  int band_rows;              // rows per warp
+  int n_bands;                // ceil(ny / band_rows)
+  size_t plane;               // nx * ny
+  Phys<typename S::C> P;
+};
+
+enum { kModeStep = 0, kModeObserve = 1, kModeObserveNoForce = 2 };
+
+// Value of population a pulled from source cell index idx.
+template <class S>
+__device__ __forceinline__ typename S::C pull_one(const StripArgs<S>& A, int a, int idx) {
+  using C = typename S::C;
+  C v = S::to_c(__ldg(A.src + a * A.plane + idx));
+  if constexpr (S::kDev) {
+    v += w_of<C>(a) * C(__ldg(A.rho_src + idx));
+  }
+  return v;
+}
+
+static __constant__ int c_ex[16] = {0, 1, 0, -1, 0, 1, -1, -1, 1, 0, 0, 0, 0, 0, 0, 0};
+static __constant__ int c_ey[16] = {0, 0, 1, 0, -1, 1, 1, -1, -1, 0, 0, 0, 0, 0, 0, 0};
+
+template <class S, int SCHEME, int MODE>
+__global__ void __launch_bounds__(kStripThreads)
+strip_kernel(const StripArgs<S> A) {
+  using C = typename S::C;
+  constexpr bool kNeedPsi = !(MODE == kModeObserveNoForce ||
+                              (MODE == kModeStep && SCHEME == kNoForce));
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * kStripThreads + threadIdx.x) >> 5;
+  const int strip = gwarp % A.n_strips;
+  const int band = gwarp / A.n_strips;
+  if (band >= A.n_bands) return;  // warp-uniform
+  const int nx = A.nx, ny = A.ny;
+  const int y0 = band * A.band_rows;
+  const int y1 = min(y0 + A.band_rows, ny);
+
+  const int x = strip * 32 + lane;
+  const bool active = x < nx;
+  const int c = x % nx;
+  const int cm = c == 0 ? nx - 1 : c - 1;
+  const int cp = c == nx - 1 ? 0 : c + 1;
+  // halo lanes: 0..8 pull direction `lane` at the column left of the strip,
+  // 16..24 direction `lane - 16` at the column right of it
+  const int ha = lane & 15;
+  const int hcol = lane < 16 ? (strip * 32 - 1 + nx) % nx : (strip * 32 + 32) % nx;
+  const int hex = c_ex[ha], hey = c_ey[ha];
+  const int hsx = ((hcol - hex) % nx + nx) % nx;
+  const bool hlane = ha < kQ;
+  const int hbase = lane & 16;
+
+  bool bad = false;
+
+  // pulled populations of row y at this lane's column, plus this lane's halo value
+  auto load_row = [&](int y, C (&P)[kQ], C& h) {
+    const int ym = y == 0 ? ny - 1 : y - 1;
+    const int yp = y == ny - 1 ? 0 : y + 1;
+    const int r0 = y * nx, rm = ym * nx, rp = yp * nx;
+    P[0] = pull_one(A, 0, r0 + c);
+    P[1] = pull_one(A, 1, r0 + cm);
+    P[2] = pull_one(A, 2, rm + c);
+    P[3] = pull_one(A, 3, r0 + cp);
+    P[4] = pull_one(A, 4, rp + c);
+    P[5] = pull_one(A, 5, rm + cm);
+    P[6] = pull_one(A, 6, rm + cp);
+    P[7] = pull_one(A, 7, rp + cp);
+    P[8] = pull_one(A, 8, rp + cm);
+    if constexpr (kNeedPsi) {
+      const int hy = ((y - hey) % ny + ny) % ny;
+      h = hlane ? pull_one(A, ha, hy * nx + hsx) : C(0);
+    }
+  };
+  // density with a fixed summation order (the halo path below repeats it)
+  auto rho_of = [](const C (&P)[kQ]) {
+    C r = P[0];
+#pragma unroll
+    for (int a = 1; a < kQ; ++a) r = add_rn(r, P[a]);
+    return r;
+  };
+  // psi of the halo column of this lane's half-warp
+  auto halo_psi = [&](C h) {
+    C r = __shfl_sync(FULL, h, hbase);
+#pragma unroll
+    for (int a = 1; a < kQ; ++a) r = add_rn(r, __shfl_sync(FULL, h, hbase + a));
+    return psi_of_rho(r, A.P, bad);
+  };
+
+  C P0[kQ], P1[kQ], P2[kQ];
+  C h1 = C(0), h2 = C(0);
+  // psi ring: rows y-1 (m), y (z), y+1 (p); W / C / E = columns x-1, x, x+1
+  C Wm = 0, Cm = 0, Em = 0, Wz = 0, Cz = 0, Ez = 0;
+  C rho0;
+
+  auto psi_row = [&](const C (&P)[kQ], C h, C& Wv, C& Cv, C& Ev, C& rho_out) {
+    rho_out = rho_of(P);
+    if constexpr (kNeedPsi) {
+      Cv = psi_of_rho(rho_out, A.P, bad);
+      const C hp = halo_psi(h);
+      Wv = __shfl_up_sync(FULL, Cv, 1);
+      Ev = __shfl_down_sync(FULL, Cv, 1);
+      if (lane == 0) Wv = hp;
+      if (lane == 31) Ev = hp;
+    }
+  };
+
+  // prologue: rows y0-1 and y0, then load y0+1
+  {
+    C rdummy;
+    load_row(y0 == 0 ? ny - 1 : y0 - 1, P0, h1);
+    psi_row(P0, h1, Wm, Cm, Em, rdummy);
+    load_row(y0, P0, h1);
+    psi_row(P0, h1, Wz, Cz, Ez, rho0);
+    load_row(y0 + 1 == ny ? 0 : y0 + 1, P1, h1);
+  }
+
+  for (int y = y0; y < y1; ++y) {
+    const bool more = y + 2 <= y1;
+    if (more) {
+      const int y2 = y + 2 >= ny ? y + 2 - ny : y + 2;
+      load_row(y2, P2, h2);
+    }
+    C Wp = 0, Cp = 0, Ep = 0, rho1;
+    psi_row(P1, h1, Wp, Cp, Ep, rho1);
+
+    C Fx = C(0), Fy = C(0);
+    if constexpr (kNeedPsi) {
+      // Eq. 3: F = -G psi(x) sum_a w(|e_a|^2) psi(x + e_a) e_a
+      const C third = C(1) / C(3), twelfth = C(1) / C(12);
+      const C sx = third * (Ez - Wz) + twelfth * ((Ep - Wp) + (Em - Wm));
+      const C sy = third * (Cp - Cm) + twelfth * ((Ep + Wp) - (Em + Wm));
+      Fx = A.P.minus_G * Cz * sx;
+      Fy = A.P.minus_G * Cz * sy;
+    }
+
+    const int idx = y * nx + c;
+    if constexpr (MODE == kModeStep) {
+      collide<C, SCHEME>(P0, rho0, Fx, Fy, Cz, A.P);
+      if (active) {
+        if constexpr (S::kDev) {
+          A.rho_dst[idx] = float(rho0);
+#pragma unroll
+          for (int a = 0; a < kQ; ++a)
+            A.dst[a * A.plane + idx] = S::from_c(P0[a] - w_of<C>(a) * rho0);
+        } else {
+#pragma unroll
+          for (int a = 0; a < kQ; ++a) A.dst[a * A.plane + idx] = S::from_c(P0[a]);
+        }
+      }
+    } else {
+      if (active) {
+        const C jx = (P0[1] - P0[3]) + (P0[5] - P0[6]) + (P0[8] - P0[7]);
+        const C jy = (P0[2] - P0[4]) + (P0[5] + P0[6]) - (P0[7] + P0[8]);
+        const double r = double(rho0);
+        A.out_rho[idx] = r;
+        A.out_vx[idx] = (double(jx) + 0.5 * double(Fx)) / r;
+        A.out_vy[idx] = (double(jy) + 0.5 * double(Fy)) / r;
+      }
+    }
+
+    // rotate
+    Wm = Wz; Cm = Cz; Em = Ez;
+    Wz = Wp; Cz = Cp; Ez = Ep;
+    rho0 = rho1;
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) { P0[a] = P1[a]; P1[a] = P2[a]; }
+    h1 = h2;
+  }
+  if (__any_sync(FULL, bad) && lane == 0) atomicOr(A.status, kStatusDiverged);
+}
+
+// ---------------------------------------------------------------------------
+// initialisation and checkpoint kernels (not on the per-step path)
+// ---------------------------------------------------------------------------
+
+// f*_a(x') = f_a(x' + e_a): store a physical state (time t, before the pull)
+// so that the next pull reproduces it.  The physical state is either
+// f_eq(rho, u) (init) or given populations (set).
+template <class S>
+__global__ void set_state_kernel(typename S::T* dst, float* rho_dst, int nx, int ny,
+                                 size_t plane, const double* rho, const double* ux,
+                                 const double* uy, const double* f_in, Phys<double> P,
+                                 unsigned* status) {
+  const size_t n = plane;
+  bool bad = false;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int x = int(i % nx), y = int(i / nx);
+    if (!f_in && status) (void)psi_of_rho(rho[i], P, bad);  // domain of psi at the start
+    double fs[kQ];
+    double rsum = 0.0;
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) {
+      const int xd = (x + ex_of(a) + nx) % nx, yd = (y + ey_of(a) + ny) % ny;
+      const size_t j = (size_t)yd * nx + xd;
+      double v;
+      if (f_in) {
+        v = f_in[a * plane + j];
+      } else {
+        const double r = rho[j], u = ux ? ux[j] : 0.0, w = uy ? uy[j] : 0.0;
+        const double eu = ex_of(a) * u + ey_of(a) * w;
+        v = w_of<double>(a) * r * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * (u * u + w * w));
+      }
+      fs[a] = v;
+      rsum += v;
+    }
+    if constexpr (S::kDev) {
+      const float rs = float(rsum);
+      rho_dst[i] = rs;
+#pragma unroll
+      for (int a = 0; a < kQ; ++a)
+        dst[a * plane + i] = S::from_c(float(fs[a] - w_of<double>(a) * double(rs)));
+    } else {
+#pragma unroll
+      for (int a = 0; a < kQ; ++a) dst[a * plane + i] = typename S::T(fs[a]);
+    }
+  }
+  if (bad) atomicOr(status, kStatusInvalidInit);
+}
+
+// f_a(x, t) = f*_a(x - e_a, t-1) as FP64 [9][ny][nx].
+template <class S>
+__global__ void get_state_kernel(const typename S::T* src, const float* rho_src, int nx,
+                                 int ny, size_t plane, double* f_out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < plane;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int x = int(i % nx), y = int(i / nx);
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) {
+      const int xs = (x - ex_of(a) + nx) % nx, ys = (y - ey_of(a) + ny) % ny;
+      const size_t j = (size_t)ys * nx + xs;
+      double v = double(S::to_c(src[a * plane + j]));
+      if constexpr (S::kDev) v += w_of<double>(a) * double(rho_src[j]);
+      f_out[a * plane + i] = v;
+    }
+  }
+}
+
+// Per-block FP64 partial sums of all populations of a buffer (mass); the
+// second pass adds the partials in a fixed order, so the result does not
+// depend on scheduling.
+constexpr int kReduceThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* smem) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) smem[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < int(blockDim.x >> 5); ++i) s += smem[i];
+  return s;
+}
+
+template <class S>
+__global__ void __launch_bounds__(kReduceThreads)
+mass_partial_kernel(const typename S::T* src, const float* rho_src, size_t plane,
+                    double* partial) {
+  __shared__ double smem[kReduceThreads / 32];
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < plane;
+       i += (size_t)gridDim.x * blockDim.x) {
+    double cell = 0.0;
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) cell += double(S::to_c(src[a * plane + i]));
+    if constexpr (S::kDev) cell += double(rho_src[i]);  // sum_a w_a = 1
+    acc += cell;
+  }
+  const double s = block_sum(acc, smem);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+static __global__ void __launch_bounds__(kReduceThreads)
+sum_partials_kernel(const double* partial, int n, double* out) {
+  __shared__ double smem[kReduceThreads / 32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partial[i];
+  const double s = block_sum(acc, smem);
+  if (threadIdx.x == 0) *out = s;
+}
+
+}  // namespace lbm

@@ -1,0 +1,236 @@
+"""Thin ctypes binding of the C ABI declared in ``include/lbm.h``.
+
+Argument marshalling only: every function forwards to the function of the
+same name in ``liblbm_gb300.so``, and every step of the method runs in that
+library's CUDA kernels.  There is no fallback: if the library is missing the
+first call raises, telling how to build it.
+
+``Lattice`` is a small convenience wrapper (numpy arrays in and out, errors
+raised as ``LbmError``) over the same calls.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm_gb300.so")
+
+LBM_OK, LBM_E_INVAL, LBM_E_NOMEM, LBM_E_CUDA, LBM_E_DIVERGED, LBM_E_TIMEOUT, LBM_E_STATE = range(7)
+STATUS_NAMES = {0: "LBM_OK", 1: "LBM_E_INVAL", 2: "LBM_E_NOMEM", 3: "LBM_E_CUDA",
+                4: "LBM_E_DIVERGED", 5: "LBM_E_TIMEOUT", 6: "LBM_E_STATE"}
+SC, EDM, IMPROVED, NOFORCE, EDM_MOD, LADD = range(6)
+FP32, FP64, BF16DEV, FP16DEV = range(4)
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("T_over_Tc", ctypes.c_double), ("tc_mode", ctypes.c_int),
+                ("a", ctypes.c_double), ("b", ctypes.c_double),
+                ("R", ctypes.c_double), ("G", ctypes.c_double),
+                ("precision", ctypes.c_int), ("device", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+_DP = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int)
+
+# name -> (restype, argtypes); the names and order follow include/lbm.h
+SIGNATURES = {
+    "lbm_default_params": (None, [ctypes.POINTER(lbm_params)]),
+    "lbm_create": (_I, [ctypes.POINTER(lbm_params), ctypes.POINTER(_P)]),
+    "lbm_init_density": (_I, [_P, _P, _P, _P]),
+    "lbm_step": (_I, [_P, _I, _I, _D, _D]),
+    "lbm_step_async": (_I, [_P, _I, _I, _D, _D]),
+    "lbm_sync_status": (_I, [_P]),
+    "lbm_get_moments": (_I, [_P, _P, _P, _P]),
+    "lbm_get_mass": (_I, [_P, _DP]),
+    "lbm_get_populations": (_I, [_P, _P]),
+    "lbm_set_populations": (_I, [_P, _P]),
+    "lbm_get_temperature": (_I, [_P, _DP]),
+    "lbm_last_error": (ctypes.c_char_p, [_P]),
+    "lbm_destroy": (_I, [_P]),
+    "lbm_cs_critical_point": (_I, [_D, _D, _D, _DP, _DP, _DP]),
+    "lbm_cs_maxwell": (_I, [_D, _D, _D, _D, _DP, _DP, _DP]),
+    "lbm_kernel_launch_count": (ctypes.c_ulonglong, []),
+    "lbm_set_band_rows": (_I, [_P, _I]),
+    "lbm_get_launch_geometry": (_I, [_P, _I, _IP, _IP, _IP, _IP]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with "
+                "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _fwd(name):
+    def call(*args):
+        return getattr(lib(), name)(*args)
+    call.__name__ = name
+    return call
+
+
+for _name in SIGNATURES:
+    globals()[_name] = _fwd(_name)
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+        return a.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(int(a))  # a raw pointer (e.g. pinned torch memory)
+
+
+def critical_point(a=1.0, b=4.0, R=1.0):
+    rc, tc, pc = _D(), _D(), _D()
+    st = lib().lbm_cs_critical_point(a, b, R, ctypes.byref(rc), ctypes.byref(tc), ctypes.byref(pc))
+    if st:
+        raise LbmError(st, "lbm_cs_critical_point")
+    return rc.value, tc.value, pc.value
+
+
+def maxwell(T, a=1.0, b=4.0, R=1.0):
+    """(rho_g, rho_l, p0) of the Maxwell construction at absolute T."""
+    rg, rl, p0 = _D(), _D(), _D()
+    st = lib().lbm_cs_maxwell(T, a, b, R, ctypes.byref(rg), ctypes.byref(rl), ctypes.byref(p0))
+    if st:
+        raise LbmError(st, "lbm_cs_maxwell")
+    return rg.value, rl.value, p0.value
+
+
+def temperature(T_over_Tc, tc_mode=0, a=1.0, b=4.0, R=1.0):
+    return T_over_Tc * (critical_point(a, b, R)[1] if tc_mode == 0 else 0.094)
+
+
+def launch_count():
+    return int(lib().lbm_kernel_launch_count())
+
+
+class Lattice:
+    """A context of the C ABI with numpy in/out (same life cycle as lbm_*)."""
+
+    def __init__(self, nx, ny, T_over_Tc, precision=FP32, tc_mode=0, a=1.0, b=4.0,
+                 R=1.0, G=-1.0, device=0, stream=None):
+        p = lbm_params()
+        lib().lbm_default_params(ctypes.byref(p))
+        p.nx, p.ny, p.T_over_Tc, p.tc_mode = int(nx), int(ny), float(T_over_Tc), int(tc_mode)
+        p.a, p.b, p.R, p.G = a, b, R, G
+        p.precision, p.device = int(precision), int(device)
+        p.cuda_stream = None if stream is None else ctypes.c_void_p(int(stream))
+        ctx = _P()
+        st = lib().lbm_create(ctypes.byref(p), ctypes.byref(ctx))
+        if st:
+            raise LbmError(st, lib().lbm_last_error(None).decode())
+        self.ctx = ctx
+        self.nx, self.ny = int(nx), int(ny)
+        self.precision = precision
+
+    def _check(self, st, what):
+        if st:
+            raise LbmError(st, f"{what}: {lib().lbm_last_error(self.ctx).decode()}")
+
+    def close(self):
+        if self.ctx:
+            lib().lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def T(self):
+        t = _D()
+        self._check(lib().lbm_get_temperature(self.ctx, ctypes.byref(t)), "lbm_get_temperature")
+        return t.value
+
+    def init_density(self, rho, ux=None, uy=None):
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        ux = None if ux is None else np.ascontiguousarray(ux, dtype=np.float64)
+        uy = None if uy is None else np.ascontiguousarray(uy, dtype=np.float64)
+        assert rho.shape == (self.ny, self.nx)
+        self._check(lib().lbm_init_density(self.ctx, _dptr(rho), _dptr(ux), _dptr(uy)),
+                    "lbm_init_density")
+
+    def step(self, n, scheme, tau, sigma=0.0, raise_on_error=True):
+        st = lib().lbm_step(self.ctx, int(n), int(scheme), float(tau), float(sigma))
+        if raise_on_error:
+            self._check(st, "lbm_step")
+        return st
+
+    def step_async(self, n, scheme, tau, sigma=0.0):
+        self._check(lib().lbm_step_async(self.ctx, int(n), int(scheme), float(tau),
+                                         float(sigma)), "lbm_step_async")
+
+    def sync(self):
+        return lib().lbm_sync_status(self.ctx)
+
+    def observe(self, out=None):
+        """(rho, vx, vy) as FP64 arrays; `out` may supply the three arrays
+        (e.g. views of pinned host memory for fast copies)."""
+        if out is None:
+            out = tuple(np.empty((self.ny, self.nx)) for _ in range(3))
+        rho, vx, vy = out
+        self._check(lib().lbm_get_moments(self.ctx, _dptr(rho), _dptr(vx), _dptr(vy)),
+                    "lbm_get_moments")
+        return rho, vx, vy
+
+    def mass(self):
+        m = _D()
+        self._check(lib().lbm_get_mass(self.ctx, ctypes.byref(m)), "lbm_get_mass")
+        return m.value
+
+    def populations(self):
+        f = np.empty((9, self.ny, self.nx))
+        self._check(lib().lbm_get_populations(self.ctx, _dptr(f)), "lbm_get_populations")
+        return f
+
+    def set_populations(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.shape == (9, self.ny, self.nx)
+        self._check(lib().lbm_set_populations(self.ctx, _dptr(f)), "lbm_set_populations")
+
+    def set_band_rows(self, rows):
+        self._check(lib().lbm_set_band_rows(self.ctx, int(rows)), "lbm_set_band_rows")
+
+    def geometry(self, scheme=SC):
+        v = [_I() for _ in range(4)]
+        self._check(lib().lbm_get_launch_geometry(self.ctx, int(scheme),
+                                                  *[ctypes.byref(x) for x in v]),
+                    "lbm_get_launch_geometry")
+        return dict(zip(("n_strips", "band_rows", "n_bands", "grid"), (x.value for x in v)))

@@ -1,0 +1,251 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on the same seeded
+inputs.  Tolerances: FP64 storage agrees to rounding (1e-13 per step, 1e-11
+after 1e4 steps); FP32 to 1e-4 relative density after 1e4 steps (and 2e-6 of
+the population scale per step); 16-bit deviation storage is reported and
+gated loosely."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import theory as th
+from paper_1204_4098_gb300 import inputs, lbm
+
+pytestmark = pytest.mark.gpu
+
+SCHEMES = [(lbm.SC, 0.0), (lbm.EDM, 0.0), (lbm.IMPROVED, 0.1), (lbm.NOFORCE, 0.0),
+           (lbm.EDM_MOD, 0.0), (lbm.LADD, 0.0)]
+
+
+def maxwell(t, tc_mode=0):
+    return th.maxwell(th.CarnahanStarling(th.temperature(t, tc_mode)))[:2]
+
+
+def droplet_state(nx, ny, t=0.9, seed=5):
+    rg, rl = maxwell(t)
+    rho = inputs.droplet(nx, ny, rg, rl, min(nx, ny) / 4.0, W=4.0)
+    rng = np.random.default_rng(seed)
+    ux = 0.01 * rng.uniform(-1, 1, (ny, nx))
+    uy = 0.01 * rng.uniform(-1, 1, (ny, nx))
+    return rho, ux, uy
+
+
+def run_pair(nx, ny, t, rho, ux, uy, scheme, tau, sigma, steps, precision):
+    gpu = lbm.Lattice(nx, ny, t, precision=precision)
+    gpu.init_density(rho, ux, uy)
+    gpu.step(steps, scheme, tau, sigma)
+    ref = oracle.Lattice(nx, ny, t)
+    ref.init_density(rho, ux, uy)
+    rc, _ = ref.step(steps, scheme, tau, sigma)
+    assert rc == 0
+    return gpu, ref
+
+
+@pytest.mark.parametrize("scheme,sigma", SCHEMES)
+@pytest.mark.parametrize("steps", [1, 20])
+def test_populations_fp32(scheme, sigma, steps):
+    nx, ny, t = 45, 37, 0.9  # two strips (one ragged), rows not a band multiple
+    rho, ux, uy = droplet_state(nx, ny, t)
+    gpu, ref = run_pair(nx, ny, t, rho, ux, uy, scheme, 0.8, sigma, steps, lbm.FP32)
+    fg, fo = gpu.populations(), ref.f
+    err = np.max(np.abs(fg - fo)) / np.max(np.abs(fo))
+    assert err < 2e-6 * steps ** 0.5, err
+    rg, vxg, vyg = gpu.observe()
+    ro, vxo, vyo = ref.observe()
+    assert np.max(np.abs(rg / ro - 1)) < 2e-6 * steps ** 0.5
+    assert np.max(np.abs(vxg - vxo)) < 1e-6 and np.max(np.abs(vyg - vyo)) < 1e-6
+
+
+@pytest.mark.parametrize("scheme,sigma", SCHEMES)
+def test_populations_fp64(scheme, sigma):
+    nx, ny, t = 45, 37, 0.9
+    rho, ux, uy = droplet_state(nx, ny, t)
+    for steps in (1, 25):
+        gpu, ref = run_pair(nx, ny, t, rho, ux, uy, scheme, 0.8, sigma, steps, lbm.FP64)
+        fg, fo = gpu.populations(), ref.f
+        assert np.max(np.abs(fg - fo)) / np.max(np.abs(fo)) < 1e-13
+        rg, vxg, vyg = gpu.observe()
+        ro, vxo, vyo = ref.observe()
+        assert np.max(np.abs(rg - ro)) < 1e-14
+        assert np.max(np.abs(vxg - vxo)) < 1e-13 and np.max(np.abs(vyg - vyo)) < 1e-13
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 5), (5, 1), (1, 1), (3, 3), (5, 4), (31, 2), (32, 32),
+                                   (33, 65), (64, 3), (97, 9)])
+def test_edge_sizes_fp64(nx, ny):
+    t = 0.9
+    rg, rl = maxwell(t)
+    rho = rg + (rl - rg) * np.random.default_rng(nx * 100 + ny).uniform(0.3, 0.7, (ny, nx))
+    gpu, ref = run_pair(nx, ny, t, rho, None, None, lbm.IMPROVED, 0.9, 0.1, 5, lbm.FP64)
+    assert np.max(np.abs(gpu.populations() - ref.f)) < 1e-13
+
+
+# --- config 1: 64 x 64 flat interface, Shan-Chen, tau = 1, T = 0.8 Tc, 1e4 steps ---
+
+_CONFIG1 = {}
+
+
+def config1_oracle():
+    if "ref" not in _CONFIG1:
+        nx = ny = 64
+        rg, rl = maxwell(0.8)
+        rho0 = inputs.slab_step(nx, ny, rg, rl, 16, 48, amp=1e-3, seed=1)
+        ref = oracle.Lattice(nx, ny, 0.8)
+        ref.init_density(rho0)
+        rc, _ = ref.step(10000, oracle.SC, 1.0)
+        assert rc == 0
+        _CONFIG1.update(rho0=rho0, ref=ref.observe(), mass0=float(rho0.sum()))
+    return _CONFIG1
+
+
+@pytest.mark.parametrize("precision,tol", [(lbm.FP32, 1e-4), (lbm.FP64, 1e-11)])
+def test_config1_flat_interface_1e4_steps(precision, tol):
+    c = config1_oracle()
+    gpu = lbm.Lattice(64, 64, 0.8, precision=precision)
+    gpu.init_density(c["rho0"])
+    gpu.step(10000, lbm.SC, 1.0)
+    rho, vx, vy = gpu.observe()
+    err = np.max(np.abs(rho / c["ref"][0] - 1))
+    assert err <= tol, err
+    # coexistence densities (vapour rows 0, ny-1; liquid rows ny/2-1, ny/2)
+    rg = 0.5 * (rho[0].mean() + rho[-1].mean())
+    rl = 0.5 * (rho[31].mean() + rho[32].mean())
+    mg, ml = maxwell(0.8)
+    assert rl == pytest.approx(ml, rel=0.02) and 0.5 * mg < rg < 2 * mg
+
+
+@pytest.mark.parametrize("precision,tol", [(lbm.FP16DEV, 2e-3), (lbm.BF16DEV, 3e-2)])
+def test_config1_16bit_deviation_storage(precision, tol):
+    """Deviation storage d_a = f_a - w_a rho in 16 bits with FP32 arithmetic;
+    the error against the FP64 oracle after 1e4 steps is reported and gated
+    loosely (half: 11-bit mantissa, bf16: 8-bit)."""
+    c = config1_oracle()
+    gpu = lbm.Lattice(64, 64, 0.8, precision=precision)
+    gpu.init_density(c["rho0"])
+    gpu.step(10000, lbm.SC, 1.0)
+    rho, _, _ = gpu.observe()
+    err = np.max(np.abs(rho / c["ref"][0] - 1))
+    print(f"16-bit precision {precision}: max rel rho error {err:.3e} after 1e4 steps")
+    assert err <= tol, err
+
+
+@pytest.mark.parametrize("precision,tol", [(lbm.FP64, 1e-13), (lbm.FP32, 1e-6)])
+def test_mass_conservation(precision, tol):
+    nx, ny, t = 70, 50, 0.85
+    rho, ux, uy = droplet_state(nx, ny, t)
+    gpu = lbm.Lattice(nx, ny, t, precision=precision)
+    gpu.init_density(rho, ux, uy)
+    m0 = gpu.mass()
+    assert m0 == pytest.approx(rho.sum(), rel=1e-7 if precision == lbm.FP32 else 1e-14)
+    gpu.step(1000, lbm.IMPROVED, 0.7, 0.105)
+    assert abs(gpu.mass() / m0 - 1) < tol
+
+
+@pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP64, lbm.BF16DEV])
+def test_band_rows_do_not_change_results(precision):
+    """The psi halo computed by a neighbouring warp equals the value the owning
+    lane computes, so the result is bit-identical for any band height."""
+    nx, ny, t = 77, 53, 0.85
+    rho, ux, uy = droplet_state(nx, ny, t)
+    out = []
+    for rows in (0, 1, 2, 5, 16, 53):
+        gpu = lbm.Lattice(nx, ny, t, precision=precision)
+        gpu.set_band_rows(rows)
+        gpu.init_density(rho, ux, uy)
+        gpu.step(30, lbm.IMPROVED, 0.8, 0.1)
+        out.append(gpu.populations())
+    for f in out[1:]:
+        assert np.array_equal(f, out[0])
+
+
+def test_checkpoint_roundtrip_is_bitwise():
+    nx, ny, t = 64, 40, 0.85
+    rho, ux, uy = droplet_state(nx, ny, t)
+    for precision in (lbm.FP32, lbm.FP64):
+        a = lbm.Lattice(nx, ny, t, precision=precision)
+        a.init_density(rho, ux, uy)
+        a.step(40, lbm.EDM, 0.7)
+        b = lbm.Lattice(nx, ny, t, precision=precision)
+        a.step(10, lbm.EDM, 0.7)
+        b.set_populations(a.populations())
+        a.step(10, lbm.EDM, 0.7)
+        b.step(10, lbm.EDM, 0.7)
+        assert np.array_equal(a.populations(), b.populations())
+
+
+def test_noforce_taylor_green_fp32_vs_oracle():
+    n = 48
+    rho, ux, uy, k = inputs.taylor_green(n, n, u0=1e-3, rho0=0.2)
+    gpu, ref = run_pair(n, n, 1.5, rho, ux, uy, lbm.NOFORCE, 0.9, 0.0, 300, lbm.FP32)
+    _, vxg, vyg = gpu.observe()
+    _, vxo, vyo = ref.observe()
+    assert np.max(np.abs(vxg - vxo)) < 1e-8 and np.max(np.abs(vyg - vyo)) < 1e-8
+
+
+def test_divergence_is_reported_and_context_survives():
+    nx, ny, t = 40, 30, 0.8
+    rg, rl = maxwell(t)
+    rho = inputs.slab_step(nx, ny, rg, rl)
+    f = oracle.init_equilibrium(rho)
+    f[:, 10, 10] *= 1.2 / rho[10, 10]  # rho = 1.2 > 4/b: outside the domain of psi
+    gpu = lbm.Lattice(nx, ny, t)
+    gpu.set_populations(f)
+    assert gpu.step(3, lbm.SC, 1.0, raise_on_error=False) == lbm.LBM_E_DIVERGED
+    gpu.init_density(rho)
+    assert gpu.step(3, lbm.SC, 1.0, raise_on_error=False) == lbm.LBM_OK
+
+
+def test_invalid_arguments():
+    gpu = lbm.Lattice(16, 16, 0.8)
+    with pytest.raises(lbm.LbmError) as e:
+        gpu.step(1, lbm.SC, 1.0)
+    assert e.value.status == lbm.LBM_E_STATE
+    bad = np.full((16, 16), 0.2)
+    bad[3, 3] = 1.5
+    with pytest.raises(lbm.LbmError) as e:
+        gpu.init_density(bad)
+    assert e.value.status == lbm.LBM_E_INVAL
+    gpu.init_density(np.full((16, 16), 0.2))
+    for args in ((1, lbm.SC, 0.5), (1, 17, 1.0), (-1, lbm.SC, 1.0), (1, lbm.SC, float("nan"))):
+        assert gpu.step(*args, raise_on_error=False) == lbm.LBM_E_INVAL
+    assert gpu.step(0, lbm.SC, 1.0, raise_on_error=False) == lbm.LBM_OK
+
+
+# --- full size: 8192 x 8192 spinodal decomposition, improved scheme -------------
+
+def _one_step_rho_at(rho0, RT, y, x, tau, sigma):
+    """rho(x, t=1) from f(., 0) = f_eq(rho0, 0), by the oracle's own primitives
+    on the 5x5 neighbourhood (psi radius 2 -> F radius 1 -> pull)."""
+    ny, nx = rho0.shape
+    ys = [(y + d) % ny for d in range(-2, 3)]
+    xs = [(x + d) % nx for d in range(-2, 3)]
+    win = rho0[np.ix_(ys, xs)]
+    psi = np.array([[oracle.psi(r, RT) for r in row] for row in win])
+    Fx, Fy = oracle.force(psi)
+    total = 0.0
+    for a in range(9):
+        sy, sx = 2 - oracle.EY[a], 2 - oracle.EX[a]  # source cell x - e_a in the window
+        fs = oracle.feq(win[sy, sx], 0.0, 0.0)
+        post = oracle.collide_cell(oracle.IMPROVED, tau, sigma, fs, Fx[sy, sx], Fy[sy, sx],
+                                   psi[sy, sx])
+        total += post[a]
+    return total
+
+
+def test_full_size_8192_sampled_against_oracle():
+    n, t, tau, sigma = 8192, 0.85, 0.8, 0.1
+    rg, rl = maxwell(t)
+    rho0 = inputs.spinodal(n, n, 0.5 * (rg + rl), amp=0.01, seed=3)
+    gpu = lbm.Lattice(n, n, t, precision=lbm.FP32)
+    gpu.init_density(rho0)
+    m0 = gpu.mass()
+    gpu.step(1, lbm.IMPROVED, tau, sigma)
+    rho1, _, _ = gpu.observe()
+    RT = th.temperature(t)
+    rng = np.random.default_rng(8)
+    cells = [(0, 0), (0, n - 1), (n - 1, 0), (n - 1, n - 1), (4095, 31), (17, 32)]
+    cells += [tuple(v) for v in rng.integers(0, n, (150, 2))]
+    for y, x in cells:
+        want = _one_step_rho_at(rho0, RT, y, x, tau, sigma)
+        assert rho1[y, x] == pytest.approx(want, rel=2e-6), (y, x)
+    gpu.step(9, lbm.IMPROVED, tau, sigma)
+    assert abs(gpu.mass() / m0 - 1) < 1e-9
