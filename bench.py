@@ -213,7 +213,9 @@ def run_ours(args, world, rank, local):
     from paper_1204_4098_gb300 import lbm
 
     torch.cuda.set_device(local)
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the library runs on it and the events are recorded on it
+    stream = torch.cuda.Stream(device=local)
+    assert stream.cuda_stream != 0
     prec = {"fp32": lbm.FP32, "fp64": lbm.FP64, "bf16dev": lbm.BF16DEV,
             "fp16dev": lbm.FP16DEV}[args.precision]
     n = args.n

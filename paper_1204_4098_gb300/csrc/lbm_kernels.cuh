@@ -48,13 +48,20 @@ struct StripArgs {
 
 enum { kModeStep = 0, kModeObserve = 1, kModeObserveNoForce = 2 };
 
-// Value of population a pulled from source cell index idx.
-template <class S>
+// Value of population a pulled from source cell index idx.  kCoherent loads
+// bypass L1 (ld.global.cg): needed when the same kernel wrote the source
+// buffer in an earlier step (persistent batch kernel); otherwise the
+// read-only path is used.
+template <class S, bool kCoherent>
 __device__ __forceinline__ typename S::C pull_one(const StripArgs<S>& A, int a, int idx) {
   using C = typename S::C;
-  C v = S::to_c(__ldg(A.src + a * A.plane + idx));
-  if constexpr (S::kDev) {
-    v += w_of<C>(a) * C(__ldg(A.rho_src + idx));
+  C v;
+  if constexpr (kCoherent) {
+    v = S::to_c(__ldcg(A.src + a * A.plane + idx));
+    if constexpr (S::kDev) v += w_of<C>(a) * C(__ldcg(A.rho_src + idx));
+  } else {
+    v = S::to_c(__ldg(A.src + a * A.plane + idx));
+    if constexpr (S::kDev) v += w_of<C>(a) * C(__ldg(A.rho_src + idx));
   }
   return v;
 }
@@ -62,18 +69,14 @@ __device__ __forceinline__ typename S::C pull_one(const StripArgs<S>& A, int a, 
 static __constant__ int c_ex[16] = {0, 1, 0, -1, 0, 1, -1, -1, 1, 0, 0, 0, 0, 0, 0, 0};
 static __constant__ int c_ey[16] = {0, 0, 1, 0, -1, 1, 1, -1, -1, 0, 0, 0, 0, 0, 0, 0};
 
-template <class S, int SCHEME, int MODE>
-__global__ void __launch_bounds__(kStripThreads)
-strip_kernel(const StripArgs<S> A) {
+// One warp advances (or observes) the cells of one strip x band item.
+template <class S, int SCHEME, int MODE, bool kCoherent>
+__device__ __forceinline__ void strip_run(const StripArgs<S>& A, int strip, int band,
+                                          int lane) {
   using C = typename S::C;
   constexpr bool kNeedPsi = !(MODE == kModeObserveNoForce ||
                               (MODE == kModeStep && SCHEME == kNoForce));
   const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  const int gwarp = (blockIdx.x * kStripThreads + threadIdx.x) >> 5;
-  const int strip = gwarp % A.n_strips;
-  const int band = gwarp / A.n_strips;
-  if (band >= A.n_bands) return;  // warp-uniform
   const int nx = A.nx, ny = A.ny;
   const int y0 = band * A.band_rows;
   const int y1 = min(y0 + A.band_rows, ny);
@@ -99,18 +102,18 @@ strip_kernel(const StripArgs<S> A) {
     const int ym = y == 0 ? ny - 1 : y - 1;
     const int yp = y == ny - 1 ? 0 : y + 1;
     const int r0 = y * nx, rm = ym * nx, rp = yp * nx;
-    P[0] = pull_one(A, 0, r0 + c);
-    P[1] = pull_one(A, 1, r0 + cm);
-    P[2] = pull_one(A, 2, rm + c);
-    P[3] = pull_one(A, 3, r0 + cp);
-    P[4] = pull_one(A, 4, rp + c);
-    P[5] = pull_one(A, 5, rm + cm);
-    P[6] = pull_one(A, 6, rm + cp);
-    P[7] = pull_one(A, 7, rp + cp);
-    P[8] = pull_one(A, 8, rp + cm);
+    P[0] = pull_one<S, kCoherent>(A, 0, r0 + c);
+    P[1] = pull_one<S, kCoherent>(A, 1, r0 + cm);
+    P[2] = pull_one<S, kCoherent>(A, 2, rm + c);
+    P[3] = pull_one<S, kCoherent>(A, 3, r0 + cp);
+    P[4] = pull_one<S, kCoherent>(A, 4, rp + c);
+    P[5] = pull_one<S, kCoherent>(A, 5, rm + cm);
+    P[6] = pull_one<S, kCoherent>(A, 6, rm + cp);
+    P[7] = pull_one<S, kCoherent>(A, 7, rp + cp);
+    P[8] = pull_one<S, kCoherent>(A, 8, rp + cm);
     if constexpr (kNeedPsi) {
       const int hy = ((y - hey) % ny + ny) % ny;
-      h = hlane ? pull_one(A, ha, hy * nx + hsx) : C(0);
+      h = hlane ? pull_one<S, kCoherent>(A, ha, hy * nx + hsx) : C(0);
     }
   };
   // density with a fixed summation order (the halo path below repeats it)
@@ -180,10 +183,16 @@ strip_kernel(const StripArgs<S> A) {
       collide<C, SCHEME>(P0, rho0, Fx, Fy, Cz, A.P);
       if (active) {
         if constexpr (S::kDev) {
-          A.rho_dst[idx] = float(rho0);
+          // the density plane absorbs the 16-bit rounding of the deviations,
+          // so w_a rho_dst + d_a still sums to rho over a (mass conserved)
+          C resid = rho0;
 #pragma unroll
-          for (int a = 0; a < kQ; ++a)
-            A.dst[a * A.plane + idx] = S::from_c(P0[a] - w_of<C>(a) * rho0);
+          for (int a = 0; a < kQ; ++a) {
+            const typename S::T d = S::from_c(P0[a] - w_of<C>(a) * rho0);
+            A.dst[a * A.plane + idx] = d;
+            resid -= S::to_c(d);
+          }
+          A.rho_dst[idx] = float(resid);
         } else {
 #pragma unroll
           for (int a = 0; a < kQ; ++a) A.dst[a * A.plane + idx] = S::from_c(P0[a]);
@@ -209,6 +218,17 @@ strip_kernel(const StripArgs<S> A) {
     h1 = h2;
   }
   if (__any_sync(FULL, bad) && lane == 0) atomicOr(A.status, kStatusDiverged);
+}
+
+template <class S, int SCHEME, int MODE>
+__global__ void __launch_bounds__(kStripThreads)
+strip_kernel(const StripArgs<S> A) {
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * kStripThreads + threadIdx.x) >> 5;
+  const int strip = gwarp % A.n_strips;
+  const int band = gwarp / A.n_strips;
+  if (band >= A.n_bands) return;  // warp-uniform
+  strip_run<S, SCHEME, MODE, false>(A, strip, band, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -248,10 +268,14 @@ __global__ void set_state_kernel(typename S::T* dst, float* rho_dst, int nx, int
     }
     if constexpr (S::kDev) {
       const float rs = float(rsum);
-      rho_dst[i] = rs;
+      float resid = rs;
 #pragma unroll
-      for (int a = 0; a < kQ; ++a)
-        dst[a * plane + i] = S::from_c(float(fs[a] - w_of<double>(a) * double(rs)));
+      for (int a = 0; a < kQ; ++a) {
+        const typename S::T d = S::from_c(float(fs[a] - double(w_of<float>(a)) * double(rs)));
+        dst[a * plane + i] = d;
+        resid -= S::to_c(d);
+      }
+      rho_dst[i] = resid;
     } else {
 #pragma unroll
       for (int a = 0; a < kQ; ++a) dst[a * plane + i] = typename S::T(fs[a]);
@@ -272,7 +296,7 @@ __global__ void get_state_kernel(const typename S::T* src, const float* rho_src,
       const int xs = (x - ex_of(a) + nx) % nx, ys = (y - ey_of(a) + ny) % ny;
       const size_t j = (size_t)ys * nx + xs;
       double v = double(S::to_c(src[a * plane + j]));
-      if constexpr (S::kDev) v += w_of<double>(a) * double(rho_src[j]);
+      if constexpr (S::kDev) v += double(w_of<float>(a)) * double(rho_src[j]);
       f_out[a * plane + i] = v;
     }
   }
