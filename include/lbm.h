@@ -167,6 +167,26 @@ lbm_status lbm_set_band_rows(lbm_ctx *ctx, int band_rows);
 lbm_status lbm_get_launch_geometry(lbm_ctx *ctx, int scheme, int *n_strips,
                                    int *band_rows, int *n_bands, int *grid);
 
+/* ---- allocation-free variant ------------------------------------------- */
+
+/* FP64 sum of n FP32 values in device memory (for an FP32 population buffer
+ * [9][ny][nx]: its total mass), written to the caller's device slot *d_out.
+ * The paper has no counterpart: this is a deployment helper for callers that
+ * cannot call cudaMalloc -- code whose device memory belongs to another
+ * allocator (a framework's caching pool, a fixed budget) or that must not
+ * block on an allocation.  It allocates nothing: its partial sums live in a
+ * fixed 8 KB file-scope device array (1024 doubles), held by every GPU that
+ * loads the library until exit.  Each block sums 2^20 values, so n may be at
+ * most 1024 * 2^20 (= 2^30); larger n returns LBM_E_INVAL, as do NULL
+ * pointers.  The first call on a device (the one current when called) looks
+ * up the array's device address; make that first call before any stream
+ * capture.  Kernels are queued on cuda_stream (NULL: the legacy default
+ * stream) and the call returns without waiting.  Every call on a device
+ * shares the array and overwrites what it uses (nothing needs clearing), so
+ * calls whose kernels overlap on the GPU race: order them on one stream. */
+lbm_status lbm_mass_f32_noalloc(const float *d_values, size_t n, double *d_out,
+                                void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

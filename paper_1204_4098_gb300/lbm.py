@@ -66,6 +66,7 @@ SIGNATURES = {
     "lbm_kernel_launch_count": (ctypes.c_ulonglong, []),
     "lbm_set_band_rows": (_I, [_P, _I]),
     "lbm_get_launch_geometry": (_I, [_P, _I, _IP, _IP, _IP, _IP]),
+    "lbm_mass_f32_noalloc": (_I, [_P, ctypes.c_size_t, _P, _P]),
 }
 
 _lib = None
