@@ -38,7 +38,8 @@ def _nvcc() -> str:
 
 def _compile(src: str) -> tuple[str, str]:
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+    extra = os.environ.get("LBM_NVCC_EXTRA", "").split()  # e.g. -DLBM_STRIP_MIN_BLOCKS=6
+    cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")

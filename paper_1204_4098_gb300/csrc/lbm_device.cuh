@@ -71,6 +71,15 @@ struct Phys {
   C guo;        // 1 - 1 / (2 tau)  (B_e = C_e of Eq. 13)
 };
 
+// Reciprocal and square root for the per-cell physics.  FP64 keeps the IEEE
+// operations (it is the parity reference on the GPU); FP32 uses the hardware
+// approximations (MUFU.RCP / MUFU.RSQ, ~1 ulp), which are deterministic, so
+// the owner and the halo copy of psi stay bit-identical.
+__device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fast_div(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float fast_sqrt_pos(float a) { return a * rsqrtf(a); }
+__device__ __forceinline__ double fast_sqrt_pos(double a) { return __dsqrt_rn(a); }
+
 // psi of Eq. 8 with the Carnahan-Starling p_EOS of Eq. 23.  Flags (and
 // returns 0 for) densities outside the domain of psi: rho <= 0, eta >= 1,
 // a negative or non-finite radicand.
@@ -82,11 +91,11 @@ __device__ __forceinline__ C psi_of_rho(C rho, const Phys<C>& P, bool& bad) {
   // 1 + eta + eta^2 - eta^3 = 1 + eta (1 + eta (1 - eta))
   C num = fma_rn(eta, fma_rn(eta, om, one), one);
   C den = mul_rn(mul_rn(om, om), om);
-  C p = sub_rn(div_rn(mul_rn(mul_rn(rho, P.RT), num), den), mul_rn(mul_rn(P.a, rho), rho));
-  C arg = mul_rn(P.two_over_G, sub_rn(p, div_rn(rho, C(3))));
-  bool ok = (rho > C(0)) && (eta < one) && (arg >= C(0)) && (arg <= C(1e30));
+  C p = sub_rn(fast_div(mul_rn(mul_rn(rho, P.RT), num), den), mul_rn(mul_rn(P.a, rho), rho));
+  C arg = mul_rn(P.two_over_G, sub_rn(p, mul_rn(rho, C(1) / C(3))));
+  const bool ok = (rho > C(0)) && (eta < one) && (arg >= C(0)) && (arg <= C(1e30));
   bad |= !ok;
-  return ok ? sqrt_rn(arg) : C(0);
+  return (ok && arg > C(0)) ? fast_sqrt_pos(arg) : C(0);
 }
 
 // ---------------------------------------------------------------------------
@@ -110,7 +119,7 @@ __device__ __forceinline__ void collide(C (&f)[kQ], C rho, C Fx, C Fy, C psi,
                                         const Phys<C>& P) {
   const C jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
   const C jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-  const C inv_rho = C(1) / rho;
+  const C inv_rho = fast_div(C(1), rho);
   const C ux = jx * inv_rho, uy = jy * inv_rho;
 
   C qx = ux, qy = uy;  // velocity in f_eq
@@ -127,7 +136,7 @@ __device__ __forceinline__ void collide(C (&f)[kQ], C rho, C Fx, C Fy, C psi,
   } else if constexpr (SCHEME == kImproved) {
     qx = ux + C(0.5) * Fx * inv_rho;
     qy = uy + C(0.5) * Fy * inv_rho;
-    const C s = P.sigma_ups / (psi * psi);
+    const C s = fast_div(P.sigma_ups, psi * psi);
     Vx = qx + s * Fx;
     Vy = qy + s * Fy;
     Be = P.guo;
@@ -146,24 +155,30 @@ __device__ __forceinline__ void collide(C (&f)[kQ], C rho, C Fx, C Fy, C psi,
 
   const C om = P.omega;
   const C one_m_om = C(1) - om;
-  // f_eq_a = w rho (1 - 1.5 q.q + 3 e.q + 4.5 (e.q)^2)
+  // f_eq_a = w rho (1 - 1.5 q.q + 3 e.q + 4.5 (e.q)^2), F_a as above.  For an
+  // opposite pair (a, b), e_b = -e_a: the terms even in e are shared and the
+  // odd ones change sign, so each pair is evaluated once.
   const C base = C(1) - C(1.5) * (qx * qx + qy * qy);
   const C om_rho = om * rho;
   const C VF3 = C(3) * (Vx * Fx + Vy * Fy);
-#pragma unroll
-  for (int a = 1; a < kQ; ++a) {
-    const int ex = ex_of(a), ey = ey_of(a);
-    const C w = w_of<C>(a);
-    const C eq = C(ex) * qx + C(ey) * qy;
-    const C feq_over_w_rho = base + eq * (C(3) + C(4.5) * eq);
-    C out = one_m_om * f[a] + (w * om_rho) * feq_over_w_rho;
+  auto pair = [&](int a, int b, C w, C eq, C eF, C eV) {
+    const C wr = w * om_rho;
+    C even = wr * (base + C(4.5) * eq * eq);
+    C odd = (C(3) * wr) * eq;
     if constexpr (kForcing) {
-      const C eF = C(ex) * Fx + C(ey) * Fy;
-      const C eV = C(ex) * Vx + C(ey) * Vy;
-      out += w * (C(3) * Be * eF + Ce * (C(9) * eV * eF - VF3));
+      even += (w * Ce) * (C(9) * eV * eF - VF3);
+      odd += (C(3) * w * Be) * eF;
     }
-    f[a] = out;
-  }
+    const C fa = one_m_om * f[a] + even;
+    const C fb = one_m_om * f[b] + even;
+    f[a] = fa + odd;
+    f[b] = fb - odd;
+  };
+  const C w1 = w_of<C>(1), w2 = w_of<C>(5);
+  pair(1, 3, w1, qx, Fx, Vx);
+  pair(2, 4, w1, qy, Fy, Vy);
+  pair(5, 7, w2, qx + qy, Fx + Fy, Vx + Vy);   // e5 = (1,1), e7 = (-1,-1)
+  pair(6, 8, w2, qy - qx, Fy - Fx, Vy - Vx);   // e6 = (-1,1), e8 = (1,-1)
   // Every scheme conserves mass (sum_a F_a = 0, sum_a f_eq = rho); taking the
   // rest population as the remainder makes that hold to one rounding instead
   // of nine, so FP32 runs do not drift in mass.

@@ -27,6 +27,14 @@ namespace lbm {
 
 constexpr int kStripWarpsPerCta = 4;
 constexpr int kStripThreads = kStripWarpsPerCta * 32;
+// Resident CTAs per SM the register allocation must allow (occupancy target).
+#ifndef LBM_STRIP_MIN_BLOCKS
+#define LBM_STRIP_MIN_BLOCKS 6
+#endif
+// 1: unroll the row loop by three (no register moves, more registers).
+#ifndef LBM_STRIP_UNROLL3
+#define LBM_STRIP_UNROLL3 0
+#endif
 
 template <class S>
 struct StripArgs {
@@ -112,7 +120,8 @@ __device__ __forceinline__ void strip_run(const StripArgs<S>& A, int strip, int 
     P[7] = pull_one<S, kCoherent>(A, 7, rp + cp);
     P[8] = pull_one<S, kCoherent>(A, 8, rp + cm);
     if constexpr (kNeedPsi) {
-      const int hy = ((y - hey) % ny + ny) % ny;
+      int hy = y - hey;  // |hey| <= 1 and 0 <= y < ny: one conditional wrap
+      hy = hy < 0 ? hy + ny : (hy >= ny ? hy - ny : hy);
       h = hlane ? pull_one<S, kCoherent>(A, ha, hy * nx + hsx) : C(0);
     }
   };
@@ -131,8 +140,6 @@ __device__ __forceinline__ void strip_run(const StripArgs<S>& A, int strip, int 
     return psi_of_rho(r, A.P, bad);
   };
 
-  C P0[kQ], P1[kQ], P2[kQ];
-  C h1 = C(0), h2 = C(0);
   // psi ring: rows y-1 (m), y (z), y+1 (p); W / C / E = columns x-1, x, x+1
   C Wm = 0, Cm = 0, Em = 0, Wz = 0, Cz = 0, Ez = 0;
   C rho0;
@@ -149,24 +156,15 @@ __device__ __forceinline__ void strip_run(const StripArgs<S>& A, int strip, int 
     }
   };
 
-  // prologue: rows y0-1 and y0, then load y0+1
-  {
-    C rdummy;
-    load_row(y0 == 0 ? ny - 1 : y0 - 1, P0, h1);
-    psi_row(P0, h1, Wm, Cm, Em, rdummy);
-    load_row(y0, P0, h1);
-    psi_row(P0, h1, Wz, Cz, Ez, rho0);
-    load_row(y0 + 1 == ny ? 0 : y0 + 1, P1, h1);
-  }
-
-  for (int y = y0; y < y1; ++y) {
-    const bool more = y + 2 <= y1;
-    if (more) {
-      const int y2 = y + 2 >= ny ? y + 2 - ny : y + 2;
-      load_row(y2, P2, h2);
-    }
+  // Output row y: Pcur holds its pulled populations, Pnext (with halo hnext)
+  // those of row y + 1, and row y + 2 is loaded into Pload while this row is
+  // computed.  The three buffers rotate through the unrolled loop below, so
+  // no populations are copied between registers.
+  auto row = [&](int y, C (&Pcur)[kQ], const C (&Pnext)[kQ], C hnext, C (&Pload)[kQ],
+                 C& hload) {
+    if (y + 2 <= y1) load_row(y + 2 >= ny ? y + 2 - ny : y + 2, Pload, hload);
     C Wp = 0, Cp = 0, Ep = 0, rho1;
-    psi_row(P1, h1, Wp, Cp, Ep, rho1);
+    psi_row(Pnext, hnext, Wp, Cp, Ep, rho1);
 
     C Fx = C(0), Fy = C(0);
     if constexpr (kNeedPsi) {
@@ -180,7 +178,7 @@ __device__ __forceinline__ void strip_run(const StripArgs<S>& A, int strip, int 
 
     const int idx = y * nx + c;
     if constexpr (MODE == kModeStep) {
-      collide<C, SCHEME>(P0, rho0, Fx, Fy, Cz, A.P);
+      collide<C, SCHEME>(Pcur, rho0, Fx, Fy, Cz, A.P);
       if (active) {
         if constexpr (S::kDev) {
           // the density plane absorbs the 16-bit rounding of the deviations,
@@ -188,40 +186,68 @@ __device__ __forceinline__ void strip_run(const StripArgs<S>& A, int strip, int 
           C resid = rho0;
 #pragma unroll
           for (int a = 0; a < kQ; ++a) {
-            const typename S::T d = S::from_c(P0[a] - w_of<C>(a) * rho0);
+            const typename S::T d = S::from_c(Pcur[a] - w_of<C>(a) * rho0);
             A.dst[a * A.plane + idx] = d;
             resid -= S::to_c(d);
           }
           A.rho_dst[idx] = float(resid);
         } else {
 #pragma unroll
-          for (int a = 0; a < kQ; ++a) A.dst[a * A.plane + idx] = S::from_c(P0[a]);
+          for (int a = 0; a < kQ; ++a) A.dst[a * A.plane + idx] = S::from_c(Pcur[a]);
         }
       }
     } else {
       if (active) {
-        const C jx = (P0[1] - P0[3]) + (P0[5] - P0[6]) + (P0[8] - P0[7]);
-        const C jy = (P0[2] - P0[4]) + (P0[5] + P0[6]) - (P0[7] + P0[8]);
+        const C jx = (Pcur[1] - Pcur[3]) + (Pcur[5] - Pcur[6]) + (Pcur[8] - Pcur[7]);
+        const C jy = (Pcur[2] - Pcur[4]) + (Pcur[5] + Pcur[6]) - (Pcur[7] + Pcur[8]);
         const double r = double(rho0);
         A.out_rho[idx] = r;
         A.out_vx[idx] = (double(jx) + 0.5 * double(Fx)) / r;
         A.out_vy[idx] = (double(jy) + 0.5 * double(Fy)) / r;
       }
     }
-
-    // rotate
     Wm = Wz; Cm = Cz; Em = Ez;
     Wz = Wp; Cz = Cp; Ez = Ep;
     rho0 = rho1;
-#pragma unroll
-    for (int a = 0; a < kQ; ++a) { P0[a] = P1[a]; P1[a] = P2[a]; }
-    h1 = h2;
+  };
+
+  C PA[kQ], PB[kQ], PC[kQ];
+  C hA = C(0), hB = C(0), hC = C(0);
+  // prologue: psi of rows y0 - 1 and y0, populations of y0 (PA) and y0 + 1 (PB)
+  {
+    C rdummy;
+    load_row(y0 == 0 ? ny - 1 : y0 - 1, PA, hA);
+    psi_row(PA, hA, Wm, Cm, Em, rdummy);
+    load_row(y0, PA, hA);
+    psi_row(PA, hA, Wz, Cz, Ez, rho0);
+    load_row(y0 + 1 == ny ? 0 : y0 + 1, PB, hB);
   }
+#if LBM_STRIP_UNROLL3
+  int y = y0;
+  for (; y + 3 <= y1; y += 3) {
+    row(y, PA, PB, hB, PC, hC);
+    row(y + 1, PB, PC, hC, PA, hA);
+    row(y + 2, PC, PA, hA, PB, hB);
+  }
+  if (y < y1) {
+    row(y, PA, PB, hB, PC, hC);
+    if (y + 1 < y1) row(y + 1, PB, PC, hC, PA, hA);
+  }
+#else
+  // rolled loop: the three population buffers are copied down once per row,
+  // which costs moves but keeps the register count (occupancy) lower
+  for (int y = y0; y < y1; ++y) {
+    row(y, PA, PB, hB, PC, hC);
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) { PA[a] = PB[a]; PB[a] = PC[a]; }
+    hB = hC;
+  }
+#endif
   if (__any_sync(FULL, bad) && lane == 0) atomicOr(A.status, kStatusDiverged);
 }
 
 template <class S, int SCHEME, int MODE>
-__global__ void __launch_bounds__(kStripThreads)
+__global__ void __launch_bounds__(kStripThreads, LBM_STRIP_MIN_BLOCKS)
 strip_kernel(const StripArgs<S> A) {
   const int lane = threadIdx.x & 31;
   const int gwarp = (blockIdx.x * kStripThreads + threadIdx.x) >> 5;
