@@ -167,6 +167,108 @@ lbm_status lbm_set_band_rows(lbm_ctx *ctx, int band_rows);
 lbm_status lbm_get_launch_geometry(lbm_ctx *ctx, int scheme, int *n_strips,
                                    int *band_rows, int *n_bands, int *grid);
 
+/* ---- batched parameter sweeps ------------------------------------------- */
+/*
+ * Many independent lattices (instances) with their own size, temperature,
+ * tau, sigma and forcing scheme, advanced together in FP32 until each one
+ * converges, diverges or reaches a step cap.  Each instance is the method of
+ * lbm_step (the same fused kernel body); the batch packs all populations in
+ * one buffer pair and runs windows of `window` steps as one CUDA graph:
+ * either one launch per step over a work list of all active instances'
+ * 32-column x band items, or one persistent launch per window in which each
+ * CTA owns whole instances and synchronises only its own threads between
+ * steps.  After every window an FP64 reduction per instance gives the
+ * coexistence densities of the flat interface (Eq. 36 slab: rho_g from rows
+ * 0 and ny-1, rho_l from rows ny/2-1 and ny/2), the interface width
+ * (rho_l - rho_g) / max_y |d rho_row / dy|, the mass, and the largest density
+ * change since the previous window.  An instance has converged when every
+ * cell changed by less than max(tol, 8 * 2^-23 * rho) over a window.
+ */
+
+typedef struct {
+  int nx, ny;        /* lattice of this instance, each >= 1                  */
+  double T_over_Tc;  /* reduced temperature, > 0                             */
+  double tau;        /* relaxation time, > 1/2                               */
+  double sigma;      /* improved-scheme constant (read by scheme 2 only)     */
+  int scheme;        /* LBM_SCHEME_*                                         */
+} lbm_instance;
+
+enum { LBM_BATCH_AUTO = 0, LBM_BATCH_WORKLIST = 1, LBM_BATCH_PERSISTENT = 2 };
+/* Convergence rules.  CELL: every cell changed by less than
+ * max(tol, 8 * 2^-23 * rho) over a window.  COEX: the coexistence densities
+ * rho_g and rho_l (FP64 row means) each changed by less than
+ * max(tol, 8 * 2^-23 * value) over two consecutive windows.  In FP32 the
+ * interface position of a relaxed slab jitters by ~1e-4 cells per window
+ * (rounding noise driving a nearly neutral mode), so CELL is met only by
+ * some runs; COEX tests what a sweep reports. */
+enum { LBM_CONV_COEX = 0, LBM_CONV_CELL = 1 };
+enum { LBM_RUN_ACTIVE = 0, LBM_RUN_CONVERGED = 1, LBM_RUN_DIVERGED = 2, LBM_RUN_CAPPED = 3 };
+
+typedef struct {
+  int tc_mode;          /* as in lbm_params                                    */
+  double a, b, R, G;    /* as in lbm_params                                    */
+  int device;
+  void *cuda_stream;    /* NULL: the batch creates and owns a stream          */
+  int window;           /* steps per convergence check, even, >= 2 (1000)      */
+  double tol;           /* density-change tolerance per window (1e-9)          */
+  int max_steps;        /* step cap per instance (200000)                      */
+  int mode;             /* LBM_BATCH_AUTO (window-level autotuning), _WORKLIST,
+                           _PERSISTENT                                         */
+  int rows_per_item;    /* band height of a work-list item; 0 = autotuned      */
+  int conv;             /* LBM_CONV_COEX (default) or LBM_CONV_CELL             */
+} lbm_batch_params;
+
+typedef struct {
+  int status;           /* LBM_RUN_*                                          */
+  int steps;            /* steps advanced                                     */
+  double rho_g, rho_l;  /* slab coexistence densities (FP64 row means)        */
+  double width;         /* interface width                                    */
+  double mass;          /* total mass (FP64)                                  */
+  double max_drho;      /* largest |rho(t) - rho(t - window)| of the last window */
+} lbm_result;
+
+typedef struct {
+  int windows;                 /* windows run so far                          */
+  unsigned long long launches; /* kernel launches queued                      */
+  double gpu_ms;               /* device time of all windows (CUDA events)    */
+  int mode;                    /* mode of the last window                      */
+  int rows_per_item;           /* work-list band height of the last window     */
+  int n_active;                /* instances still running                      */
+} lbm_batch_stats;
+
+typedef struct lbm_batch lbm_batch;
+
+void lbm_batch_default_params(lbm_batch_params *p);
+
+/* Allocate a batch of `count` instances.  LBM_E_INVAL for count < 1 or any
+ * instance with a bad size, temperature, tau or scheme. */
+lbm_status lbm_batch_create(const lbm_batch_params *p, const lbm_instance *inst,
+                            int count, lbm_batch **out);
+
+/* Instance i starts at rest from the host density rho (ny*nx doubles,
+ * copied); LBM_E_INVAL if it leaves the domain of psi. */
+lbm_status lbm_batch_init_density(lbm_batch *b, int i, const double *rho);
+
+/* Every instance starts at rest from the flat-interface profile of Eq. 36
+ * built on the device: rho_g + (rho_l - rho_g)/2 [tanh(2(y - ny/4)/W) -
+ * tanh(2(y - 3ny/4)/W)] with the per-instance rho_g[i], rho_l[i], W = width[i]
+ * (width[i] <= 0: a sharp step, liquid on rows [ny/4, 3ny/4)). */
+lbm_status lbm_batch_init_slabs(lbm_batch *b, const double *rho_g, const double *rho_l,
+                                const double *width);
+
+/* Run at most max_windows windows (or until no instance is active); the
+ * number still active is written to *n_active (may be NULL). */
+lbm_status lbm_batch_run(lbm_batch *b, int max_windows, int *n_active);
+
+lbm_status lbm_batch_get_result(const lbm_batch *b, int i, lbm_result *r);
+
+/* Density of instance i (FP64 host array of ny*nx). */
+lbm_status lbm_batch_get_density(lbm_batch *b, int i, double *rho);
+
+lbm_status lbm_batch_get_stats(const lbm_batch *b, lbm_batch_stats *s);
+const char *lbm_batch_last_error(const lbm_batch *b);
+lbm_status lbm_batch_destroy(lbm_batch *b);
+
 /* ---- allocation-free variant ------------------------------------------- */
 
 /* FP64 sum of n FP32 values in device memory (for an FP32 population buffer

@@ -1,0 +1,853 @@
+// Batched parameter sweeps: many independent FP32 lattices advanced together.
+//
+// Every instance runs the fused step body of the single-domain kernel
+// (strip_run in lbm_kernels.cuh) on its own slice of one packed buffer pair.
+// A window of `window` steps is one CUDA graph, in one of two launch modes:
+//   work list   -- one launch per step; warps take 32-column x band items of
+//                  all active instances from a prefix table (balanced for any
+//                  mix of sizes);
+//   persistent  -- one launch per window; each CTA owns whole instances
+//                  (longest-processing-time assignment) and only
+//                  __syncthreads() separates its steps, so no CTA ever waits
+//                  for another.  Small active sets then stay in L2.
+// Both give bit-identical results (the band height never changes a value),
+// so the window-level autotuner can try configurations on live windows.
+// After each window one CTA per active instance reduces, in FP64, the row
+// means (coexistence densities, width, mass) and the largest density change
+// since the previous window (convergence), and flags non-finite values.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <queue>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+struct BatchInst {
+  size_t off;              // element offset of plane 0 in each population buffer
+  size_t coff;             // cell offset in the density snapshot
+  int nx, ny, n_strips;
+  int band_rows, n_bands;  // work-list geometry
+  int pband_rows, pn_bands;  // persistent geometry
+  int scheme;
+  int row_off;             // offset in the row-mean scratch
+  Phys<float> P;
+};
+
+struct BatchOut {
+  float max_dev;  // max over cells of |drho| / max(tol, 8 eps rho)
+  float max_abs;  // max |drho|
+  double rho_g, rho_l, width, mass;
+  int finite;
+};
+
+constexpr int kWorklistThreads = 128;
+constexpr int kPersistentThreads = 256;
+constexpr int kReduceCta = 256;
+
+__device__ __forceinline__ StripArgs<StoreF32> inst_args(const BatchInst& I, const float* src,
+                                                        float* dst, unsigned* status,
+                                                        bool persistent) {
+  StripArgs<StoreF32> A;
+  A.src = src + I.off;
+  A.dst = dst + I.off;
+  A.rho_src = nullptr;
+  A.rho_dst = nullptr;
+  A.out_rho = A.out_vx = A.out_vy = nullptr;
+  A.status = status;
+  A.nx = I.nx;
+  A.ny = I.ny;
+  A.n_strips = I.n_strips;
+  A.band_rows = persistent ? I.pband_rows : I.band_rows;
+  A.n_bands = persistent ? I.pn_bands : I.n_bands;
+  A.plane = size_t(I.nx) * I.ny;
+  A.P = I.P;
+  return A;
+}
+
+template <bool kCoherent>
+__device__ __forceinline__ void run_item(const StripArgs<StoreF32>& A, int scheme, int strip,
+                                         int band, int lane) {
+  switch (scheme) {
+    case kSC: strip_run<StoreF32, kSC, kModeStep, kCoherent>(A, strip, band, lane); break;
+    case kEDM: strip_run<StoreF32, kEDM, kModeStep, kCoherent>(A, strip, band, lane); break;
+    case kImproved:
+      strip_run<StoreF32, kImproved, kModeStep, kCoherent>(A, strip, band, lane);
+      break;
+    case kNoForce: strip_run<StoreF32, kNoForce, kModeStep, kCoherent>(A, strip, band, lane); break;
+    case kEDMMod: strip_run<StoreF32, kEDMMod, kModeStep, kCoherent>(A, strip, band, lane); break;
+    case kLadd: strip_run<StoreF32, kLadd, kModeStep, kCoherent>(A, strip, band, lane); break;
+  }
+}
+
+// One step of every active instance; warp w takes items w, w + W, ...
+__global__ void __launch_bounds__(kWorklistThreads, 5)
+batch_worklist_kernel(const BatchInst* __restrict__ inst, const int* __restrict__ active,
+                      const int* __restrict__ prefix, const int* __restrict__ n_active_p,
+                      const float* src, float* dst, unsigned* inst_status) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * (kWorklistThreads / 32);
+  const int na = *n_active_p;
+  const int total = prefix[na];
+  for (int item = (blockIdx.x * kWorklistThreads + threadIdx.x) >> 5; item < total;
+       item += nwarps) {
+    int lo = 0, hi = na;  // prefix[lo] <= item < prefix[lo + 1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (prefix[mid] <= item) lo = mid; else hi = mid;
+    }
+    const int i = active[lo];
+    const BatchInst I = inst[i];
+    const int local = item - prefix[lo];
+    const StripArgs<StoreF32> A = inst_args(I, src, dst, inst_status + i, false);
+    run_item<false>(A, I.scheme, local % I.n_strips, local / I.n_strips, lane);
+  }
+}
+
+// `steps` steps of the instances this CTA owns; buffers alternate, starting
+// from buf0.  The loads bypass L1 because this kernel wrote them.
+__global__ void __launch_bounds__(kPersistentThreads, 2)
+batch_persistent_kernel(const BatchInst* __restrict__ inst, const int* __restrict__ cta_begin,
+                        const int* __restrict__ cta_list, int steps, float* buf0, float* buf1,
+                        unsigned* inst_status) {
+  const int k0 = cta_begin[blockIdx.x], k1 = cta_begin[blockIdx.x + 1];
+  if (k0 >= k1) return;  // block-uniform
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int kWarps = kPersistentThreads / 32;
+  for (int s = 0; s < steps; ++s) {
+    const float* src = (s & 1) ? buf1 : buf0;
+    float* dst = (s & 1) ? buf0 : buf1;
+    for (int k = k0; k < k1; ++k) {
+      const int i = cta_list[k];
+      const BatchInst I = inst[i];
+      const StripArgs<StoreF32> A = inst_args(I, src, dst, inst_status + i, true);
+      const int items = I.n_strips * I.pn_bands;
+      for (int item = warp; item < items; item += kWarps)
+        run_item<true>(A, I.scheme, item % I.n_strips, item / I.n_strips, lane);
+    }
+    __syncthreads();  // step s of every owned instance is complete
+  }
+}
+
+__device__ __forceinline__ float pulled_rho(const float* f, size_t plane, int nx, int ny, int x,
+                                            int y) {
+  const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+  const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+  float r = f[size_t(y) * nx + x];
+  r += f[plane + size_t(y) * nx + xm];
+  r += f[2 * plane + size_t(ym) * nx + x];
+  r += f[3 * plane + size_t(y) * nx + xp];
+  r += f[4 * plane + size_t(yp) * nx + x];
+  r += f[5 * plane + size_t(ym) * nx + xm];
+  r += f[6 * plane + size_t(ym) * nx + xp];
+  r += f[7 * plane + size_t(yp) * nx + xp];
+  r += f[8 * plane + size_t(yp) * nx + xm];
+  return r;
+}
+
+// One CTA per active instance: convergence against the snapshot, then the
+// FP64 row means, coexistence densities, width and mass.
+__global__ void __launch_bounds__(kReduceCta)
+batch_window_reduce(const BatchInst* __restrict__ inst, const int* __restrict__ active,
+                    const int* __restrict__ n_active_p, const float* cur, float* snap,
+                    double* rowmean, BatchOut* out, float tol) {
+  const int k = blockIdx.x;
+  if (k >= *n_active_p) return;
+  const int i = active[k];
+  const BatchInst I = inst[i];
+  __shared__ unsigned s_maxdev, s_maxabs;
+  __shared__ int s_finite;
+  if (threadIdx.x == 0) {
+    s_maxdev = 0u;
+    s_maxabs = 0u;
+    s_finite = 1;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const size_t plane = size_t(I.nx) * I.ny;
+  const float* f = cur + I.off;
+  float maxdev = 0.f, maxabs = 0.f;
+  bool finite = true;
+  for (int y = warp; y < I.ny; y += kReduceCta / 32) {
+    double rs = 0.0;
+    for (int x = lane; x < I.nx; x += 32) {
+      const float r = pulled_rho(f, plane, I.nx, I.ny, x, y);
+      float* sp = snap + I.coff + size_t(y) * I.nx + x;
+      const float d = fabsf(r - *sp);
+      const float thr = fmaxf(tol, 8.f * 1.1920929e-7f * fabsf(r));
+      maxdev = fmaxf(maxdev, d / thr);
+      maxabs = fmaxf(maxabs, d);
+      finite = finite && isfinite(r);
+      *sp = r;
+      rs += double(r);
+    }
+    for (int o = 16; o > 0; o >>= 1) rs += __shfl_down_sync(0xffffffffu, rs, o);
+    if (lane == 0) rowmean[I.row_off + y] = rs / I.nx;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    maxdev = fmaxf(maxdev, __shfl_down_sync(0xffffffffu, maxdev, o));
+    maxabs = fmaxf(maxabs, __shfl_down_sync(0xffffffffu, maxabs, o));
+  }
+  finite = __all_sync(0xffffffffu, finite);
+  if (lane == 0) {
+    atomicMax(&s_maxdev, __float_as_uint(maxdev));  // non-negative floats order as uints
+    atomicMax(&s_maxabs, __float_as_uint(maxabs));
+    if (!finite) s_finite = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double* rm = rowmean + I.row_off;
+    const int ny = I.ny;
+    const int lo = ny >= 2 ? ny / 2 - 1 : 0, hi = ny / 2;
+    const double rg = 0.5 * (rm[0] + rm[ny - 1]);
+    const double rl = 0.5 * (rm[lo] + rm[hi]);
+    double gmax = 0.0, mass = 0.0;
+    for (int y = 0; y < ny; ++y) {
+      const double g = 0.5 * fabs(rm[y + 1 < ny ? y + 1 : 0] - rm[y > 0 ? y - 1 : ny - 1]);
+      gmax = fmax(gmax, g);
+      mass += rm[y];
+    }
+    BatchOut o;
+    o.max_dev = __uint_as_float(s_maxdev);
+    o.max_abs = __uint_as_float(s_maxabs);
+    o.rho_g = rg;
+    o.rho_l = rl;
+    o.width = gmax > 0.0 ? (rl - rg) / gmax : 0.0;
+    o.mass = mass * I.nx;
+    o.finite = s_finite && isfinite(mass);
+    out[i] = o;
+  }
+}
+
+// Eq. 36 flat interface at rest for every instance (blockIdx.y = instance):
+// f_a(x) = w_a rho(y), stored so that the next pull reproduces it.
+__global__ void batch_init_slab_kernel(const BatchInst* __restrict__ inst,
+                                       const double* __restrict__ prof, float* buf0,
+                                       float* snap, unsigned* inst_status) {
+  const int i = blockIdx.y;
+  const BatchInst I = inst[i];
+  const double rg = prof[3 * i], rl = prof[3 * i + 1], W = prof[3 * i + 2];
+  const size_t plane = size_t(I.nx) * I.ny;
+  const int ny = I.ny;
+  auto rho_at = [&](int y) {
+    y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+    if (W > 0.0)
+      return rg + 0.5 * (rl - rg) *
+                      (tanh(2.0 * (y - ny / 4.0) / W) - tanh(2.0 * (y - 3.0 * ny / 4.0) / W));
+    return (y >= ny / 4 && y < 3 * ny / 4) ? rl : rg;
+  };
+  bool bad = false;
+  for (size_t c = blockIdx.x * size_t(blockDim.x) + threadIdx.x; c < plane;
+       c += size_t(gridDim.x) * blockDim.x) {
+    const int y = int(c / I.nx);
+#pragma unroll
+    for (int a = 0; a < kQ; ++a)
+      buf0[I.off + a * plane + c] = float(double(w_of<float>(a)) * rho_at(y + ey_of(a)));
+    const double r = rho_at(y);
+    snap[I.coff + c] = float(r);
+    (void)psi_of_rho(float(r), I.P, bad);
+  }
+  if (bad) atomicOr(inst_status + i, kStatusInvalidInit);
+}
+
+__global__ void batch_density_kernel(const BatchInst* __restrict__ inst, int i, const float* cur,
+                                     double* out) {
+  const BatchInst I = inst[i];
+  const size_t plane = size_t(I.nx) * I.ny;
+  for (size_t c = blockIdx.x * size_t(blockDim.x) + threadIdx.x; c < plane;
+       c += size_t(gridDim.x) * blockDim.x)
+    out[c] = double(pulled_rho(cur + I.off, plane, I.nx, I.ny, int(c % I.nx), int(c / I.nx)));
+}
+
+__global__ void to_float_kernel(const double* in, float* out, size_t n) {
+  for (size_t c = blockIdx.x * size_t(blockDim.x) + threadIdx.x; c < n;
+       c += size_t(gridDim.x) * blockDim.x)
+    out[c] = float(in[c]);
+}
+
+}  // namespace lbm
+
+using namespace lbm;
+
+struct lbm_batch {
+  lbm_batch_params p{};
+  int count = 0;
+  std::vector<lbm_instance> inst;
+  std::vector<BatchInst> desc;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  float* buf[2] = {nullptr, nullptr};
+  float* snap = nullptr;
+  double* rowmean = nullptr;
+  BatchInst* d_inst = nullptr;
+  BatchOut* d_out = nullptr;
+  unsigned* d_status = nullptr;  // per instance
+  double* d_prof = nullptr;      // 3 per instance
+  double* d_tmp = nullptr;       // staging for one instance's density
+  size_t tmp_cells = 0;
+  // device work tables and their pinned host staging
+  int* d_active = nullptr;
+  int* d_prefix = nullptr;
+  int* d_n_active = nullptr;
+  int* d_cta_begin = nullptr;
+  int* d_cta_list = nullptr;
+  int* h_active = nullptr;
+  int* h_prefix = nullptr;
+  int* h_cta_begin = nullptr;
+  int* h_cta_list = nullptr;
+  BatchOut* h_out = nullptr;
+  unsigned* h_status = nullptr;
+  std::vector<lbm_result> res;
+  std::vector<int> calm;  // consecutive windows meeting the COEX rule
+  std::vector<int> active;
+  int sm_count = 0;
+  int wl_grid = 0;
+  int pers_grid_max = 0;
+  int pers_grid = 0;
+  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};  // indexed by mode
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool initialized = false;
+  // current launch configuration and autotuner state
+  int cur_mode = LBM_BATCH_WORKLIST;
+  int cur_rows = 32;
+  std::vector<std::pair<int, int>> candidates;
+  std::vector<double> cand_cost;  // ns per cell update, <0 = not measured
+  size_t tuned_cells = 0;
+  bool tuned = false;
+  lbm_batch_stats stats{};
+  std::string err;
+};
+
+namespace {
+
+lbm_status bfail(lbm_batch* b, lbm_status st, const std::string& m) {
+  if (b) b->err = m;
+  return st;
+}
+
+#define LBM_BCUDA(b, call)                                                               \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return bfail(b, LBM_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+struct BDeviceGuard {
+  int prev = -1;
+  explicit BDeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~BDeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+void set_geometry(BatchInst& d, int rows) {
+  d.band_rows = std::max(1, std::min(rows, d.ny));
+  d.n_bands = (d.ny + d.band_rows - 1) / d.band_rows;
+  const int want = (kPersistentThreads / 32 + d.n_strips - 1) / d.n_strips;  // fill 8 warps
+  const int pb = std::max(1, std::min(want, d.ny));
+  d.pband_rows = (d.ny + pb - 1) / pb;
+  d.pn_bands = (d.ny + d.pband_rows - 1) / d.pband_rows;
+}
+
+// Rebuild the active list, the work-list prefix and the persistent
+// assignment (largest instance first onto the least-loaded CTA).
+lbm_status upload_tables(lbm_batch* b) {
+  const int na = int(b->active.size());
+  int acc = 0;
+  b->h_prefix[0] = 0;
+  for (int k = 0; k < na; ++k) {
+    const BatchInst& d = b->desc[b->active[k]];
+    b->h_active[k] = b->active[k];
+    acc += d.n_strips * d.n_bands;
+    b->h_prefix[k + 1] = acc;
+  }
+  b->h_prefix[b->count + 1] = na;  // n_active rides at the end of the prefix staging
+  const int G = std::max(1, std::min(na, b->pers_grid_max));
+  b->pers_grid = G;
+  std::vector<int> order(b->active);
+  std::sort(order.begin(), order.end(), [&](int x, int y) {
+    const size_t cx = size_t(b->desc[x].nx) * b->desc[x].ny;
+    const size_t cy = size_t(b->desc[y].nx) * b->desc[y].ny;
+    return cx != cy ? cx > cy : x < y;
+  });
+  using Load = std::pair<size_t, int>;
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+  for (int c = 0; c < G; ++c) heap.push({0, c});
+  std::vector<std::vector<int>> lists(G);
+  for (int i : order) {
+    Load l = heap.top();
+    heap.pop();
+    lists[l.second].push_back(i);
+    heap.push({l.first + size_t(b->desc[i].nx) * b->desc[i].ny, l.second});
+  }
+  int pos = 0;
+  for (int c = 0; c <= b->pers_grid_max; ++c) {
+    b->h_cta_begin[c] = pos;
+    if (c < G)
+      for (int i : lists[c]) b->h_cta_list[pos++] = i;
+  }
+  LBM_BCUDA(b, cudaMemcpyAsync(b->d_inst, b->desc.data(), b->count * sizeof(BatchInst),
+                               cudaMemcpyHostToDevice, b->stream));
+  LBM_BCUDA(b, cudaMemcpyAsync(b->d_active, b->h_active, std::max(na, 1) * sizeof(int),
+                               cudaMemcpyHostToDevice, b->stream));
+  LBM_BCUDA(b, cudaMemcpyAsync(b->d_prefix, b->h_prefix, (na + 1) * sizeof(int),
+                               cudaMemcpyHostToDevice, b->stream));
+  LBM_BCUDA(b, cudaMemcpyAsync(b->d_n_active, b->h_prefix + b->count + 1, sizeof(int),
+                               cudaMemcpyHostToDevice, b->stream));
+  LBM_BCUDA(b, cudaMemcpyAsync(b->d_cta_begin, b->h_cta_begin,
+                               (b->pers_grid_max + 1) * sizeof(int), cudaMemcpyHostToDevice,
+                               b->stream));
+  LBM_BCUDA(b, cudaMemcpyAsync(b->d_cta_list, b->h_cta_list, std::max(pos, 1) * sizeof(int),
+                               cudaMemcpyHostToDevice, b->stream));
+  return LBM_OK;
+}
+
+// One window as a CUDA graph (captured once per mode; the kernels read the
+// active set and geometry from device memory, so the graph stays valid).
+lbm_status window_graph(lbm_batch* b, int mode, cudaGraphExec_t* out) {
+  if (b->graph[mode]) {
+    *out = b->graph[mode];
+    return LBM_OK;
+  }
+  cudaGraph_t g = nullptr;
+  LBM_BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  const int W = b->p.window;
+  if (mode == LBM_BATCH_WORKLIST) {
+    for (int s = 0; s < W; ++s)
+      batch_worklist_kernel<<<b->wl_grid, kWorklistThreads, 0, b->stream>>>(
+          b->d_inst, b->d_active, b->d_prefix, b->d_n_active, b->buf[s & 1],
+          b->buf[(s + 1) & 1], b->d_status);
+  } else {
+    batch_persistent_kernel<<<b->pers_grid_max, kPersistentThreads, 0, b->stream>>>(
+        b->d_inst, b->d_cta_begin, b->d_cta_list, W, b->buf[0], b->buf[1], b->d_status);
+  }
+  batch_window_reduce<<<b->count, kReduceCta, 0, b->stream>>>(
+      b->d_inst, b->d_active, b->d_n_active, b->buf[0], b->snap, b->rowmean, b->d_out,
+      float(b->p.tol));
+  cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+  if (e != cudaSuccess) return bfail(b, LBM_E_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&b->graph[mode], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess)
+    return bfail(b, LBM_E_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+  *out = b->graph[mode];
+  return LBM_OK;
+}
+
+size_t active_cells(const lbm_batch* b) {
+  size_t c = 0;
+  for (int i : b->active) c += size_t(b->desc[i].nx) * b->desc[i].ny;
+  return c;
+}
+
+size_t max_active_cells(const lbm_batch* b) {
+  size_t m = 0;
+  for (int i : b->active) m = std::max(m, size_t(b->desc[i].nx) * b->desc[i].ny);
+  return m;
+}
+
+// Window-level autotuner: measure each candidate (mode, rows) on one live
+// window, keep the cheapest per cell update, and tune again once the active
+// work has halved.
+void choose_config(lbm_batch* b, int& mode, int& rows) {
+  if (b->p.mode != LBM_BATCH_AUTO) {
+    mode = b->p.mode;
+    rows = b->p.rows_per_item > 0 ? b->p.rows_per_item : 32;
+    return;
+  }
+  const size_t cells = active_cells(b);
+  if (b->tuned && cells * 2 < b->tuned_cells) {
+    b->tuned = false;
+    std::fill(b->cand_cost.begin(), b->cand_cost.end(), -1.0);
+  }
+  if (!b->tuned) {
+    for (size_t k = 0; k < b->candidates.size(); ++k) {
+      if (b->cand_cost[k] >= 0) continue;
+      const auto& c = b->candidates[k];
+      if (b->p.rows_per_item > 0 && c.first == LBM_BATCH_WORKLIST && c.second != b->p.rows_per_item)
+        continue;
+      // a persistent window puts each instance on one SM: only worth trying
+      // when the active populations are within a few times the L2 size and
+      // no single instance is large
+      if (c.first == LBM_BATCH_PERSISTENT &&
+          (cells * 72 > size_t(512) << 20 || max_active_cells(b) > 65536))
+        continue;
+      mode = c.first;
+      rows = c.second;
+      return;
+    }
+    double best = 1e300;
+    int bk = 0;
+    for (size_t k = 0; k < b->candidates.size(); ++k)
+      if (b->cand_cost[k] >= 0 && b->cand_cost[k] < best) {
+        best = b->cand_cost[k];
+        bk = int(k);
+      }
+    b->cur_mode = b->candidates[bk].first;
+    b->cur_rows = b->candidates[bk].second;
+    b->tuned = true;
+    b->tuned_cells = cells;
+  }
+  mode = b->cur_mode;
+  rows = b->cur_rows;
+}
+
+void record_cost(lbm_batch* b, int mode, int rows, double ms, size_t cells) {
+  for (size_t k = 0; k < b->candidates.size(); ++k)
+    if (b->candidates[k].first == mode &&
+        (mode == LBM_BATCH_PERSISTENT || b->candidates[k].second == rows) &&
+        b->cand_cost[k] < 0)
+      b->cand_cost[k] = ms * 1e6 / (double(cells) * b->p.window);
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_batch_default_params(lbm_batch_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->a = 1.0;
+  p->b = 4.0;
+  p->R = 1.0;
+  p->G = -1.0;
+  p->window = 1000;
+  p->tol = 1e-9;
+  p->max_steps = 200000;
+  p->mode = LBM_BATCH_AUTO;
+}
+
+lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, int count,
+                            lbm_batch** out) {
+  if (!p || !in || !out || count < 1) return LBM_E_INVAL;
+  *out = nullptr;
+  if (p->window < 2 || p->window % 2 || p->max_steps < 1 || !(p->tol >= 0) ||
+      p->mode < LBM_BATCH_AUTO || p->mode > LBM_BATCH_PERSISTENT || p->rows_per_item < 0 ||
+      p->conv < LBM_CONV_COEX || p->conv > LBM_CONV_CELL ||
+      !(p->G < 0) || !(p->a > 0) || !(p->b > 0) || !(p->R > 0) || p->tc_mode < 0 ||
+      p->tc_mode > 1)
+    return LBM_E_INVAL;
+  double Tc = 0.094, rc, pc;
+  if (p->tc_mode == 0 && lbm_cs_critical_point(p->a, p->b, p->R, &rc, &Tc, &pc) != LBM_OK)
+    return LBM_E_INVAL;
+  for (int i = 0; i < count; ++i) {
+    const lbm_instance& s = in[i];
+    if (s.nx < 1 || s.ny < 1 || (long long)s.nx * s.ny > (1LL << 28) || !(s.T_over_Tc > 0) ||
+        !(s.tau > 0.5) || !std::isfinite(s.tau) || !std::isfinite(s.sigma) || s.scheme < 0 ||
+        s.scheme > LBM_SCHEME_LADD)
+      return LBM_E_INVAL;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || p->device < 0 || p->device >= ndev)
+    return LBM_E_CUDA;
+  BDeviceGuard guard(p->device);
+  lbm_batch* b = new lbm_batch();
+  b->p = *p;
+  b->count = count;
+  b->inst.assign(in, in + count);
+  b->desc.resize(count);
+  size_t off = 0, coff = 0;
+  int roff = 0, max_cells = 0;
+  for (int i = 0; i < count; ++i) {
+    BatchInst& d = b->desc[i];
+    const lbm_instance& s = in[i];
+    d.off = off;
+    d.coff = coff;
+    d.nx = s.nx;
+    d.ny = s.ny;
+    d.n_strips = (s.nx + 31) / 32;
+    d.scheme = s.scheme;
+    d.row_off = roff;
+    const double T = s.T_over_Tc * Tc;
+    d.P.RT = float(p->R * T);
+    d.P.a = float(p->a);
+    d.P.b4 = float(p->b / 4.0);
+    d.P.two_over_G = float(2.0 / p->G);
+    d.P.minus_G = float(-p->G);
+    d.P.tau = float(s.tau);
+    d.P.omega = float(1.0 / s.tau);
+    d.P.sigma_ups = float(s.sigma / (s.tau - 0.5));
+    d.P.guo = float(1.0 - 1.0 / (2.0 * s.tau));
+    set_geometry(d, 32);
+    const size_t cells = size_t(s.nx) * s.ny;
+    off += (9 * cells + 31) / 32 * 32;
+    coff += cells;
+    roff += s.ny;
+    max_cells = std::max<int>(max_cells, int(cells));
+  }
+  b->tmp_cells = max_cells;
+  b->res.assign(count, lbm_result{});
+  b->calm.assign(count, 0);
+  auto bail = [&](lbm_status st, const char* m) {
+    lbm_batch_destroy(b);
+    (void)m;
+    return st;
+  };
+  if (cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, p->device) !=
+      cudaSuccess)
+    return bail(LBM_E_CUDA, "attribute");
+  if (p->cuda_stream) {
+    b->stream = static_cast<cudaStream_t>(p->cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(LBM_E_CUDA, "stream");
+    b->own_stream = true;
+  }
+  int occ_wl = 0, occ_p = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_wl, batch_worklist_kernel,
+                                                    kWorklistThreads, 0) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, batch_persistent_kernel,
+                                                    kPersistentThreads, 0) != cudaSuccess)
+    return bail(LBM_E_CUDA, "occupancy");
+  b->wl_grid = std::max(1, occ_wl) * b->sm_count;
+  b->pers_grid_max = std::max(1, std::max(1, occ_p) * b->sm_count);
+  bool ok = true;
+  ok &= cudaMalloc(&b->buf[0], off * sizeof(float)) == cudaSuccess;
+  ok &= cudaMalloc(&b->buf[1], off * sizeof(float)) == cudaSuccess;
+  ok &= cudaMalloc(&b->snap, coff * sizeof(float)) == cudaSuccess;
+  ok &= cudaMalloc(&b->rowmean, roff * sizeof(double)) == cudaSuccess;
+  ok &= cudaMalloc(&b->d_inst, count * sizeof(BatchInst)) == cudaSuccess;
+  ok &= cudaMalloc(&b->d_out, count * sizeof(BatchOut)) == cudaSuccess;
+  ok &= cudaMalloc(&b->d_status, count * sizeof(unsigned)) == cudaSuccess;
+  ok &= cudaMalloc(&b->d_prof, 3 * count * sizeof(double)) == cudaSuccess;
+  ok &= cudaMalloc(&b->d_tmp, b->tmp_cells * sizeof(double)) == cudaSuccess;
+  ok &= cudaMalloc(&b->d_active, count * sizeof(int)) == cudaSuccess;
+  ok &= cudaMalloc(&b->d_prefix, (count + 1) * sizeof(int)) == cudaSuccess;
+  ok &= cudaMalloc(&b->d_n_active, sizeof(int)) == cudaSuccess;
+  ok &= cudaMalloc(&b->d_cta_begin, (b->pers_grid_max + 1) * sizeof(int)) == cudaSuccess;
+  ok &= cudaMalloc(&b->d_cta_list, count * sizeof(int)) == cudaSuccess;
+  if (!ok) return bail(LBM_E_NOMEM, "cudaMalloc");
+  ok &= cudaMallocHost(&b->h_active, count * sizeof(int)) == cudaSuccess;
+  ok &= cudaMallocHost(&b->h_prefix, (count + 2) * sizeof(int)) == cudaSuccess;
+  ok &= cudaMallocHost(&b->h_cta_begin, (b->pers_grid_max + 1) * sizeof(int)) == cudaSuccess;
+  ok &= cudaMallocHost(&b->h_cta_list, count * sizeof(int)) == cudaSuccess;
+  ok &= cudaMallocHost(&b->h_out, count * sizeof(BatchOut)) == cudaSuccess;
+  ok &= cudaMallocHost(&b->h_status, count * sizeof(unsigned)) == cudaSuccess;
+  if (!ok) return bail(LBM_E_NOMEM, "cudaMallocHost");
+  if (cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess)
+    return bail(LBM_E_CUDA, "event");
+  if (cudaMemsetAsync(b->d_status, 0, count * sizeof(unsigned), b->stream) != cudaSuccess ||
+      cudaMemsetAsync(b->buf[0], 0, off * sizeof(float), b->stream) != cudaSuccess ||
+      cudaMemsetAsync(b->buf[1], 0, off * sizeof(float), b->stream) != cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess)
+    return bail(LBM_E_CUDA, "memset");
+  for (int rows : {8, 16, 32, 64, 128}) b->candidates.push_back({LBM_BATCH_WORKLIST, rows});
+  b->candidates.push_back({LBM_BATCH_PERSISTENT, 0});
+  b->cand_cost.assign(b->candidates.size(), -1.0);
+  for (int i = 0; i < count; ++i) b->active.push_back(i);
+  b->stats.n_active = count;
+  *out = b;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_destroy(lbm_batch* b) {
+  if (!b) return LBM_OK;
+  BDeviceGuard guard(b->p.device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (auto& g : b->graph)
+    if (g) cudaGraphExecDestroy(g);
+  cudaFree(b->buf[0]);
+  cudaFree(b->buf[1]);
+  cudaFree(b->snap);
+  cudaFree(b->rowmean);
+  cudaFree(b->d_inst);
+  cudaFree(b->d_out);
+  cudaFree(b->d_status);
+  cudaFree(b->d_prof);
+  cudaFree(b->d_tmp);
+  cudaFree(b->d_active);
+  cudaFree(b->d_prefix);
+  cudaFree(b->d_n_active);
+  cudaFree(b->d_cta_begin);
+  cudaFree(b->d_cta_list);
+  if (b->h_active) cudaFreeHost(b->h_active);
+  if (b->h_prefix) cudaFreeHost(b->h_prefix);
+  if (b->h_cta_begin) cudaFreeHost(b->h_cta_begin);
+  if (b->h_cta_list) cudaFreeHost(b->h_cta_list);
+  if (b->h_out) cudaFreeHost(b->h_out);
+  if (b->h_status) cudaFreeHost(b->h_status);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return LBM_OK;
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str() : ""; }
+
+lbm_status lbm_batch_init_density(lbm_batch* b, int i, const double* rho) {
+  if (!b || !rho || i < 0 || i >= b->count) return bfail(b, LBM_E_INVAL, "bad argument");
+  BDeviceGuard guard(b->p.device);
+  const BatchInst& d = b->desc[i];
+  const size_t cells = size_t(d.nx) * d.ny;
+  LBM_BCUDA(b, cudaMemcpyAsync(b->d_tmp, rho, cells * sizeof(double), cudaMemcpyHostToDevice,
+                               b->stream));
+  LBM_BCUDA(b, cudaMemsetAsync(b->d_status + i, 0, sizeof(unsigned), b->stream));
+  EosCheck chk{};
+  chk.RT = double(d.P.RT);
+  chk.a = double(d.P.a);
+  chk.b4 = double(d.P.b4);
+  chk.two_over_G = double(d.P.two_over_G);
+  chk.status = b->d_status + i;
+  LBM_BCUDA(b, set_state_launch(kFP32, b->buf[0] + d.off, nullptr, d.nx, d.ny, cells, b->d_tmp,
+                                nullptr, nullptr, nullptr, chk, b->stream));
+  to_float_kernel<<<256, 256, 0, b->stream>>>(b->d_tmp, b->snap + d.coff, cells);
+  LBM_BCUDA(b, cudaGetLastError());
+  count_launches(2);
+  b->stats.launches += 2;
+  LBM_BCUDA(b, cudaMemcpyAsync(b->h_status + i, b->d_status + i, sizeof(unsigned),
+                               cudaMemcpyDeviceToHost, b->stream));
+  LBM_BCUDA(b, cudaStreamSynchronize(b->stream));
+  if (b->h_status[i] & kStatusInvalidInitFlag) {
+    cudaMemsetAsync(b->d_status + i, 0, sizeof(unsigned), b->stream);
+    cudaStreamSynchronize(b->stream);
+    return bfail(b, LBM_E_INVAL, "rho of instance " + std::to_string(i) +
+                                     " outside the domain of psi");
+  }
+  b->initialized = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_init_slabs(lbm_batch* b, const double* rho_g, const double* rho_l,
+                                const double* width) {
+  if (!b || !rho_g || !rho_l || !width) return bfail(b, LBM_E_INVAL, "null argument");
+  BDeviceGuard guard(b->p.device);
+  std::vector<double> prof(3 * b->count);
+  for (int i = 0; i < b->count; ++i) {
+    prof[3 * i] = rho_g[i];
+    prof[3 * i + 1] = rho_l[i];
+    prof[3 * i + 2] = width[i];
+  }
+  LBM_BCUDA(b, cudaMemcpyAsync(b->d_prof, prof.data(), prof.size() * sizeof(double),
+                               cudaMemcpyHostToDevice, b->stream));
+  LBM_BCUDA(b, cudaMemcpyAsync(b->d_inst, b->desc.data(), b->count * sizeof(BatchInst),
+                               cudaMemcpyHostToDevice, b->stream));
+  LBM_BCUDA(b, cudaMemsetAsync(b->d_status, 0, b->count * sizeof(unsigned), b->stream));
+  dim3 grid(64, b->count);
+  batch_init_slab_kernel<<<grid, 256, 0, b->stream>>>(b->d_inst, b->d_prof, b->buf[0], b->snap,
+                                                       b->d_status);
+  LBM_BCUDA(b, cudaGetLastError());
+  count_launches(1);
+  b->stats.launches += 1;
+  LBM_BCUDA(b, cudaMemcpyAsync(b->h_status, b->d_status, b->count * sizeof(unsigned),
+                               cudaMemcpyDeviceToHost, b->stream));
+  LBM_BCUDA(b, cudaStreamSynchronize(b->stream));  // prof is a local vector
+  for (int i = 0; i < b->count; ++i)
+    if (b->h_status[i] & kStatusInvalidInitFlag) {
+      cudaMemsetAsync(b->d_status, 0, b->count * sizeof(unsigned), b->stream);
+      cudaStreamSynchronize(b->stream);
+      return bfail(b, LBM_E_INVAL, "slab of instance " + std::to_string(i) +
+                                       " outside the domain of psi");
+    }
+  b->initialized = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_run(lbm_batch* b, int max_windows, int* n_active) {
+  if (!b || max_windows < 0) return bfail(b, LBM_E_INVAL, "bad argument");
+  if (!b->initialized) return bfail(b, LBM_E_STATE, "batch not initialised");
+  BDeviceGuard guard(b->p.device);
+  for (int w = 0; w < max_windows && !b->active.empty(); ++w) {
+    int mode = LBM_BATCH_WORKLIST, rows = 32;
+    choose_config(b, mode, rows);
+    for (auto& d : b->desc) set_geometry(d, rows);
+    lbm_status st = upload_tables(b);
+    if (st != LBM_OK) return st;
+    cudaGraphExec_t g = nullptr;
+    st = window_graph(b, mode, &g);
+    if (st != LBM_OK) return st;
+    const size_t cells = active_cells(b);
+    LBM_BCUDA(b, cudaEventRecord(b->ev0, b->stream));
+    LBM_BCUDA(b, cudaGraphLaunch(g, b->stream));
+    LBM_BCUDA(b, cudaEventRecord(b->ev1, b->stream));
+    const unsigned long long nl = mode == LBM_BATCH_WORKLIST ? b->p.window + 1 : 2;
+    count_launches(nl);
+    b->stats.launches += nl;
+    LBM_BCUDA(b, cudaMemcpyAsync(b->h_out, b->d_out, b->count * sizeof(BatchOut),
+                                 cudaMemcpyDeviceToHost, b->stream));
+    LBM_BCUDA(b, cudaMemcpyAsync(b->h_status, b->d_status, b->count * sizeof(unsigned),
+                                 cudaMemcpyDeviceToHost, b->stream));
+    LBM_BCUDA(b, cudaStreamSynchronize(b->stream));
+    float ms = 0.f;
+    LBM_BCUDA(b, cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+    b->stats.gpu_ms += ms;
+    b->stats.windows += 1;
+    b->stats.mode = mode;
+    b->stats.rows_per_item = rows;
+    if (b->p.mode == LBM_BATCH_AUTO && !b->tuned) record_cost(b, mode, rows, ms, cells);
+    std::vector<int> still;
+    const double floor32 = 8.0 * 1.1920928955078125e-7;
+    for (int i : b->active) {
+      lbm_result& r = b->res[i];
+      const BatchOut& o = b->h_out[i];
+      const bool first = r.steps == 0;
+      const bool coex_calm =
+          !first && std::fabs(o.rho_g - r.rho_g) < std::max(b->p.tol, floor32 * std::fabs(o.rho_g)) &&
+          std::fabs(o.rho_l - r.rho_l) < std::max(b->p.tol, floor32 * std::fabs(o.rho_l));
+      b->calm[i] = coex_calm ? b->calm[i] + 1 : 0;
+      r.steps += b->p.window;
+      r.rho_g = o.rho_g;
+      r.rho_l = o.rho_l;
+      r.width = o.width;
+      r.mass = o.mass;
+      r.max_drho = o.max_abs;
+      const bool converged =
+          b->p.conv == LBM_CONV_CELL ? o.max_dev < 1.0f : b->calm[i] >= 2;
+      if ((b->h_status[i] & kStatusDivergedFlag) || !o.finite) {
+        r.status = LBM_RUN_DIVERGED;
+      } else if (converged) {
+        r.status = LBM_RUN_CONVERGED;
+      } else if (r.steps >= b->p.max_steps) {
+        r.status = LBM_RUN_CAPPED;
+      } else {
+        r.status = LBM_RUN_ACTIVE;
+        still.push_back(i);
+      }
+    }
+    b->active.swap(still);
+    b->stats.n_active = int(b->active.size());
+  }
+  if (n_active) *n_active = int(b->active.size());
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_get_result(const lbm_batch* b, int i, lbm_result* r) {
+  if (!b || !r || i < 0 || i >= b->count) return LBM_E_INVAL;
+  *r = b->res[i];
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_get_density(lbm_batch* b, int i, double* rho) {
+  if (!b || !rho || i < 0 || i >= b->count) return bfail(b, LBM_E_INVAL, "bad argument");
+  if (!b->initialized) return bfail(b, LBM_E_STATE, "batch not initialised");
+  BDeviceGuard guard(b->p.device);
+  const size_t cells = size_t(b->desc[i].nx) * b->desc[i].ny;
+  LBM_BCUDA(b, cudaMemcpyAsync(b->d_inst, b->desc.data(), b->count * sizeof(BatchInst),
+                               cudaMemcpyHostToDevice, b->stream));
+  batch_density_kernel<<<128, 256, 0, b->stream>>>(b->d_inst, i, b->buf[0], b->d_tmp);
+  LBM_BCUDA(b, cudaGetLastError());
+  count_launches(1);
+  LBM_BCUDA(b, cudaMemcpyAsync(rho, b->d_tmp, cells * sizeof(double), cudaMemcpyDeviceToHost,
+                               b->stream));
+  LBM_BCUDA(b, cudaStreamSynchronize(b->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_get_stats(const lbm_batch* b, lbm_batch_stats* s) {
+  if (!b || !s) return LBM_E_INVAL;
+  *s = b->stats;
+  return LBM_OK;
+}
+
+}  // extern "C"

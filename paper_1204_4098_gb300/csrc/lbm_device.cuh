@@ -114,36 +114,42 @@ enum Scheme { kSC = 0, kEDM = 1, kImproved = 2, kNoForce = 3, kEDMMod = 4, kLadd
 //   EDM, C_e = 1/tau: u_eq = u, B_e = 1, C_e = 1/tau, V = v
 //   Ladd:            u_eq = u, B_e = C_e = 1, V = u
 //   no force:        u_eq = u, no forcing term
+//
+// Every operation is explicitly rounded (no compiler contraction), so all
+// kernels that inline this body -- single domain, batch work list, batch
+// persistent -- produce bit-identical populations.
 template <class C, int SCHEME>
 __device__ __forceinline__ void collide(C (&f)[kQ], C rho, C Fx, C Fy, C psi,
                                         const Phys<C>& P) {
-  const C jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-  const C jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+  const C jx = add_rn(add_rn(sub_rn(f[1], f[3]), sub_rn(f[5], f[6])), sub_rn(f[8], f[7]));
+  const C jy = sub_rn(add_rn(sub_rn(f[2], f[4]), add_rn(f[5], f[6])), add_rn(f[7], f[8]));
   const C inv_rho = fast_div(C(1), rho);
-  const C ux = jx * inv_rho, uy = jy * inv_rho;
+  const C ux = mul_rn(jx, inv_rho), uy = mul_rn(jy, inv_rho);
+  const C half_inv = mul_rn(C(0.5), inv_rho);
 
   C qx = ux, qy = uy;  // velocity in f_eq
   C Vx = C(0), Vy = C(0), Be = C(0), Ce = C(0);
   constexpr bool kForcing = SCHEME != kSC && SCHEME != kNoForce;
   if constexpr (SCHEME == kSC) {
-    qx = ux + P.tau * Fx * inv_rho;
-    qy = uy + P.tau * Fy * inv_rho;
+    const C t = mul_rn(P.tau, inv_rho);
+    qx = fma_rn(t, Fx, ux);
+    qy = fma_rn(t, Fy, uy);
   } else if constexpr (SCHEME == kEDM) {
-    Vx = ux + C(0.5) * Fx * inv_rho;
-    Vy = uy + C(0.5) * Fy * inv_rho;
+    Vx = fma_rn(half_inv, Fx, ux);
+    Vy = fma_rn(half_inv, Fy, uy);
     Be = C(1);
     Ce = C(1);
   } else if constexpr (SCHEME == kImproved) {
-    qx = ux + C(0.5) * Fx * inv_rho;
-    qy = uy + C(0.5) * Fy * inv_rho;
-    const C s = fast_div(P.sigma_ups, psi * psi);
-    Vx = qx + s * Fx;
-    Vy = qy + s * Fy;
+    qx = fma_rn(half_inv, Fx, ux);
+    qy = fma_rn(half_inv, Fy, uy);
+    const C s = fast_div(P.sigma_ups, mul_rn(psi, psi));
+    Vx = fma_rn(s, Fx, qx);
+    Vy = fma_rn(s, Fy, qy);
     Be = P.guo;
     Ce = P.guo;
   } else if constexpr (SCHEME == kEDMMod) {
-    Vx = ux + C(0.5) * Fx * inv_rho;
-    Vy = uy + C(0.5) * Fy * inv_rho;
+    Vx = fma_rn(half_inv, Fx, ux);
+    Vy = fma_rn(half_inv, Fy, uy);
     Be = C(1);
     Ce = P.omega;
   } else if constexpr (SCHEME == kLadd) {
@@ -154,38 +160,38 @@ __device__ __forceinline__ void collide(C (&f)[kQ], C rho, C Fx, C Fy, C psi,
   }
 
   const C om = P.omega;
-  const C one_m_om = C(1) - om;
+  const C one_m_om = sub_rn(C(1), om);
   // f_eq_a = w rho (1 - 1.5 q.q + 3 e.q + 4.5 (e.q)^2), F_a as above.  For an
   // opposite pair (a, b), e_b = -e_a: the terms even in e are shared and the
   // odd ones change sign, so each pair is evaluated once.
-  const C base = C(1) - C(1.5) * (qx * qx + qy * qy);
-  const C om_rho = om * rho;
-  const C VF3 = C(3) * (Vx * Fx + Vy * Fy);
+  const C base = fma_rn(C(-1.5), fma_rn(qx, qx, mul_rn(qy, qy)), C(1));
+  const C om_rho = mul_rn(om, rho);
+  const C VF3 = mul_rn(C(3), fma_rn(Vx, Fx, mul_rn(Vy, Fy)));
   auto pair = [&](int a, int b, C w, C eq, C eF, C eV) {
-    const C wr = w * om_rho;
-    C even = wr * (base + C(4.5) * eq * eq);
-    C odd = (C(3) * wr) * eq;
+    const C wr = mul_rn(w, om_rho);
+    C even = mul_rn(wr, fma_rn(mul_rn(C(4.5), eq), eq, base));
+    C odd = mul_rn(mul_rn(C(3), wr), eq);
     if constexpr (kForcing) {
-      even += (w * Ce) * (C(9) * eV * eF - VF3);
-      odd += (C(3) * w * Be) * eF;
+      even = fma_rn(mul_rn(w, Ce), fma_rn(mul_rn(C(9), eV), eF, -VF3), even);
+      odd = fma_rn(mul_rn(mul_rn(C(3), w), Be), eF, odd);
     }
-    const C fa = one_m_om * f[a] + even;
-    const C fb = one_m_om * f[b] + even;
-    f[a] = fa + odd;
-    f[b] = fb - odd;
+    const C fa = fma_rn(one_m_om, f[a], even);
+    const C fb = fma_rn(one_m_om, f[b], even);
+    f[a] = add_rn(fa, odd);
+    f[b] = sub_rn(fb, odd);
   };
   const C w1 = w_of<C>(1), w2 = w_of<C>(5);
   pair(1, 3, w1, qx, Fx, Vx);
   pair(2, 4, w1, qy, Fy, Vy);
-  pair(5, 7, w2, qx + qy, Fx + Fy, Vx + Vy);   // e5 = (1,1), e7 = (-1,-1)
-  pair(6, 8, w2, qy - qx, Fy - Fx, Vy - Vx);   // e6 = (-1,1), e8 = (1,-1)
+  pair(5, 7, w2, add_rn(qx, qy), add_rn(Fx, Fy), add_rn(Vx, Vy));  // e5 = (1,1), e7 = (-1,-1)
+  pair(6, 8, w2, sub_rn(qy, qx), sub_rn(Fy, Fx), sub_rn(Vy, Vx));  // e6 = (-1,1), e8 = (1,-1)
   // Every scheme conserves mass (sum_a F_a = 0, sum_a f_eq = rho); taking the
   // rest population as the remainder makes that hold to one rounding instead
   // of nine, so FP32 runs do not drift in mass.
   C rest = f[1];
 #pragma unroll
-  for (int a = 2; a < kQ; ++a) rest += f[a];
-  f[0] = rho - rest;
+  for (int a = 2; a < kQ; ++a) rest = add_rn(rest, f[a]);
+  f[0] = sub_rn(rho, rest);
 }
 
 // ---------------------------------------------------------------------------

@@ -66,10 +66,10 @@ __device__ __forceinline__ typename S::C pull_one(const StripArgs<S>& A, int a, 
   C v;
   if constexpr (kCoherent) {
     v = S::to_c(__ldcg(A.src + a * A.plane + idx));
-    if constexpr (S::kDev) v += w_of<C>(a) * C(__ldcg(A.rho_src + idx));
+    if constexpr (S::kDev) v = fma_rn(w_of<C>(a), C(__ldcg(A.rho_src + idx)), v);
   } else {
     v = S::to_c(__ldg(A.src + a * A.plane + idx));
-    if constexpr (S::kDev) v += w_of<C>(a) * C(__ldg(A.rho_src + idx));
+    if constexpr (S::kDev) v = fma_rn(w_of<C>(a), C(__ldg(A.rho_src + idx)), v);
   }
   return v;
 }
@@ -170,10 +170,13 @@ __device__ __forceinline__ void strip_run(const StripArgs<S>& A, int strip, int 
     if constexpr (kNeedPsi) {
       // Eq. 3: F = -G psi(x) sum_a w(|e_a|^2) psi(x + e_a) e_a
       const C third = C(1) / C(3), twelfth = C(1) / C(12);
-      const C sx = third * (Ez - Wz) + twelfth * ((Ep - Wp) + (Em - Wm));
-      const C sy = third * (Cp - Cm) + twelfth * ((Ep + Wp) - (Em + Wm));
-      Fx = A.P.minus_G * Cz * sx;
-      Fy = A.P.minus_G * Cz * sy;
+      const C sx = fma_rn(third, sub_rn(Ez, Wz),
+                          mul_rn(twelfth, add_rn(sub_rn(Ep, Wp), sub_rn(Em, Wm))));
+      const C sy = fma_rn(third, sub_rn(Cp, Cm),
+                          mul_rn(twelfth, sub_rn(add_rn(Ep, Wp), add_rn(Em, Wm))));
+      const C gpsi = mul_rn(A.P.minus_G, Cz);
+      Fx = mul_rn(gpsi, sx);
+      Fy = mul_rn(gpsi, sy);
     }
 
     const int idx = y * nx + c;
@@ -186,9 +189,9 @@ __device__ __forceinline__ void strip_run(const StripArgs<S>& A, int strip, int 
           C resid = rho0;
 #pragma unroll
           for (int a = 0; a < kQ; ++a) {
-            const typename S::T d = S::from_c(Pcur[a] - w_of<C>(a) * rho0);
+            const typename S::T d = S::from_c(sub_rn(Pcur[a], mul_rn(w_of<C>(a), rho0)));
             A.dst[a * A.plane + idx] = d;
-            resid -= S::to_c(d);
+            resid = sub_rn(resid, S::to_c(d));
           }
           A.rho_dst[idx] = float(resid);
         } else {

@@ -34,6 +34,36 @@ class lbm_params(ctypes.Structure):
                 ("cuda_stream", ctypes.c_void_p)]
 
 
+class lbm_instance(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("T_over_Tc", ctypes.c_double),
+                ("tau", ctypes.c_double), ("sigma", ctypes.c_double), ("scheme", ctypes.c_int)]
+
+
+class lbm_batch_params(ctypes.Structure):
+    _fields_ = [("tc_mode", ctypes.c_int), ("a", ctypes.c_double), ("b", ctypes.c_double),
+                ("R", ctypes.c_double), ("G", ctypes.c_double), ("device", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p), ("window", ctypes.c_int),
+                ("tol", ctypes.c_double), ("max_steps", ctypes.c_int), ("mode", ctypes.c_int),
+                ("rows_per_item", ctypes.c_int), ("conv", ctypes.c_int)]
+
+
+class lbm_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("steps", ctypes.c_int), ("rho_g", ctypes.c_double),
+                ("rho_l", ctypes.c_double), ("width", ctypes.c_double),
+                ("mass", ctypes.c_double), ("max_drho", ctypes.c_double)]
+
+
+class lbm_batch_stats(ctypes.Structure):
+    _fields_ = [("windows", ctypes.c_int), ("launches", ctypes.c_ulonglong),
+                ("gpu_ms", ctypes.c_double), ("mode", ctypes.c_int),
+                ("rows_per_item", ctypes.c_int), ("n_active", ctypes.c_int)]
+
+
+BATCH_AUTO, BATCH_WORKLIST, BATCH_PERSISTENT = range(3)
+CONV_COEX, CONV_CELL = range(2)
+RUN_ACTIVE, RUN_CONVERGED, RUN_DIVERGED, RUN_CAPPED = range(4)
+
+
 class LbmError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -67,6 +97,17 @@ SIGNATURES = {
     "lbm_set_band_rows": (_I, [_P, _I]),
     "lbm_get_launch_geometry": (_I, [_P, _I, _IP, _IP, _IP, _IP]),
     "lbm_mass_f32_noalloc": (_I, [_P, ctypes.c_size_t, _P, _P]),
+    "lbm_batch_default_params": (None, [ctypes.POINTER(lbm_batch_params)]),
+    "lbm_batch_create": (_I, [ctypes.POINTER(lbm_batch_params), ctypes.POINTER(lbm_instance),
+                              _I, ctypes.POINTER(_P)]),
+    "lbm_batch_init_density": (_I, [_P, _I, _P]),
+    "lbm_batch_init_slabs": (_I, [_P, _P, _P, _P]),
+    "lbm_batch_run": (_I, [_P, _I, _IP]),
+    "lbm_batch_get_result": (_I, [_P, _I, ctypes.POINTER(lbm_result)]),
+    "lbm_batch_get_density": (_I, [_P, _I, _P]),
+    "lbm_batch_get_stats": (_I, [_P, ctypes.POINTER(lbm_batch_stats)]),
+    "lbm_batch_last_error": (ctypes.c_char_p, [_P]),
+    "lbm_batch_destroy": (_I, [_P]),
 }
 
 _lib = None
@@ -235,3 +276,94 @@ class Lattice:
                                                   *[ctypes.byref(x) for x in v]),
                     "lbm_get_launch_geometry")
         return dict(zip(("n_strips", "band_rows", "n_bands", "grid"), (x.value for x in v)))
+
+
+class Batch:
+    """A batch of independent instances (lbm_batch_* of the C ABI).
+
+    `instances` is a list of dicts with nx, ny, T_over_Tc, tau, sigma, scheme.
+    """
+
+    def __init__(self, instances, window=1000, tol=1e-9, max_steps=200000, mode=BATCH_AUTO,
+                 rows_per_item=0, tc_mode=0, device=0, stream=None, conv=CONV_COEX):
+        p = lbm_batch_params()
+        lib().lbm_batch_default_params(ctypes.byref(p))
+        p.window, p.tol, p.max_steps, p.conv = int(window), float(tol), int(max_steps), int(conv)
+        p.mode, p.rows_per_item, p.tc_mode, p.device = int(mode), int(rows_per_item), \
+            int(tc_mode), int(device)
+        p.cuda_stream = None if stream is None else ctypes.c_void_p(int(stream))
+        arr = (lbm_instance * len(instances))()
+        for k, d in enumerate(instances):
+            arr[k] = lbm_instance(int(d["nx"]), int(d["ny"]), float(d["T_over_Tc"]),
+                                  float(d["tau"]), float(d.get("sigma", 0.0)),
+                                  int(d["scheme"]))
+        h = _P()
+        st = lib().lbm_batch_create(ctypes.byref(p), arr, len(instances), ctypes.byref(h))
+        if st:
+            raise LbmError(st, "lbm_batch_create")
+        self.h = h
+        self.instances = [dict(d) for d in instances]
+
+    def _check(self, st, what):
+        if st:
+            raise LbmError(st, f"{what}: {lib().lbm_batch_last_error(self.h).decode()}")
+
+    def close(self):
+        if self.h:
+            lib().lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __len__(self):
+        return len(self.instances)
+
+    def init_density(self, i, rho):
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        d = self.instances[i]
+        assert rho.shape == (d["ny"], d["nx"])
+        self._check(lib().lbm_batch_init_density(self.h, int(i), _dptr(rho)),
+                    "lbm_batch_init_density")
+
+    def init_slabs(self, rho_g, rho_l, width):
+        g, l, w = (np.ascontiguousarray(v, dtype=np.float64) for v in (rho_g, rho_l, width))
+        assert len(g) == len(l) == len(w) == len(self)
+        self._check(lib().lbm_batch_init_slabs(self.h, _dptr(g), _dptr(l), _dptr(w)),
+                    "lbm_batch_init_slabs")
+
+    def run(self, max_windows=1 << 30):
+        n = _I()
+        self._check(lib().lbm_batch_run(self.h, int(max_windows), ctypes.byref(n)),
+                    "lbm_batch_run")
+        return n.value
+
+    def result(self, i):
+        r = lbm_result()
+        self._check(lib().lbm_batch_get_result(self.h, int(i), ctypes.byref(r)),
+                    "lbm_batch_get_result")
+        return {k: getattr(r, k) for k, _ in lbm_result._fields_}
+
+    def results(self):
+        return [self.result(i) for i in range(len(self))]
+
+    def density(self, i):
+        d = self.instances[i]
+        rho = np.empty((d["ny"], d["nx"]))
+        self._check(lib().lbm_batch_get_density(self.h, int(i), _dptr(rho)),
+                    "lbm_batch_get_density")
+        return rho
+
+    def stats(self):
+        s = lbm_batch_stats()
+        self._check(lib().lbm_batch_get_stats(self.h, ctypes.byref(s)), "lbm_batch_get_stats")
+        return {k: getattr(s, k) for k, _ in lbm_batch_stats._fields_}

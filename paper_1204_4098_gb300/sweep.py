@@ -1,0 +1,133 @@
+"""Parameter sweeps of flat-interface runs: batched engine, sequential plain
+runs, and sharding across ranks.
+
+* ``cold_start_profiles`` -- per-instance (rho_g, rho_l) from the Maxwell
+  construction (Eq. 7) of the library's host EOS helper, i.e. the cold start.
+* ``run_batched`` -- all instances in one lbm_batch (CUDA graphs, autotuned).
+* ``run_sequential`` -- one plain lbm_step run per instance, with the same
+  convergence rule checked on the host after every window (the baseline the
+  batched engine is compared with).
+* ``shard`` -- longest-processing-time split of instances over ranks (cost =
+  cells); ranks run their shards independently (no data-path collective).
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import inputs, lbm
+
+F32_EPS = 2.0 ** -23
+
+
+def cold_start_profiles(instances, tc_mode=0):
+    """(rho_g, rho_l) of the Maxwell construction at each instance's T."""
+    g, l = [], []
+    for d in instances:
+        rg, rl, _ = lbm.maxwell(lbm.temperature(d["T_over_Tc"], tc_mode))
+        g.append(rg)
+        l.append(rl)
+    return np.array(g), np.array(l)
+
+
+def run_batched(instances, rho_g, rho_l, width, window=1000, tol=1e-9, max_steps=200000,
+                mode=lbm.BATCH_AUTO, rows_per_item=0, device=0, stream=None,
+                conv=lbm.CONV_COEX):
+    """Run every instance to convergence in one batch; returns (results, stats,
+    wall seconds).  width <= 0 starts from a sharp slab."""
+    t0 = time.perf_counter()
+    with lbm.Batch(instances, window=window, tol=tol, max_steps=max_steps, mode=mode,
+                   rows_per_item=rows_per_item, device=device, stream=stream,
+                   conv=conv) as b:
+        b.init_slabs(rho_g, rho_l, width)
+        b.run()
+        res, stats = b.results(), b.stats()
+    return res, stats, time.perf_counter() - t0
+
+
+def _coexistence(rho):
+    ny = rho.shape[0]
+    rows = rho.mean(1)
+    lo = ny // 2 - 1 if ny >= 2 else 0
+    return 0.5 * (rows[0] + rows[-1]), 0.5 * (rows[lo] + rows[ny // 2])
+
+
+def _calm(new, old, tol):
+    return abs(new - old) < max(tol, 8 * F32_EPS * abs(new))
+
+
+def run_sequential(instances, rho_g, rho_l, width, window=1000, tol=1e-9, max_steps=200000,
+                   device=0, conv=lbm.CONV_COEX):
+    """Plain runs, one instance after another, through lbm_step; convergence
+    is checked on the host with the batch engine's rules (CONV_COEX: rho_g
+    and rho_l each changed by less than max(tol, 8 eps_32 value) over two
+    consecutive windows; CONV_CELL: every cell by less than
+    max(tol, 8 eps_32 rho) over a window).  Returns (results, wall seconds)."""
+    out = []
+    t0 = time.perf_counter()
+    for k, d in enumerate(instances):
+        nx, ny = d["nx"], d["ny"]
+        if width[k] > 0:
+            rho0 = inputs.slab_tanh(nx, ny, rho_g[k], rho_l[k], W=width[k])
+        else:
+            rho0 = inputs.slab_step(nx, ny, rho_g[k], rho_l[k])
+        with lbm.Lattice(nx, ny, d["T_over_Tc"], precision=lbm.FP32, device=device) as lat:
+            lat.init_density(rho0)
+            prev = lat.observe()[0]
+            prev_c = None
+            steps, status, calm = 0, lbm.RUN_ACTIVE, 0
+            while status == lbm.RUN_ACTIVE:
+                st = lat.step(window, d["scheme"], d["tau"], d.get("sigma", 0.0),
+                              raise_on_error=False)
+                steps += window
+                if st == lbm.LBM_E_DIVERGED:
+                    status = lbm.RUN_DIVERGED
+                    break
+                rho = lat.observe()[0]
+                c = _coexistence(rho)
+                calm = calm + 1 if prev_c is not None and _calm(c[0], prev_c[0], tol) and \
+                    _calm(c[1], prev_c[1], tol) else 0
+                cell = np.all(np.abs(rho - prev) < np.maximum(tol, 8 * F32_EPS * np.abs(rho)))
+                if not np.all(np.isfinite(rho)):
+                    status = lbm.RUN_DIVERGED
+                elif (cell if conv == lbm.CONV_CELL else calm >= 2):
+                    status = lbm.RUN_CONVERGED
+                elif steps >= max_steps:
+                    status = lbm.RUN_CAPPED
+                prev, prev_c = rho, c
+            g, l = _coexistence(prev) if status != lbm.RUN_DIVERGED else (np.nan, np.nan)
+        out.append(dict(status=status, steps=steps, rho_g=g, rho_l=l))
+    return out, time.perf_counter() - t0
+
+
+def shard(instances, world, rank):
+    """Indices of the instances rank `rank` runs: largest first onto the
+    least-loaded rank (cost = cells), deterministic for every rank."""
+    loads = [0] * world
+    owner = {}
+    order = sorted(range(len(instances)),
+                   key=lambda i: (-instances[i]["nx"] * instances[i]["ny"], i))
+    for i in order:
+        r = min(range(world), key=lambda q: (loads[q], q))
+        owner[i] = r
+        loads[r] += instances[i]["nx"] * instances[i]["ny"]
+    return [i for i in range(len(instances)) if owner[i] == rank]
+
+
+def gather_results(local_idx, local_results, n_total, world):
+    """All ranks' results in instance order (torch.distributed all_gather of
+    Python objects; a host-side exchange, not on the data path)."""
+    if world == 1:
+        out = [None] * n_total
+        for i, r in zip(local_idx, local_results):
+            out[i] = r
+        return out
+    import torch.distributed as dist
+    parts = [None] * world
+    dist.all_gather_object(parts, list(zip(local_idx, local_results)))
+    out = [None] * n_total
+    for part in parts:
+        for i, r in part:
+            out[i] = r
+    return out
