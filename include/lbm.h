@@ -246,10 +246,13 @@ lbm_status lbm_batch_create(const lbm_batch_params *p, const lbm_instance *inst,
                             int count, lbm_batch **out);
 
 /* Instance i starts at rest from the host density rho (ny*nx doubles,
- * copied); LBM_E_INVAL if it leaves the domain of psi. */
+ * copied); LBM_E_INVAL if it leaves the domain of psi.  Called on an instance
+ * that has run, it restarts it from rho (active again, convergence history
+ * cleared) while its step count keeps the steps already spent. */
 lbm_status lbm_batch_init_density(lbm_batch *b, int i, const double *rho);
 
-/* Every instance starts at rest from the flat-interface profile of Eq. 36
+/* Every instance starts (all results reset) at rest from the flat-interface
+ * profile of Eq. 36
  * built on the device: rho_g + (rho_l - rho_g)/2 [tanh(2(y - ny/4)/W) -
  * tanh(2(y - 3ny/4)/W)] with the per-instance rho_g[i], rho_l[i], W = width[i]
  * (width[i] <= 0: a sharp step, liquid on rows [ny/4, 3ny/4)). */
@@ -268,6 +271,45 @@ lbm_status lbm_batch_get_density(lbm_batch *b, int i, double *rho);
 lbm_status lbm_batch_get_stats(const lbm_batch *b, lbm_batch_stats *s);
 const char *lbm_batch_last_error(const lbm_batch *b);
 lbm_status lbm_batch_destroy(lbm_batch *b);
+
+/* ---- warm-start network ------------------------------------------------- */
+/*
+ * A 4 -> 64 -> 64 -> 3 MLP with tanh hidden layers, y = tanh(tanh(x W1 + b1)
+ * W2 + b2) W3 + b3, trained on the mean squared error with Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8).  The paper has no network: it maps a
+ * sweep point (T/Tc, tau, sigma, scheme, scaled by the caller) to the
+ * relaxed slab's (rho_l, log rho_g, width) (standardised by the caller) to
+ * start new runs near their answer.  Parameters are one flat FP32 vector
+ * W1[4][64], b1[64], W2[64][64], b2[64], W3[64][3], b3[3] (row-major,
+ * lbm_mlp_num_params() = 4675 values).  X is [n][4], Y is [n][3], host FP32.
+ */
+typedef struct lbm_mlp lbm_mlp;
+
+int lbm_mlp_num_params(void);
+lbm_status lbm_mlp_create(int device, void *cuda_stream, lbm_mlp **out);
+lbm_status lbm_mlp_destroy(lbm_mlp *m);
+const char *lbm_mlp_last_error(const lbm_mlp *m);
+
+/* Set the parameters (and reset the Adam state) / read them back. */
+lbm_status lbm_mlp_set_params(lbm_mlp *m, const float *params);
+lbm_status lbm_mlp_get_params(lbm_mlp *m, float *params);
+
+/* Gradient of the loss over the n <= 128 samples (no update); *loss may be
+ * NULL. */
+lbm_status lbm_mlp_gradient(lbm_mlp *m, const float *X, const float *Y, int n,
+                            float *grad, float *loss);
+
+/* Adam over `epochs` epochs; order holds epochs x n sample indices (the
+ * caller's shuffles, so runs are reproducible), minibatch k of epoch e is
+ * order[e*n + k*batch ...] (1 <= batch <= 128, a short last batch is used as
+ * is).  One kernel launch trains all epochs.  *final_loss (nullable) gets the
+ * last minibatch's loss. */
+lbm_status lbm_mlp_train(lbm_mlp *m, const float *X, const float *Y, int n,
+                         const int *order, int epochs, int batch, float lr,
+                         float *final_loss);
+
+/* Y = network(X) for n samples. */
+lbm_status lbm_mlp_predict(lbm_mlp *m, const float *X, int n, float *Y);
 
 /* ---- allocation-free variant ------------------------------------------- */
 

@@ -306,7 +306,8 @@ struct lbm_batch {
   BatchOut* h_out = nullptr;
   unsigned* h_status = nullptr;
   std::vector<lbm_result> res;
-  std::vector<int> calm;  // consecutive windows meeting the COEX rule
+  std::vector<int> calm;     // consecutive windows meeting the COEX rule
+  std::vector<char> fresh;   // (re)initialised since the last window
   std::vector<int> active;
   int sm_count = 0;
   int wl_grid = 0;
@@ -589,6 +590,7 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
   b->tmp_cells = max_cells;
   b->res.assign(count, lbm_result{});
   b->calm.assign(count, 0);
+  b->fresh.assign(count, 1);
   auto bail = [&](lbm_status st, const char* m) {
     lbm_batch_destroy(b);
     (void)m;
@@ -715,6 +717,16 @@ lbm_status lbm_batch_init_density(lbm_batch* b, int i, const double* rho) {
     return bfail(b, LBM_E_INVAL, "rho of instance " + std::to_string(i) +
                                      " outside the domain of psi");
   }
+  // a restart: the instance runs again from this state; its step count keeps
+  // the steps already spent
+  b->fresh[i] = 1;
+  b->calm[i] = 0;
+  b->res[i].status = LBM_RUN_ACTIVE;
+  if (std::find(b->active.begin(), b->active.end(), i) == b->active.end()) {
+    b->active.push_back(i);
+    std::sort(b->active.begin(), b->active.end());
+    b->stats.n_active = int(b->active.size());
+  }
   b->initialized = true;
   return LBM_OK;
 }
@@ -750,6 +762,14 @@ lbm_status lbm_batch_init_slabs(lbm_batch* b, const double* rho_g, const double*
       return bfail(b, LBM_E_INVAL, "slab of instance " + std::to_string(i) +
                                        " outside the domain of psi");
     }
+  for (int i = 0; i < b->count; ++i) {
+    b->fresh[i] = 1;
+    b->calm[i] = 0;
+    b->res[i] = lbm_result{};
+  }
+  b->active.resize(b->count);
+  std::iota(b->active.begin(), b->active.end(), 0);
+  b->stats.n_active = b->count;
   b->initialized = true;
   return LBM_OK;
 }
@@ -791,7 +811,8 @@ lbm_status lbm_batch_run(lbm_batch* b, int max_windows, int* n_active) {
     for (int i : b->active) {
       lbm_result& r = b->res[i];
       const BatchOut& o = b->h_out[i];
-      const bool first = r.steps == 0;
+      const bool first = b->fresh[i] != 0;
+      b->fresh[i] = 0;
       const bool coex_calm =
           !first && std::fabs(o.rho_g - r.rho_g) < std::max(b->p.tol, floor32 * std::fabs(o.rho_g)) &&
           std::fabs(o.rho_l - r.rho_l) < std::max(b->p.tol, floor32 * std::fabs(o.rho_l));

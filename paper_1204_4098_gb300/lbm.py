@@ -108,6 +108,15 @@ SIGNATURES = {
     "lbm_batch_get_stats": (_I, [_P, ctypes.POINTER(lbm_batch_stats)]),
     "lbm_batch_last_error": (ctypes.c_char_p, [_P]),
     "lbm_batch_destroy": (_I, [_P]),
+    "lbm_mlp_num_params": (_I, []),
+    "lbm_mlp_create": (_I, [_I, _P, ctypes.POINTER(_P)]),
+    "lbm_mlp_destroy": (_I, [_P]),
+    "lbm_mlp_last_error": (ctypes.c_char_p, [_P]),
+    "lbm_mlp_set_params": (_I, [_P, _P]),
+    "lbm_mlp_get_params": (_I, [_P, _P]),
+    "lbm_mlp_gradient": (_I, [_P, _P, _P, _I, _P, _P]),
+    "lbm_mlp_train": (_I, [_P, _P, _P, _I, _P, _I, _I, ctypes.c_float, _P]),
+    "lbm_mlp_predict": (_I, [_P, _P, _I, _P]),
 }
 
 _lib = None
@@ -367,3 +376,74 @@ class Batch:
         s = lbm_batch_stats()
         self._check(lib().lbm_batch_get_stats(self.h, ctypes.byref(s)), "lbm_batch_get_stats")
         return {k: getattr(s, k) for k, _ in lbm_batch_stats._fields_}
+
+
+def _fptr(a, dtype=np.float32):
+    assert a.dtype == dtype and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class MLP:
+    """The warm-start network of the C ABI (lbm_mlp_*), FP32."""
+
+    def __init__(self, params=None, device=0, stream=None):
+        h = _P()
+        st = lib().lbm_mlp_create(int(device), None if stream is None else
+                                  ctypes.c_void_p(int(stream)), ctypes.byref(h))
+        if st:
+            raise LbmError(st, "lbm_mlp_create")
+        self.h = h
+        self.n_params = int(lib().lbm_mlp_num_params())
+        if params is not None:
+            self.set_params(params)
+
+    def _check(self, st, what):
+        if st:
+            raise LbmError(st, f"{what}: {lib().lbm_mlp_last_error(self.h).decode()}")
+
+    def close(self):
+        if self.h:
+            lib().lbm_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.shape == (self.n_params,)
+        self._check(lib().lbm_mlp_set_params(self.h, _fptr(p)), "lbm_mlp_set_params")
+
+    def params(self):
+        p = np.empty(self.n_params, dtype=np.float32)
+        self._check(lib().lbm_mlp_get_params(self.h, _fptr(p)), "lbm_mlp_get_params")
+        return p
+
+    def gradient(self, X, Y):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.ascontiguousarray(Y, dtype=np.float32)
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        self._check(lib().lbm_mlp_gradient(self.h, _fptr(X), _fptr(Y), len(X), _fptr(g),
+                                           _fptr(loss)), "lbm_mlp_gradient")
+        return float(loss[0]), g
+
+    def train(self, X, Y, order, batch, lr):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.ascontiguousarray(Y, dtype=np.float32)
+        order = np.ascontiguousarray(order, dtype=np.int32)
+        loss = np.zeros(1, dtype=np.float32)
+        self._check(lib().lbm_mlp_train(self.h, _fptr(X), _fptr(Y), len(X),
+                                        _fptr(order, np.int32), order.shape[0], int(batch),
+                                        float(lr), _fptr(loss)), "lbm_mlp_train")
+        return float(loss[0])
+
+    def predict(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.empty((len(X), 3), dtype=np.float32)
+        self._check(lib().lbm_mlp_predict(self.h, _fptr(X), len(X), _fptr(Y)),
+                    "lbm_mlp_predict")
+        return Y

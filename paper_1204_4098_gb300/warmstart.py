@@ -1,0 +1,134 @@
+"""Learned warm start of flat-interface sweeps.
+
+A 4 -> 64 -> 64 -> 3 network (lbm_mlp_*, trained on the GPU by the
+library's kernels) maps a sweep point (T/Tc, tau, sigma, scheme) to the
+relaxed slab's (rho_l, rho_g, interface width W).  New runs then start from
+the Eq. 36 profile with the predicted values instead of the Maxwell step
+(cold start).  Fallback: if, after the first window, rho_l or rho_g has moved
+by more than 1e-2 (relative) from the prediction, the instance restarts cold;
+the steps already spent are counted.  Cold runs remain the judge of the
+error: the tests and the sweep report compare warm and cold coexistence
+densities.
+
+Inputs are scaled to [-1, 1] over the sweep ranges.  The network learns
+the answer relative to the Maxwell construction at the same temperature
+(computed on the host): targets (rho_l / rho_l^M - 1, log(rho_g / rho_g^M),
+log W), standardised with the training set's mean and spread.  rho_g spans
+2.5 decades over the sweep's temperatures; the ratio to Maxwell is smooth.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import inputs, lbm, sweep
+
+T_RANGE, TAU_RANGE, SIGMA_RANGE = (0.45, 0.95), (0.6, 1.5), (0.0, 0.2)
+
+
+def features(instances):
+    """(T/Tc, tau, sigma, scheme) scaled to [-1, 1]."""
+    def scale(v, lo, hi):
+        return 2.0 * (v - lo) / (hi - lo) - 1.0
+    return np.array([[scale(d["T_over_Tc"], *T_RANGE), scale(d["tau"], *TAU_RANGE),
+                      scale(d.get("sigma", 0.0), *SIGMA_RANGE), float(d["scheme"]) - 1.0]
+                     for d in instances], dtype=np.float32)
+
+
+def glorot_params(seed):
+    """Glorot-uniform weights, zero biases, in the lbm_mlp layout."""
+    g = np.random.default_rng(seed)
+    parts = []
+    for fan_in, fan_out in ((4, 64), (64, 64), (64, 3)):
+        lim = np.sqrt(6.0 / (fan_in + fan_out))
+        parts += [g.uniform(-lim, lim, fan_in * fan_out), np.zeros(fan_out)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+@dataclass
+class WarmStartModel:
+    mlp: lbm.MLP
+    mean: np.ndarray
+    std: np.ndarray
+    train_loss: float
+    train_seconds: float
+
+    def predict(self, instances):
+        """(rho_l, rho_g, W) per instance."""
+        y = self.mlp.predict(features(instances)).astype(np.float64) * self.std + self.mean
+        mg, ml = sweep.cold_start_profiles(instances)
+        return ml * (1.0 + y[:, 0]), mg * np.exp(y[:, 1]), np.exp(y[:, 2])
+
+
+def targets(instances, rho_l, rho_g, width):
+    """Network targets relative to the Maxwell densities at each T."""
+    mg, ml = sweep.cold_start_profiles(instances)
+    return np.stack([np.asarray(rho_l) / ml - 1.0, np.log(np.asarray(rho_g) / mg),
+                     np.log(np.asarray(width))], 1)
+
+
+def training_data(n_draws, seed=40, ny_range=(128, 512), max_steps=100000, window=1000):
+    """Cold batched runs of narrow (nx = 32) slabs drawn from the sweep
+    distribution; the converged ones give (features, targets).  Slabs are
+    x-invariant, so the width of the lattice does not change the answer."""
+    inst = inputs.sweep_instances(n_draws, seed=seed, nx_range=(32, 32), ny_range=ny_range)
+    g, l = sweep.cold_start_profiles(inst)
+    res, stats, wall = sweep.run_batched(inst, g, l, np.zeros(len(inst)), window=window,
+                                         max_steps=max_steps)
+    keep = [k for k, r in enumerate(res)
+            if r["status"] == lbm.RUN_CONVERGED and r["rho_g"] > 0 and r["width"] > 0]
+    kept = [inst[k] for k in keep]
+    X = features(kept)
+    Y = targets(kept, [res[k]["rho_l"] for k in keep], [res[k]["rho_g"] for k in keep],
+                [res[k]["width"] for k in keep])
+    return X, Y, dict(draws=n_draws, converged=len(keep), gpu_ms=stats["gpu_ms"], wall=wall)
+
+
+def train(X, Y, epochs=1500, batch=128, lr=2e-3, seed=0, device=0):
+    mean, std = Y.mean(0), Y.std(0) + 1e-12
+    T = ((Y - mean) / std).astype(np.float32)
+    rng = np.random.default_rng(seed)
+    order = np.stack([rng.permutation(len(X)) for _ in range(epochs)]).astype(np.int32)
+    mlp = lbm.MLP(glorot_params(seed), device=device)
+    t0 = time.perf_counter()
+    loss = mlp.train(X, T, order, batch, lr)
+    return WarmStartModel(mlp, mean, std, loss, time.perf_counter() - t0)
+
+
+def run_warm(instances, model, window=1000, tol=1e-9, max_steps=200000, fallback_tol=1e-2,
+             device=0):
+    """Warm-started batched runs with the cold-start fallback.  Returns
+    (results, info): results per instance (status, steps including any
+    wasted warm window, rho_g, rho_l, width, fallback flag)."""
+    pl, pg, pw = model.predict(instances)
+    pw = np.clip(pw, 1.0, None)
+    cg, cl = sweep.cold_start_profiles(instances)
+    t0 = time.perf_counter()
+    with lbm.Batch(instances, window=window, tol=tol, max_steps=max_steps, device=device) as b:
+        b.init_slabs(pg, pl, pw)
+        b.run(1)
+        fallback = []
+        for k, d in enumerate(instances):
+            r = b.result(k)
+            if r["status"] == lbm.RUN_DIVERGED:
+                continue
+            if abs(r["rho_l"] / pl[k] - 1) > fallback_tol or \
+                    abs(r["rho_g"] / pg[k] - 1) > fallback_tol:
+                fallback.append(k)
+                b.init_density(k, inputs.slab_step(d["nx"], d["ny"], cg[k], cl[k]))
+        b.run()
+        res, stats = b.results(), b.stats()
+    for k, r in enumerate(res):
+        r["fallback"] = k in fallback
+    return res, dict(gpu_ms=stats["gpu_ms"], wall=time.perf_counter() - t0,
+                     fallbacks=len(fallback), predicted=(pl, pg, pw))
+
+
+def run_cold_batched(instances, window=1000, tol=1e-9, max_steps=200000, device=0):
+    cg, cl = sweep.cold_start_profiles(instances)
+    res, stats, wall = sweep.run_batched(instances, cg, cl, np.zeros(len(instances)),
+                                         window=window, tol=tol, max_steps=max_steps,
+                                         device=device)
+    return res, dict(gpu_ms=stats["gpu_ms"], wall=wall)
