@@ -307,6 +307,10 @@ def run_ours(args, world, rank, local):
                               "frac": gbs / peak, "bytes_per_cell": BYTES_PER_CELL[name]}
             v.close()
 
+    sweep_line = None
+    if rank == 0 and not args.no_sweep:
+        sweep_line = sweep_measure(128, 16, seed=4, device=local)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
@@ -322,7 +326,129 @@ def run_ours(args, world, rank, local):
                 "gpu_launches": launches}
         if variants:
             line["storage_variants"] = variants
+        if sweep_line:
+            line["batched_sweep"] = sweep_line
         print(json.dumps(line), flush=True)
+
+
+def _status_counts(res):
+    names = {0: "active", 1: "converged", 2: "diverged", 3: "capped"}
+    out = {}
+    for r in res:
+        out[names[r["status"]]] = out.get(names[r["status"]], 0) + 1
+    return out
+
+
+def _coex_agreement(a, b):
+    """Max relative difference of rho_g and rho_l over runs converged in both."""
+    both = [k for k in range(len(a)) if a[k]["status"] == 1 and b[k]["status"] == 1]
+    if not both:
+        return None, 0
+    err = max(max(abs(a[k]["rho_g"] / b[k]["rho_g"] - 1), abs(a[k]["rho_l"] / b[k]["rho_l"] - 1))
+              for k in both)
+    return err, len(both)
+
+
+def sweep_measure(n_inst, n_seq, seed=4, device=0):
+    """Config-4 style sweep: n_inst instances (grid 32..512 x 128..512, T/Tc in
+    [0.45, 0.95], tau in [0.6, 1.5], sigma in [0, 0.2], scheme in {SC, EDM,
+    improved}) from the cold Maxwell step, batched to convergence, against
+    sequential plain runs of the first n_seq of them."""
+    import numpy as np
+
+    from paper_1204_4098_gb300 import inputs, sweep
+    inst = inputs.sweep_instances(n_inst, seed=seed)
+    g, l = sweep.cold_start_profiles(inst)
+    w = np.zeros(n_inst)
+    res, stats, wall = sweep.run_batched(inst, g, l, w, device=device)
+    seq, seq_wall = sweep.run_sequential(inst[:n_seq], g[:n_seq], l[:n_seq], w[:n_seq],
+                                         device=device)
+    agree, n_both = _coex_agreement(res[:n_seq], seq)
+    # sequential time per instance, over the same instances the batch also ran
+    seq_total = seq_wall * n_inst / max(n_seq, 1)
+    cells_steps = sum(d["nx"] * d["ny"] * r["steps"] for d, r in zip(inst, res))
+    return {"instances": n_inst, "batched_wall_s": wall, "batched_gpu_s": stats["gpu_ms"] / 1e3,
+            "instances_per_s": n_inst / wall,
+            "batched_MLUPS": cells_steps / (stats["gpu_ms"] * 1e-3) / 1e6,
+            "windows": stats["windows"], "status": _status_counts(res),
+            "sequential_instances_timed": n_seq, "sequential_wall_s": seq_wall,
+            "sequential_wall_s_all": seq_total,
+            "speedup_vs_sequential": seq_total / wall,
+            "coexistence_max_rel_diff_vs_sequential": agree, "converged_in_both": n_both,
+            "convergence_rule": "COEX: rho_g, rho_l (FP64 row means) change < max(1e-9, 8 ulp) "
+                                "over two consecutive 1000-step windows; cap 2e5 steps",
+            "init": "cold: Maxwell densities, sharp slab (rows [ny/4, 3ny/4) liquid)"}
+
+
+def run_sweep_workload(args, world, rank, local):
+    import torch
+    torch.cuda.set_device(local)
+    res = sweep_measure(args.sweep_instances, args.seq_sample, device=local)
+    line = {"metric": METRIC, "workload": "batched parameter sweep (config 4)",
+            "value": res["instances_per_s"], "unit": "instances/s", "n_gpus": world,
+            "higher_is_better": True, "data": "synthetic", "dtype": "f32", **res}
+    print(json.dumps(line), flush=True)
+
+
+def run_warmstart_workload(args, world, rank, local):
+    """Config 5: train the network on converged cold runs, then start held-out
+    points on 256 x 256 grids from its predictions; compare with cold runs."""
+    import numpy as np
+    import torch
+
+    from paper_1204_4098_gb300 import inputs, lbm, sweep, warmstart
+    torch.cuda.set_device(local)
+    t0 = time.perf_counter()
+    X, Y, info = warmstart.training_data(args.train_draws, seed=40, max_steps=100000)
+    data_s = time.perf_counter() - t0
+    model = warmstart.train(X, Y, stages=((args.epochs, 2e-3), (args.epochs, 5e-4),
+                                          (args.epochs, 1e-4)), batch=128, seed=1)
+    held = inputs.sweep_instances(args.held_out, seed=41, nx_range=(256, 256),
+                                  ny_range=(256, 256))
+    warm, winfo = warmstart.run_warm(held, model)
+    cold, cinfo = warmstart.run_cold_batched(held)
+    g, l = sweep.cold_start_profiles(held)
+    ns = args.seq_sample
+    seq, seq_wall = sweep.run_sequential(held[:ns], g[:ns], l[:ns], np.zeros(ns))
+    seq_all = seq_wall * len(held) / max(ns, 1)
+    err, n_both = _coex_agreement(warm, cold)
+    both = [k for k in range(len(held)) if warm[k]["status"] == 1 and cold[k]["status"] == 1]
+    ws = float(np.mean([warm[k]["steps"] for k in both])) if both else None
+    cs = float(np.mean([cold[k]["steps"] for k in both])) if both else None
+    # time to the answer: rho_g, rho_l settled within 1e-3 of the cold converged values
+    t_warm, s_warm = warmstart.time_to_answer(warm, winfo, cold, among=both)
+    t_coldb, s_coldb = warmstart.time_to_answer(cold, cinfo, cold, among=both)
+    seq_t = []
+    for k, r in enumerate(seq):
+        if k not in both:
+            seq_t.append(r["wall"])  # outside the compared set: its whole time
+            continue
+        a = sweep.answer_step(r["history"], cold[k]["rho_g"], cold[k]["rho_l"])
+        seq_t.append(r["wall"] * (a[0] / r["steps"] if a else 1.0))
+    seq_answer_all = float(np.sum(seq_t)) * len(held) / max(ns, 1)
+    line = {"metric": METRIC, "workload": "learned warm start (config 5)",
+            "value": seq_answer_all / t_warm if t_warm else None,
+            "unit": "x less time to the coexistence densities within 1e-3 (warm batched vs "
+                    "cold sequential plain runs)",
+            "higher_is_better": True, "n_gpus": world, "data": "synthetic", "dtype": "f32",
+            "time_to_answer_s": {"warm_batched_gpu": t_warm, "cold_batched_gpu": t_coldb,
+                                 "cold_sequential_wall": seq_answer_all,
+                                 "mean_steps_warm": s_warm, "mean_steps_cold": s_coldb},
+            "training": {**info, "data_wall_s": data_s, "train_loss": model.train_loss,
+                         "train_s": model.train_seconds,
+                         "epochs": [args.epochs, args.epochs, args.epochs],
+                         "learning_rates": [2e-3, 5e-4, 1e-4]},
+            "held_out": len(held), "grid": "256x256",
+            "warm": {"wall_s": winfo["wall"], "gpu_s": winfo["gpu_ms"] / 1e3,
+                     "fallbacks": winfo["fallbacks"], "status": _status_counts(warm),
+                     "mean_steps_converged_both": ws},
+            "cold_batched": {"wall_s": cinfo["wall"], "gpu_s": cinfo["gpu_ms"] / 1e3,
+                             "status": _status_counts(cold), "mean_steps_converged_both": cs},
+            "cold_sequential": {"instances_timed": args.seq_sample, "wall_s": seq_wall,
+                                "wall_s_all": seq_all},
+            "coexistence_max_rel_err_warm_vs_cold": err, "converged_in_both": n_both,
+            "speedup_warm_batched_vs_cold_batched": cinfo["wall"] / winfo["wall"]}
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -338,12 +464,23 @@ def main():
     ap.add_argument("--variants", action="store_true", default=True)
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--ref-side", type=int, default=384)
+    ap.add_argument("--workload", choices=("roofline", "sweep", "warmstart"), default="roofline")
+    ap.add_argument("--sweep-instances", type=int, default=512)
+    ap.add_argument("--seq-sample", type=int, default=32)
+    ap.add_argument("--train-draws", type=int, default=11000)
+    ap.add_argument("--epochs", type=int, default=1500)
+    ap.add_argument("--held-out", type=int, default=256)
+    ap.add_argument("--no-sweep", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "sweep":
+        run_sweep_workload(args, world, rank, local)
+    elif args.workload == "warmstart":
+        run_warmstart_workload(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

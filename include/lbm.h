@@ -252,10 +252,13 @@ lbm_status lbm_batch_create(const lbm_batch_params *p, const lbm_instance *inst,
 lbm_status lbm_batch_init_density(lbm_batch *b, int i, const double *rho);
 
 /* Every instance starts (all results reset) at rest from the flat-interface
- * profile of Eq. 36
- * built on the device: rho_g + (rho_l - rho_g)/2 [tanh(2(y - ny/4)/W) -
- * tanh(2(y - 3ny/4)/W)] with the per-instance rho_g[i], rho_l[i], W = width[i]
- * (width[i] <= 0: a sharp step, liquid on rows [ny/4, 3ny/4)). */
+ * profile of Eq. 36 built on the device: rho_g + (rho_l - rho_g)/2
+ * [tanh(2(y - ny/4)/W) - tanh(2(y - 3ny/4)/W)] with the per-instance rho_g[i],
+ * rho_l[i], W = width[i] (width[i] <= 0: a sharp step, liquid on rows
+ * [ny/4, 3ny/4)).  At rest: for W > 0, zero actual velocity
+ * v = u + F/(2 rho) (Table I), i.e. f = f_eq(rho, u) with u = -F/(2 rho) from
+ * the Eq. 3 force of the initial profile; for the sharp step (and
+ * LBM_SCHEME_NOFORCE instances) u = 0. */
 lbm_status lbm_batch_init_slabs(lbm_batch *b, const double *rho_g, const double *rho_l,
                                 const double *width);
 

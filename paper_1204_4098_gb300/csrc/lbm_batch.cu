@@ -227,8 +227,15 @@ batch_window_reduce(const BatchInst* __restrict__ inst, const int* __restrict__ 
   }
 }
 
-// Eq. 36 flat interface at rest for every instance (blockIdx.y = instance):
-// f_a(x) = w_a rho(y), stored so that the next pull reproduces it.
+// Eq. 36 flat interface at rest for every instance (blockIdx.y = instance).
+// For the smooth profile (W > 0) "at rest" means zero actual velocity
+// v = u + F/(2 rho) (Table I): with the x-invariant profile F = (0, F_y),
+// F_y = -G psi(y) (psi(y+1) - psi(y-1)) / 2 (Eq. 3 summed over the three
+// neighbours in each row), so the equilibrium is taken at
+// u = (0, -F_y / (2 rho)); starting at u = 0 instead gives the interface a
+// velocity F/(2 rho) and a long transient.  For the sharp step (W <= 0) the
+// force at the discontinuity is not that of any relaxed profile, so u = 0.
+// Stored so that the next pull reproduces f_a(x) = f_eq_a(rho(y), u(y)).
 __global__ void batch_init_slab_kernel(const BatchInst* __restrict__ inst,
                                        const double* __restrict__ prof, float* buf0,
                                        float* snap, unsigned* inst_status) {
@@ -237,23 +244,33 @@ __global__ void batch_init_slab_kernel(const BatchInst* __restrict__ inst,
   const double rg = prof[3 * i], rl = prof[3 * i + 1], W = prof[3 * i + 2];
   const size_t plane = size_t(I.nx) * I.ny;
   const int ny = I.ny;
+  auto wrap = [&](int y) { return y < 0 ? y + ny : (y >= ny ? y - ny : y); };
   auto rho_at = [&](int y) {
-    y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+    y = wrap(y);
     if (W > 0.0)
       return rg + 0.5 * (rl - rg) *
                       (tanh(2.0 * (y - ny / 4.0) / W) - tanh(2.0 * (y - 3.0 * ny / 4.0) / W));
     return (y >= ny / 4 && y < 3 * ny / 4) ? rl : rg;
   };
   bool bad = false;
+  auto psi_at = [&](int y) { return double(psi_of_rho(float(rho_at(y)), I.P, bad)); };
+  auto uy_at = [&](int y) {
+    const double Fy = double(I.P.minus_G) * psi_at(y) * 0.5 * (psi_at(y + 1) - psi_at(y - 1));
+    return -Fy / (2.0 * rho_at(y));
+  };
   for (size_t c = blockIdx.x * size_t(blockDim.x) + threadIdx.x; c < plane;
        c += size_t(gridDim.x) * blockDim.x) {
     const int y = int(c / I.nx);
 #pragma unroll
-    for (int a = 0; a < kQ; ++a)
-      buf0[I.off + a * plane + c] = float(double(w_of<float>(a)) * rho_at(y + ey_of(a)));
-    const double r = rho_at(y);
-    snap[I.coff + c] = float(r);
-    (void)psi_of_rho(float(r), I.P, bad);
+    for (int a = 0; a < kQ; ++a) {
+      const int ys = y + ey_of(a);
+      const double r = rho_at(ys);
+      const double u = (I.scheme == kNoForce || W <= 0.0) ? 0.0 : uy_at(ys);
+      const double eu = ey_of(a) * u;
+      buf0[I.off + a * plane + c] =
+          float(double(w_of<float>(a)) * r * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * u * u));
+    }
+    snap[I.coff + c] = float(rho_at(y));
   }
   if (bad) atomicOr(inst_status + i, kStatusInvalidInit);
 }

@@ -46,6 +46,41 @@ def run_batched(instances, rho_g, rho_l, width, window=1000, tol=1e-9, max_steps
     return res, stats, time.perf_counter() - t0
 
 
+def run_batch_with_history(batch, max_windows=1 << 30):
+    """Run a prepared lbm.Batch one window at a time, recording per instance
+    the (steps, rho_g, rho_l) after each window it was active in, and the
+    cumulative device time after each window.  Returns (history, times)."""
+    n = len(batch)
+    hist = [[] for _ in range(n)]
+    times = []
+    active = set(range(n))
+    while active and len(times) < max_windows:
+        left = batch.run(1)
+        times.append(batch.stats()["gpu_ms"] * 1e-3)
+        for k in list(active):
+            r = batch.result(k)
+            hist[k].append((r["steps"], r["rho_g"], r["rho_l"], len(times) - 1))
+            if r["status"] != lbm.RUN_ACTIVE:
+                active.discard(k)
+        if left == 0:
+            break
+    return hist, times
+
+
+def answer_step(history, ref_g, ref_l, rtol=1e-3):
+    """First recorded step from which rho_g and rho_l stay within rtol of the
+    reference values (None if they never settle there); with the window
+    index it was recorded at."""
+    ok_from = None
+    for steps, g, l, w in history:
+        good = abs(g / ref_g - 1) <= rtol and abs(l / ref_l - 1) <= rtol
+        if good and ok_from is None:
+            ok_from = (steps, w)
+        elif not good:
+            ok_from = None
+    return ok_from
+
+
 def _coexistence(rho):
     ny = rho.shape[0]
     rows = rho.mean(1)
@@ -67,6 +102,8 @@ def run_sequential(instances, rho_g, rho_l, width, window=1000, tol=1e-9, max_st
     out = []
     t0 = time.perf_counter()
     for k, d in enumerate(instances):
+        ti = time.perf_counter()
+        history = []
         nx, ny = d["nx"], d["ny"]
         if width[k] > 0:
             rho0 = inputs.slab_tanh(nx, ny, rho_g[k], rho_l[k], W=width[k])
@@ -96,8 +133,10 @@ def run_sequential(instances, rho_g, rho_l, width, window=1000, tol=1e-9, max_st
                 elif steps >= max_steps:
                     status = lbm.RUN_CAPPED
                 prev, prev_c = rho, c
+                history.append((steps, c[0], c[1], len(history)))
             g, l = _coexistence(prev) if status != lbm.RUN_DIVERGED else (np.nan, np.nan)
-        out.append(dict(status=status, steps=steps, rho_g=g, rho_l=l))
+        out.append(dict(status=status, steps=steps, rho_g=g, rho_l=l, history=history,
+                        wall=time.perf_counter() - ti))
     return out, time.perf_counter() - t0
 
 
