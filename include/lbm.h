@@ -158,6 +158,18 @@ unsigned long long lbm_kernel_launch_count(void);
 
 /* ---- launch tuning ------------------------------------------------------ */
 
+/* Step kernel variant; all give bit-identical results.  REGISTER: one column
+ * per lane, rows loaded into registers one row ahead.  PAIR: two adjacent
+ * columns per lane (8-byte vector loads and stores), for FP32/FP64 storage
+ * with even nx.  STAGED: one column per lane, rows brought into shared
+ * memory by asynchronous bulk copies several rows ahead (FP32 steps with
+ * nx % 4 == 0 and nx >= 64; a bounded wait that gives up makes lbm_step
+ * return LBM_E_TIMEOUT).  AUTO (default) = PAIR for FP32 with even nx, else
+ * REGISTER.  A variant that does not apply falls back to REGISTER. */
+enum { LBM_VARIANT_AUTO = 0, LBM_VARIANT_REGISTER = 1, LBM_VARIANT_STAGED = 2,
+       LBM_VARIANT_PAIR = 3 };
+lbm_status lbm_set_kernel_variant(lbm_ctx *ctx, int variant);
+
 /* Rows per warp band of the step kernel (0 = automatic: one wave of warps,
  * at least 8 rows each).  Changes only speed, never results. */
 lbm_status lbm_set_band_rows(lbm_ctx *ctx, int band_rows);

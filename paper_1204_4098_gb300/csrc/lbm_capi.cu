@@ -23,6 +23,12 @@ cudaError_t strip_launch_f64(int, int, const StripLaunch&, int, cudaStream_t);
 cudaError_t strip_launch_bf16(int, int, const StripLaunch&, int, cudaStream_t);
 cudaError_t strip_launch_f16(int, int, const StripLaunch&, int, cudaStream_t);
 cudaError_t strip_occupancy_f32(int, int, int*);
+cudaError_t strip2_launch_f32(int, int, const StripLaunch&, int, cudaStream_t);
+cudaError_t strip2_launch_f64(int, int, const StripLaunch&, int, cudaStream_t);
+cudaError_t strip2_occupancy_f32(int, int, int*);
+cudaError_t strip2_occupancy_f64(int, int, int*);
+cudaError_t strip_tma_launch_f32(int, const StripLaunch&, int, cudaStream_t);
+cudaError_t strip_tma_occupancy_f32(int, int*);
 cudaError_t strip_occupancy_f64(int, int, int*);
 cudaError_t strip_occupancy_bf16(int, int, int*);
 cudaError_t strip_occupancy_f16(int, int, int*);
@@ -61,6 +67,26 @@ cudaError_t strip_occupancy(int precision, int scheme, int mode, int* b) {
     case kFP16Dev: return strip_occupancy_f16(scheme, mode, b);
   }
   return cudaErrorInvalidValue;
+}
+cudaError_t strip2_launch(int precision, int scheme, int mode, const StripLaunch& L, int grid,
+                          cudaStream_t s) {
+  if (precision == kFP32) return strip2_launch_f32(scheme, mode, L, grid, s);
+  if (precision == kFP64) return strip2_launch_f64(scheme, mode, L, grid, s);
+  return cudaErrorNotSupported;
+}
+cudaError_t strip2_occupancy(int precision, int scheme, int mode, int* b) {
+  if (precision == kFP32) return strip2_occupancy_f32(scheme, mode, b);
+  if (precision == kFP64) return strip2_occupancy_f64(scheme, mode, b);
+  return cudaErrorNotSupported;
+}
+cudaError_t strip_tma_launch(int precision, int scheme, const StripLaunch& L, int grid,
+                             cudaStream_t s) {
+  if (precision != kFP32) return cudaErrorNotSupported;
+  return strip_tma_launch_f32(scheme, L, grid, s);
+}
+cudaError_t strip_tma_occupancy(int precision, int scheme, int* b) {
+  if (precision != kFP32) return cudaErrorNotSupported;
+  return strip_tma_occupancy_f32(scheme, b);
 }
 cudaError_t set_state_launch(int precision, void* dst, float* rd, int nx, int ny, size_t plane,
                              const double* rho, const double* ux, const double* uy,
@@ -130,6 +156,7 @@ struct lbm_ctx {
   int last_scheme = LBM_SCHEME_SC;
   int sm_count = 0;
   int band_rows_override = 0;
+  int variant = LBM_VARIANT_AUTO;
   std::string err;
 };
 
@@ -189,16 +216,41 @@ StripLaunch base_launch(lbm_ctx* c) {
   return L;
 }
 
+// Kernel variant for this lattice: the two-columns-per-lane kernel for direct
+// storage with even nx (AUTO), the bulk-copy staged kernel when asked for
+// (FP32 steps, nx % 4 == 0 so rows are 16-byte aligned, nx >= 64), else one
+// column per lane.
+int pick_variant(const lbm_ctx* c, int mode) {
+  const bool direct = c->p.precision == LBM_FP32 || c->p.precision == LBM_FP64;
+  const bool pair_ok = direct && c->p.nx % 2 == 0;
+  const bool staged_ok = mode == kStepMode && c->p.precision == LBM_FP32 && c->p.nx >= 64 &&
+                         c->p.nx % 4 == 0;
+  if (c->variant == LBM_VARIANT_STAGED && staged_ok) return LBM_VARIANT_STAGED;
+  // AUTO takes PAIR for FP32 only: in FP64 its doubled register state spills
+  if (((c->variant == LBM_VARIANT_AUTO && c->p.precision == LBM_FP32) ||
+       c->variant == LBM_VARIANT_PAIR) && pair_ok)
+    return LBM_VARIANT_PAIR;
+  return LBM_VARIANT_REGISTER;
+}
+bool use_staged(const lbm_ctx* c, int mode) { return pick_variant(c, mode) == LBM_VARIANT_STAGED; }
+
 // Warp-strip geometry: strips of 32 columns, and as many row bands as fill
 // the resident warp slots once (one wave: every warp of a band runs at the
 // same time as its neighbours).
 lbm_status geometry(lbm_ctx* c, int scheme, int mode, StripLaunch& L, int& grid) {
   int bps = 0;
-  LBM_CUDA(c, strip_occupancy(c->p.precision, scheme, mode, &bps));
+  const int variant = pick_variant(c, mode);
+  if (variant == LBM_VARIANT_STAGED)
+    LBM_CUDA(c, strip_tma_occupancy(c->p.precision, scheme, &bps));
+  else if (variant == LBM_VARIANT_PAIR)
+    LBM_CUDA(c, strip2_occupancy(c->p.precision, scheme, mode, &bps));
+  else
+    LBM_CUDA(c, strip_occupancy(c->p.precision, scheme, mode, &bps));
   if (bps < 1) bps = 1;
   const int warps_per_cta = kStripCtaThreads / 32;
   const long long resident = (long long)c->sm_count * bps * warps_per_cta;
-  const int n_strips = (c->p.nx + 31) / 32;
+  const int strip_w = variant == LBM_VARIANT_PAIR ? 64 : 32;
+  const int n_strips = (c->p.nx + strip_w - 1) / strip_w;
   const int ny = c->p.ny;
   int band_rows;
   if (c->band_rows_override > 0) {
@@ -250,7 +302,13 @@ lbm_status queue_steps(lbm_ctx* c, int n, int scheme, double tau, double sigma) 
     L.dst = c->f[d];
     L.rho_src = c->rho[s];
     L.rho_dst = c->rho[d];
-    cudaError_t e = strip_launch(c->p.precision, scheme, kStepMode, L, grid, c->stream);
+    const int variant = pick_variant(c, kStepMode);
+    cudaError_t e =
+        variant == LBM_VARIANT_STAGED
+            ? strip_tma_launch(c->p.precision, scheme, L, grid, c->stream)
+            : variant == LBM_VARIANT_PAIR
+                  ? strip2_launch(c->p.precision, scheme, kStepMode, L, grid, c->stream)
+                  : strip_launch(c->p.precision, scheme, kStepMode, L, grid, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
     c->cur = d;
   }
@@ -431,6 +489,11 @@ lbm_status lbm_sync_status(lbm_ctx* c) {
   LBM_CUDA(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(unsigned),
                               cudaMemcpyDeviceToHost, c->stream));
   LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (*c->h_status & kStatusTimeoutFlag) {
+    cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream);
+    cudaStreamSynchronize(c->stream);
+    return fail(c, LBM_E_TIMEOUT, "a bounded wait for staged rows gave up");
+  }
   if (*c->h_status & kStatusDivergedFlag)
     return fail(c, LBM_E_DIVERGED, "density left the domain of psi");
   return LBM_OK;
@@ -459,7 +522,10 @@ lbm_status lbm_get_moments(lbm_ctx* c, double* rho, double* vx, double* vy) {
   st = geometry(c, LBM_SCHEME_SC, mode, L, grid);
   if (st != LBM_OK) return st;
   LBM_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream));
-  LBM_CUDA(c, strip_launch(c->p.precision, LBM_SCHEME_SC, mode, L, grid, c->stream));
+  if (pick_variant(c, mode) == LBM_VARIANT_PAIR)
+    LBM_CUDA(c, strip2_launch(c->p.precision, LBM_SCHEME_SC, mode, L, grid, c->stream));
+  else
+    LBM_CUDA(c, strip_launch(c->p.precision, LBM_SCHEME_SC, mode, L, grid, c->stream));
   count_launches(1);
   const size_t bytes = c->plane * sizeof(double);
   if (rho) LBM_CUDA(c, cudaMemcpyAsync(rho, L.out_rho, bytes, cudaMemcpyDeviceToHost, c->stream));
@@ -514,6 +580,14 @@ lbm_status lbm_set_populations(lbm_ctx* c, const double* f) {
 }
 
 unsigned long long lbm_kernel_launch_count(void) { return g_launches.load(); }
+
+lbm_status lbm_set_kernel_variant(lbm_ctx* c, int variant) {
+  if (!c) return LBM_E_INVAL;
+  if (variant < LBM_VARIANT_AUTO || variant > LBM_VARIANT_PAIR)
+    return fail(c, LBM_E_INVAL, "unknown kernel variant");
+  c->variant = variant;
+  return LBM_OK;
+}
 
 lbm_status lbm_set_band_rows(lbm_ctx* c, int band_rows) {
   if (!c) return LBM_E_INVAL;

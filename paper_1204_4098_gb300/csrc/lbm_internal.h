@@ -45,6 +45,15 @@ cudaError_t strip_launch(int precision, int scheme, int mode, const StripLaunch&
                          int grid, cudaStream_t s);
 // Resident CTAs per SM of that kernel.
 cudaError_t strip_occupancy(int precision, int scheme, int mode, int* blocks_per_sm);
+// Two-columns-per-lane kernel (direct storage FP32 / FP64; needs even nx;
+// L.n_strips counts 64-column strips).
+cudaError_t strip2_launch(int precision, int scheme, int mode, const StripLaunch& L, int grid,
+                          cudaStream_t s);
+cudaError_t strip2_occupancy(int precision, int scheme, int mode, int* blocks_per_sm);
+// Bulk-copy staged step kernel (FP32 only; needs nx % 4 == 0 and nx >= 64).
+cudaError_t strip_tma_launch(int precision, int scheme, const StripLaunch& L, int grid,
+                             cudaStream_t s);
+cudaError_t strip_tma_occupancy(int precision, int scheme, int* blocks_per_sm);
 
 // f*_a(x') = f_a(x' + e_a) from f_eq(rho, u) (f_in == NULL) or from f_in;
 // with f_in == NULL and chk.status set, flags rho outside the domain of psi.

@@ -261,6 +261,426 @@ strip_kernel(const StripArgs<S> A) {
 }
 
 // ---------------------------------------------------------------------------
+// Two columns per lane (direct storage, even nx)
+// ---------------------------------------------------------------------------
+// The same computation with lane l owning columns x0 + 2l and x0 + 2l + 1 of
+// a 64-column strip: populations move as 8-byte (float2 / double2) vectors,
+// and the per-row overhead (indices, halo psi, shuffles, loop control) is
+// shared by two cells.  A pull with e_x = +1 takes the left cell's value from
+// the previous lane's upper element (shuffle), e_x = -1 the right cell's from
+// the next lane's lower element; the strip's two boundary lanes get those
+// elements, and the halo densities, from one extra load spread over lanes
+// 0-11 (left) and 16-27 (right).  Every per-cell expression is the one of
+// strip_run, so results are bit-identical.
+template <class T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+template <class S, int SCHEME, int MODE>
+__device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int band,
+                                           int lane) {
+  using C = typename S::C;
+  using T = typename S::T;
+  using V = typename Vec2<T>::type;
+  static_assert(!S::kDev, "two-column variant is for direct storage");
+  constexpr bool kNeedPsi = !(MODE == kModeObserveNoForce ||
+                              (MODE == kModeStep && SCHEME == kNoForce));
+  const unsigned FULL = 0xffffffffu;
+  const int nx = A.nx, ny = A.ny;
+  const int y0 = band * A.band_rows;
+  const int y1 = min(y0 + A.band_rows, ny);
+  const int x0 = strip * 64;
+  const int xa = x0 + 2 * lane;         // left column of this lane
+  const bool active_a = xa < nx, active_b = xa + 1 < nx;
+  const int ca = xa % nx;               // even: nx is even
+  // extra-element lanes: 0..8 halo pulls of column x0-1 (plane = lane),
+  // 9..11 column x0-1 of planes 1, 5, 8 (e_x = +1), 16..24 halo pulls of
+  // column x0+64 (plane = lane-16), 25..27 column x0+64 of planes 3, 6, 7.
+  const int q = lane & 15;
+  const bool left = lane < 16;
+  const int hcol = left ? (x0 - 1 + nx) % nx : (x0 + 64) % nx;
+  int qa, qsx;   // plane and source column of this lane's extra element
+  bool qlane = true;
+  if (q < kQ) {
+    qa = q;
+    qsx = ((hcol - c_ex[q]) % nx + nx) % nx;
+  } else if (q < 12) {
+    qa = left ? (q == 9 ? 1 : (q == 10 ? 5 : 8)) : (q == 9 ? 3 : (q == 10 ? 6 : 7));
+    qsx = hcol;
+  } else {
+    qa = 0;
+    qsx = 0;
+    qlane = false;
+  }
+  const int qey = c_ey[qa];
+  const int hbase = lane & 16;
+  bool bad = false;
+
+  // pulled populations of row y for both cells, plus this lane's extra element
+  auto load_row = [&](int y, C (&PA)[kQ], C (&PB)[kQ], C& h) {
+    const int ym = y == 0 ? ny - 1 : y - 1;
+    const int yp = y == ny - 1 ? 0 : y + 1;
+    const int rows[3] = {ym, y, yp};
+    {
+      int qy = y - qey;
+      qy = qy < 0 ? qy + ny : (qy >= ny ? qy - ny : qy);
+      h = qlane ? S::to_c(__ldg(A.src + qa * A.plane + size_t(qy) * nx + qsx)) : C(0);
+    }
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) {
+      const int ex = ex_of(a), ey = ey_of(a);
+      const int r = rows[1 - ey];  // source row y - ey
+      const V v = __ldg(reinterpret_cast<const V*>(A.src + a * A.plane + size_t(r) * nx + ca));
+      if (ex == 0) {
+        PA[a] = S::to_c(v.x);
+        PB[a] = S::to_c(v.y);
+      } else if (ex == 1) {  // sources x-1: (prev lane's .y, own .x)
+        const int k = a == 1 ? 9 : (a == 5 ? 10 : 11);
+        const C fromL = __shfl_sync(FULL, h, k);
+        const C up = __shfl_up_sync(FULL, S::to_c(v.y), 1);
+        PA[a] = lane == 0 ? fromL : up;
+        PB[a] = S::to_c(v.x);
+      } else {  // sources x+1: (own .y, next lane's .x)
+        const int k = a == 3 ? 25 : (a == 6 ? 26 : 27);
+        const C fromR = __shfl_sync(FULL, h, k);
+        const C dn = __shfl_down_sync(FULL, S::to_c(v.x), 1);
+        PA[a] = S::to_c(v.y);
+        PB[a] = lane == 31 ? fromR : dn;
+      }
+    }
+  };
+  auto rho_of = [](const C (&P)[kQ]) {
+    C r = P[0];
+#pragma unroll
+    for (int a = 1; a < kQ; ++a) r = add_rn(r, P[a]);
+    return r;
+  };
+  // psi of the row's cells; Wa = psi(xa - 1), Eb = psi(xa + 2)
+  auto psi_row = [&](const C (&PA)[kQ], const C (&PB)[kQ], C h, C& Wa, C& Ca, C& Cb, C& Eb,
+                     C& ra, C& rb) {
+    ra = rho_of(PA);
+    rb = rho_of(PB);
+    if constexpr (kNeedPsi) {
+      Ca = psi_of_rho(ra, A.P, bad);
+      Cb = psi_of_rho(rb, A.P, bad);
+      C hr = __shfl_sync(FULL, h, hbase);
+#pragma unroll
+      for (int a = 1; a < kQ; ++a) hr = add_rn(hr, __shfl_sync(FULL, h, hbase + a));
+      const C hp = psi_of_rho(hr, A.P, bad);
+      Wa = __shfl_up_sync(FULL, Cb, 1);
+      Eb = __shfl_down_sync(FULL, Ca, 1);
+      if (lane == 0) Wa = hp;
+      if (lane == 31) Eb = hp;
+    }
+  };
+  auto force = [&](C Wm, C Cm, C Em, C Wz, C Cz, C Ez, C Wp, C Cp, C Ep, C& Fx, C& Fy) {
+    const C third = C(1) / C(3), twelfth = C(1) / C(12);
+    const C sx = fma_rn(third, sub_rn(Ez, Wz),
+                        mul_rn(twelfth, add_rn(sub_rn(Ep, Wp), sub_rn(Em, Wm))));
+    const C sy = fma_rn(third, sub_rn(Cp, Cm),
+                        mul_rn(twelfth, sub_rn(add_rn(Ep, Wp), add_rn(Em, Wm))));
+    const C gpsi = mul_rn(A.P.minus_G, Cz);
+    Fx = mul_rn(gpsi, sx);
+    Fy = mul_rn(gpsi, sy);
+  };
+
+  C PA0[kQ], PB0[kQ], PA1[kQ], PB1[kQ], PA2[kQ], PB2[kQ];
+  C h1 = C(0), h2 = C(0);
+  // psi ring per row: (Wa, Ca, Cb, Eb) for rows y-1 (m), y (z)
+  C Wam = 0, Cam = 0, Cbm = 0, Ebm = 0, Waz = 0, Caz = 0, Cbz = 0, Ebz = 0;
+  C ra0, rb0;
+  {
+    C rda, rdb;
+    load_row(y0 == 0 ? ny - 1 : y0 - 1, PA0, PB0, h1);
+    psi_row(PA0, PB0, h1, Wam, Cam, Cbm, Ebm, rda, rdb);
+    load_row(y0, PA0, PB0, h1);
+    psi_row(PA0, PB0, h1, Waz, Caz, Cbz, Ebz, ra0, rb0);
+    load_row(y0 + 1 == ny ? 0 : y0 + 1, PA1, PB1, h1);
+  }
+  for (int y = y0; y < y1; ++y) {
+    if (y + 2 <= y1) load_row(y + 2 >= ny ? y + 2 - ny : y + 2, PA2, PB2, h2);
+    C Wap = 0, Cap = 0, Cbp = 0, Ebp = 0, ra1, rb1;
+    psi_row(PA1, PB1, h1, Wap, Cap, Cbp, Ebp, ra1, rb1);
+    C Fxa = C(0), Fya = C(0), Fxb = C(0), Fyb = C(0);
+    if constexpr (kNeedPsi) {
+      force(Wam, Cam, Cbm, Waz, Caz, Cbz, Wap, Cap, Cbp, Fxa, Fya);
+      force(Cam, Cbm, Ebm, Caz, Cbz, Ebz, Cap, Cbp, Ebp, Fxb, Fyb);
+    }
+    const size_t idx = size_t(y) * nx + ca;
+    if constexpr (MODE == kModeStep) {
+      collide<C, SCHEME>(PA0, ra0, Fxa, Fya, Caz, A.P);
+      collide<C, SCHEME>(PB0, rb0, Fxb, Fyb, Cbz, A.P);
+      if (active_b) {
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) {
+          V v;
+          v.x = S::from_c(PA0[a]);
+          v.y = S::from_c(PB0[a]);
+          *reinterpret_cast<V*>(A.dst + a * A.plane + idx) = v;
+        }
+      } else if (active_a) {
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) A.dst[a * A.plane + idx] = S::from_c(PA0[a]);
+      }
+    } else {
+      auto out = [&](const C (&P)[kQ], C r0, C Fx, C Fy, size_t i) {
+        const C jx = (P[1] - P[3]) + (P[5] - P[6]) + (P[8] - P[7]);
+        const C jy = (P[2] - P[4]) + (P[5] + P[6]) - (P[7] + P[8]);
+        const double r = double(r0);
+        A.out_rho[i] = r;
+        A.out_vx[i] = (double(jx) + 0.5 * double(Fx)) / r;
+        A.out_vy[i] = (double(jy) + 0.5 * double(Fy)) / r;
+      };
+      if (active_a) out(PA0, ra0, Fxa, Fya, idx);
+      if (active_b) out(PB0, rb0, Fxb, Fyb, idx + 1);
+    }
+    Wam = Waz; Cam = Caz; Cbm = Cbz; Ebm = Ebz;
+    Waz = Wap; Caz = Cap; Cbz = Cbp; Ebz = Ebp;
+    ra0 = ra1;
+    rb0 = rb1;
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) {
+      PA0[a] = PA1[a]; PB0[a] = PB1[a];
+      PA1[a] = PA2[a]; PB1[a] = PB2[a];
+    }
+    h1 = h2;
+  }
+  if (__any_sync(FULL, bad) && lane == 0) atomicOr(A.status, kStatusDiverged);
+}
+
+#ifndef LBM_STRIP2_MIN_BLOCKS
+#define LBM_STRIP2_MIN_BLOCKS 5
+#endif
+
+template <class S, int SCHEME, int MODE>
+__global__ void __launch_bounds__(kStripThreads, LBM_STRIP2_MIN_BLOCKS)
+strip2_kernel(const StripArgs<S> A) {
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * kStripThreads + threadIdx.x) >> 5;
+  const int strip = gwarp % A.n_strips;  // n_strips counts 64-column strips here
+  const int band = gwarp / A.n_strips;
+  if (band >= A.n_bands) return;
+  strip_run2<S, SCHEME, MODE>(A, strip, band, lane);
+}
+
+// ---------------------------------------------------------------------------
+// Bulk-copy staged variant (FP32 direct storage, nx % 4 == 0, nx >= 64)
+// ---------------------------------------------------------------------------
+// The same warp-strip computation, but the rows a warp needs are brought into
+// shared memory by the copy engine (cp.async.bulk, completion counted in
+// bytes on an mbarrier) up to kTmaStages rows ahead, instead of being held in
+// registers: more bytes in flight per SM at fewer registers, and one copy
+// instruction per plane-row instead of per-lane address arithmetic.
+//
+// Stage layout: for each plane a, the 40 floats of source row (r - ey_a) at
+// columns x0-4 .. x0+35 (16-byte aligned; covers the pulls of the 32 lanes
+// and of both halo columns).  At the domain's left/right edge the periodic
+// part comes from a second copy.  Pulled value of lane l, plane a:
+// stage[a][4 + l - ex_a]; left halo stage[a][3 - ex_a]; right stage[a][36 - ex_a].
+constexpr int kTmaStages = 4;
+constexpr int kTmaSpan = 40;
+constexpr unsigned kTmaStageBytes = kQ * kTmaSpan * 4;  // 1440
+constexpr long long kTmaSpinLimit = 1ll << 20;           // bounded waits
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return unsigned(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned phase) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(float* dst, const float* src, unsigned bytes,
+                                         unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+template <int SCHEME>
+__global__ void __launch_bounds__(kStripThreads, 8)
+strip_tma_kernel(const StripArgs<StoreF32> A) {
+  using C = float;
+  __shared__ __align__(128) float s_stage[kStripWarpsPerCta][kTmaStages][kQ][kTmaSpan];
+  __shared__ __align__(8) unsigned long long s_bar[kStripWarpsPerCta][kTmaStages];
+  constexpr bool kNeedPsi = SCHEME != kNoForce;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int gwarp = (blockIdx.x * kStripThreads + threadIdx.x) >> 5;
+  const int strip = gwarp % A.n_strips;
+  const int band = gwarp / A.n_strips;
+  if (band >= A.n_bands) return;  // warp-uniform
+  const int nx = A.nx, ny = A.ny;
+  const int y0 = band * A.band_rows;
+  const int y1 = min(y0 + A.band_rows, ny);
+  const int x0 = strip * 32;
+  const bool active = x0 + lane < nx;
+  float(*stage)[kQ][kTmaSpan] = s_stage[wib];
+  unsigned long long* bar = s_bar[wib];
+  if (lane == 0) {
+    for (int d = 0; d < kTmaStages; ++d) mbar_init(&bar[d], 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
+
+  // pulled rows r = y0-1 .. y1 (n_rows of them) go through the stages in turn
+  const int n_rows = y1 - y0 + 2;
+  const int ha = lane & 15;
+  const bool hlane = ha < kQ;
+  const int hoff = lane < 16 ? 3 - c_ex[ha] : 36 - c_ex[ha];
+  const int hbase = lane & 16;
+  unsigned phase = 0u;  // bit d: parity to wait for on stage d
+  unsigned pending = 0u;
+  bool bad = false, timed_out = false;
+
+  auto issue = [&](int k) {  // pulled row y0 - 1 + k into stage k % kTmaStages
+    const int d = k % kTmaStages;
+    if (lane == 0) mbar_expect_tx(&bar[d], kTmaStageBytes);
+    __syncwarp();
+    if (lane < kQ) {
+      int sr = y0 - 1 + k - c_ey[lane];
+      sr = sr < 0 ? sr + ny : (sr >= ny ? sr - ny : sr);
+      sr = sr < 0 ? sr + ny : (sr >= ny ? sr - ny : sr);
+      const float* row = A.src + size_t(lane) * A.plane + size_t(sr) * nx;
+      float* dst = stage[d][lane];
+      const int lo = x0 - 4, hi = x0 + 36;
+      if (lo < 0) {
+        bulk_g2s(dst, row + nx - 4, 16, &bar[d]);
+        bulk_g2s(dst + 4, row, 144, &bar[d]);
+      } else if (hi > nx) {
+        const int n1 = nx - lo;
+        bulk_g2s(dst, row + lo, unsigned(n1) * 4u, &bar[d]);
+        bulk_g2s(dst + n1, row, unsigned(kTmaSpan - n1) * 4u, &bar[d]);
+      } else {
+        bulk_g2s(dst, row + lo, kTmaSpan * 4u, &bar[d]);
+      }
+    }
+    pending |= 1u << d;
+  };
+  auto wait = [&](int k) {
+    const int d = k % kTmaStages;
+    bool ok = false;
+    for (long long it = 0; it < kTmaSpinLimit && !ok; ++it)
+      ok = __any_sync(FULL, mbar_try_wait(&bar[d], (phase >> d) & 1u));
+    if (ok) {
+      phase ^= 1u << d;
+      pending &= ~(1u << d);
+    }
+    return ok;
+  };
+  auto pulled = [&](int k, C (&P)[kQ], C& h) {
+    const int d = k % kTmaStages;
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) P[a] = stage[d][a][4 + lane - ex_of(a)];
+    if constexpr (kNeedPsi) h = hlane ? stage[d][ha][hoff] : C(0);
+  };
+  auto rho_of = [](const C (&P)[kQ]) {
+    C r = P[0];
+#pragma unroll
+    for (int a = 1; a < kQ; ++a) r = add_rn(r, P[a]);
+    return r;
+  };
+  auto psi_row = [&](const C (&P)[kQ], C h, C& Wv, C& Cv, C& Ev, C& rho_out) {
+    rho_out = rho_of(P);
+    if constexpr (kNeedPsi) {
+      Cv = psi_of_rho(rho_out, A.P, bad);
+      C hr = __shfl_sync(FULL, h, hbase);
+#pragma unroll
+      for (int a = 1; a < kQ; ++a) hr = add_rn(hr, __shfl_sync(FULL, h, hbase + a));
+      const C hp = psi_of_rho(hr, A.P, bad);
+      Wv = __shfl_up_sync(FULL, Cv, 1);
+      Ev = __shfl_down_sync(FULL, Cv, 1);
+      if (lane == 0) Wv = hp;
+      if (lane == 31) Ev = hp;
+    }
+  };
+
+  for (int k = 0; k < kTmaStages && k < n_rows; ++k) issue(k);
+  C Wm = 0, Cm = 0, Em = 0, Wz = 0, Cz = 0, Ez = 0, rho0 = 0, hdummy = 0, rdummy;
+  C Pcur[kQ], Pnext[kQ];
+  // prologue: rows y0 - 1 (k = 0) and y0 (k = 1)
+  if (!wait(0)) timed_out = true;
+  if (!timed_out) {
+    pulled(0, Pnext, hdummy);
+    psi_row(Pnext, hdummy, Wm, Cm, Em, rdummy);
+    __syncwarp();
+    if (kTmaStages < n_rows) issue(kTmaStages);
+  }
+  if (!timed_out && !wait(1)) timed_out = true;
+  if (!timed_out) {
+    C h;
+    pulled(1, Pcur, h);
+    psi_row(Pcur, h, Wz, Cz, Ez, rho0);
+    __syncwarp();
+    if (kTmaStages + 1 < n_rows) issue(kTmaStages + 1);
+  }
+  for (int y = y0; y < y1 && !timed_out; ++y) {
+    const int k = y - y0 + 2;  // pulled row y + 1
+    if (!wait(k)) {
+      timed_out = true;
+      break;
+    }
+    C h, Wp = 0, Cp = 0, Ep = 0, rho1;
+    pulled(k, Pnext, h);
+    psi_row(Pnext, h, Wp, Cp, Ep, rho1);
+    __syncwarp();
+    if (k + kTmaStages < n_rows) issue(k + kTmaStages);
+
+    C Fx = C(0), Fy = C(0);
+    if constexpr (kNeedPsi) {
+      const C third = C(1) / C(3), twelfth = C(1) / C(12);
+      const C sx = fma_rn(third, sub_rn(Ez, Wz),
+                          mul_rn(twelfth, add_rn(sub_rn(Ep, Wp), sub_rn(Em, Wm))));
+      const C sy = fma_rn(third, sub_rn(Cp, Cm),
+                          mul_rn(twelfth, sub_rn(add_rn(Ep, Wp), add_rn(Em, Wm))));
+      const C gpsi = mul_rn(A.P.minus_G, Cz);
+      Fx = mul_rn(gpsi, sx);
+      Fy = mul_rn(gpsi, sy);
+    }
+    collide<C, SCHEME>(Pcur, rho0, Fx, Fy, Cz, A.P);
+    if (active) {
+      const int idx = y * nx + x0 + lane;
+#pragma unroll
+      for (int a = 0; a < kQ; ++a) A.dst[a * A.plane + idx] = Pcur[a];
+    }
+    Wm = Wz; Cm = Cz; Em = Ez;
+    Wz = Wp; Cz = Cp; Ez = Ep;
+    rho0 = rho1;
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) Pcur[a] = Pnext[a];
+  }
+  if (timed_out) {
+    // drain this warp's copies still in flight (bounded), then report
+    for (int d = 0; d < kTmaStages; ++d) {
+      if (!((pending >> d) & 1u)) continue;
+      for (long long it = 0; it < kTmaSpinLimit; ++it)
+        if (__any_sync(FULL, mbar_try_wait(&bar[d], (phase >> d) & 1u))) break;
+    }
+    if (lane == 0) atomicOr(A.status, kStatusTimeout);
+  }
+  if (__any_sync(FULL, bad) && lane == 0) atomicOr(A.status, kStatusDiverged);
+}
+
+// ---------------------------------------------------------------------------
 // initialisation and checkpoint kernels (not on the per-step path)
 // ---------------------------------------------------------------------------
 

@@ -1,6 +1,8 @@
 // Launch helpers shared by the per-precision kernel translation units.
 #pragma once
 
+#include <type_traits>
+
 #include "lbm_internal.h"
 #include "lbm_kernels.cuh"
 
@@ -80,6 +82,92 @@ cudaError_t strip_occupancy_t(int scheme, int mode, int* b) {
   return cudaErrorInvalidValue;
 }
 
+// Bulk-copy staged step kernel: FP32 direct storage only.
+template <class S>
+cudaError_t strip_tma_launch_t(int scheme, const StripLaunch& L, int grid, cudaStream_t s) {
+  if constexpr (!std::is_same<S, StoreF32>::value) {
+    return cudaErrorNotSupported;
+  } else {
+    const StripArgs<S> A = make_args<S>(L);
+    switch (scheme) {
+      case kSC: strip_tma_kernel<kSC><<<grid, kStripThreads, 0, s>>>(A); break;
+      case kEDM: strip_tma_kernel<kEDM><<<grid, kStripThreads, 0, s>>>(A); break;
+      case kImproved: strip_tma_kernel<kImproved><<<grid, kStripThreads, 0, s>>>(A); break;
+      case kNoForce: strip_tma_kernel<kNoForce><<<grid, kStripThreads, 0, s>>>(A); break;
+      case kEDMMod: strip_tma_kernel<kEDMMod><<<grid, kStripThreads, 0, s>>>(A); break;
+      case kLadd: strip_tma_kernel<kLadd><<<grid, kStripThreads, 0, s>>>(A); break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
+}
+
+template <class S>
+cudaError_t strip_tma_occupancy_t(int scheme, int* b) {
+  if constexpr (!std::is_same<S, StoreF32>::value) {
+    return cudaErrorNotSupported;
+  } else {
+    switch (scheme) {
+      case kSC: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, strip_tma_kernel<kSC>, kStripThreads, 0);
+      case kEDM: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, strip_tma_kernel<kEDM>, kStripThreads, 0);
+      case kImproved: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, strip_tma_kernel<kImproved>, kStripThreads, 0);
+      case kNoForce: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, strip_tma_kernel<kNoForce>, kStripThreads, 0);
+      case kEDMMod: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, strip_tma_kernel<kEDMMod>, kStripThreads, 0);
+      case kLadd: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, strip_tma_kernel<kLadd>, kStripThreads, 0);
+    }
+    return cudaErrorInvalidValue;
+  }
+}
+
+// Two-columns-per-lane kernel: direct storage (FP32, FP64) only.
+template <class S, int SCHEME, int MODE>
+cudaError_t launch2_one(const StripLaunch& L, int grid, cudaStream_t s) {
+  strip2_kernel<S, SCHEME, MODE><<<grid, kStripThreads, 0, s>>>(make_args<S>(L));
+  return cudaGetLastError();
+}
+template <class S, int SCHEME, int MODE>
+cudaError_t occ2_one(int* b) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, strip2_kernel<S, SCHEME, MODE>,
+                                                       kStripThreads, 0);
+}
+template <class S>
+cudaError_t strip2_launch_t(int scheme, int mode, const StripLaunch& L, int grid,
+                            cudaStream_t s) {
+  if constexpr (S::kDev) {
+    return cudaErrorNotSupported;
+  } else {
+    if (mode == kObserveMode) return launch2_one<S, kSC, kModeObserve>(L, grid, s);
+    if (mode == kObserveNoForceMode) return launch2_one<S, kSC, kModeObserveNoForce>(L, grid, s);
+    switch (scheme) {
+      case kSC: return launch2_one<S, kSC, kModeStep>(L, grid, s);
+      case kEDM: return launch2_one<S, kEDM, kModeStep>(L, grid, s);
+      case kImproved: return launch2_one<S, kImproved, kModeStep>(L, grid, s);
+      case kNoForce: return launch2_one<S, kNoForce, kModeStep>(L, grid, s);
+      case kEDMMod: return launch2_one<S, kEDMMod, kModeStep>(L, grid, s);
+      case kLadd: return launch2_one<S, kLadd, kModeStep>(L, grid, s);
+    }
+    return cudaErrorInvalidValue;
+  }
+}
+template <class S>
+cudaError_t strip2_occupancy_t(int scheme, int mode, int* b) {
+  if constexpr (S::kDev) {
+    return cudaErrorNotSupported;
+  } else {
+    if (mode == kObserveMode) return occ2_one<S, kSC, kModeObserve>(b);
+    if (mode == kObserveNoForceMode) return occ2_one<S, kSC, kModeObserveNoForce>(b);
+    switch (scheme) {
+      case kSC: return occ2_one<S, kSC, kModeStep>(b);
+      case kEDM: return occ2_one<S, kEDM, kModeStep>(b);
+      case kImproved: return occ2_one<S, kImproved, kModeStep>(b);
+      case kNoForce: return occ2_one<S, kNoForce, kModeStep>(b);
+      case kEDMMod: return occ2_one<S, kEDMMod, kModeStep>(b);
+      case kLadd: return occ2_one<S, kLadd, kModeStep>(b);
+    }
+    return cudaErrorInvalidValue;
+  }
+}
+
 inline int grid_for(size_t n, int threads) {
   size_t g = (n + threads - 1) / threads;
   if (g > 65535u * 8u) g = 65535u * 8u;
@@ -131,6 +219,20 @@ cudaError_t mass_t(const void* src, const float* rho_src, size_t plane, double* 
   }                                                                                     \
   cudaError_t strip_occupancy_##SUFFIX(int scheme, int mode, int* b) {                  \
     return strip_occupancy_t<STORE>(scheme, mode, b);                                   \
+  }                                                                                     \
+  cudaError_t strip2_launch_##SUFFIX(int scheme, int mode, const StripLaunch& L, int grid, \
+                                     cudaStream_t s) {                                  \
+    return strip2_launch_t<STORE>(scheme, mode, L, grid, s);                            \
+  }                                                                                     \
+  cudaError_t strip2_occupancy_##SUFFIX(int scheme, int mode, int* b) {                 \
+    return strip2_occupancy_t<STORE>(scheme, mode, b);                                  \
+  }                                                                                     \
+  cudaError_t strip_tma_launch_##SUFFIX(int scheme, const StripLaunch& L, int grid,      \
+                                        cudaStream_t s) {                               \
+    return strip_tma_launch_t<STORE>(scheme, L, grid, s);                               \
+  }                                                                                     \
+  cudaError_t strip_tma_occupancy_##SUFFIX(int scheme, int* b) {                        \
+    return strip_tma_occupancy_t<STORE>(scheme, b);                                     \
   }                                                                                     \
   cudaError_t set_state_##SUFFIX(void* dst, float* rd, int nx, int ny, size_t plane,     \
                                  const double* rho, const double* ux, const double* uy, \

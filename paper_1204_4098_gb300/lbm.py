@@ -23,6 +23,7 @@ STATUS_NAMES = {0: "LBM_OK", 1: "LBM_E_INVAL", 2: "LBM_E_NOMEM", 3: "LBM_E_CUDA"
                 4: "LBM_E_DIVERGED", 5: "LBM_E_TIMEOUT", 6: "LBM_E_STATE"}
 SC, EDM, IMPROVED, NOFORCE, EDM_MOD, LADD = range(6)
 FP32, FP64, BF16DEV, FP16DEV = range(4)
+VARIANT_AUTO, VARIANT_REGISTER, VARIANT_STAGED, VARIANT_PAIR = range(4)
 
 
 class lbm_params(ctypes.Structure):
@@ -95,6 +96,7 @@ SIGNATURES = {
     "lbm_cs_maxwell": (_I, [_D, _D, _D, _D, _DP, _DP, _DP]),
     "lbm_kernel_launch_count": (ctypes.c_ulonglong, []),
     "lbm_set_band_rows": (_I, [_P, _I]),
+    "lbm_set_kernel_variant": (_I, [_P, _I]),
     "lbm_get_launch_geometry": (_I, [_P, _I, _IP, _IP, _IP, _IP]),
     "lbm_mass_f32_noalloc": (_I, [_P, ctypes.c_size_t, _P, _P]),
     "lbm_batch_default_params": (None, [ctypes.POINTER(lbm_batch_params)]),
@@ -275,6 +277,10 @@ class Lattice:
         f = np.ascontiguousarray(f, dtype=np.float64)
         assert f.shape == (9, self.ny, self.nx)
         self._check(lib().lbm_set_populations(self.ctx, _dptr(f)), "lbm_set_populations")
+
+    def set_variant(self, variant):
+        self._check(lib().lbm_set_kernel_variant(self.ctx, int(variant)),
+                    "lbm_set_kernel_variant")
 
     def set_band_rows(self, rows):
         self._check(lib().lbm_set_band_rows(self.ctx, int(rows)), "lbm_set_band_rows")
