@@ -38,12 +38,17 @@ sys.path.insert(0, ROOT)
 METRIC = "D2Q9 pseudopotential MLUPS & % HBM roofline; batched sweep; warm-start speedup"
 BYTES_PER_CELL = {"fp32": 72, "fp64": 144, "bf16dev": 44, "fp16dev": 44}
 KERNEL_SOURCES = ["lbm_device.cuh", "lbm_kernels.cuh", "lbm_launch.cuh"]
+STORE_NAMES = {"fp32": "StoreF32", "fp64": "StoreF64", "bf16dev": "StoreBF16",
+               "fp16dev": "StoreF16"}
 # DRAM bytes per launch of the step kernel from an ncu capture, keyed by the
 # hash of the kernel sources it was taken on (null once they change).
 MEASURED_TRAFFIC = {
     # ncu launch list, 25 launches of strip_kernel<StoreF32, improved, step> at
     # 8192^2: 2.437 GB read + 2.370 GB written per launch
     ("8a40f73e27882b9d", "fp32", 8192): 4.807e9,
+    # ncu launch list, 25 launches of strip2_kernel<StoreF32, improved, step>
+    # at 8192^2: 2.431 GB read + 2.368 GB written per launch
+    ("c8b20c715c92ee44", "fp32", 8192): 4.7996e9,
 }
 
 
@@ -250,6 +255,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     dist_barrier(world)
     launches = lbm.launch_count() - launches0
+    variant_used = lat.variant()
     ms = start.elapsed_time(end)
     assert lat.sync() == lbm.LBM_OK
     clocks = sampler.stop()
@@ -263,7 +269,9 @@ def run_ours(args, world, rank, local):
     traffic = MEASURED_TRAFFIC.get((kernel_source_hash(), args.precision, n))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "strip_kernel<Store, improved, step>",
+                "kernel": {lbm.VARIANT_PAIR: "strip2_kernel", lbm.VARIANT_STAGED:
+                           "strip_tma_kernel"}.get(variant_used, "strip_kernel")
+                + f"<{STORE_NAMES[args.precision]}, improved, step>",
                 "algorithmic_bytes_per_launch": bpc * cells,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s"}

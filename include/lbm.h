@@ -160,12 +160,13 @@ unsigned long long lbm_kernel_launch_count(void);
 
 /* Step kernel variant; all give bit-identical results.  REGISTER: one column
  * per lane, rows loaded into registers one row ahead.  PAIR: two adjacent
- * columns per lane (8-byte vector loads and stores), for FP32/FP64 storage
- * with even nx.  STAGED: one column per lane, rows brought into shared
+ * columns per lane (vector loads and stores of two populations), for even
+ * nx.  STAGED: one column per lane, rows brought into shared
  * memory by asynchronous bulk copies several rows ahead (FP32 steps with
  * nx % 4 == 0 and nx >= 64; a bounded wait that gives up makes lbm_step
- * return LBM_E_TIMEOUT).  AUTO (default) = PAIR for FP32 with even nx, else
- * REGISTER.  A variant that does not apply falls back to REGISTER. */
+ * return LBM_E_TIMEOUT).  AUTO (default) = PAIR for even nx except with FP64
+ * storage, else REGISTER.  A variant that does not apply falls back to
+ * REGISTER. */
 enum { LBM_VARIANT_AUTO = 0, LBM_VARIANT_REGISTER = 1, LBM_VARIANT_STAGED = 2,
        LBM_VARIANT_PAIR = 3 };
 lbm_status lbm_set_kernel_variant(lbm_ctx *ctx, int variant);
@@ -174,10 +175,15 @@ lbm_status lbm_set_kernel_variant(lbm_ctx *ctx, int variant);
  * at least 8 rows each).  Changes only speed, never results. */
 lbm_status lbm_set_band_rows(lbm_ctx *ctx, int band_rows);
 
-/* The launch geometry lbm_step would use for `scheme`: 32-column strips,
- * rows per band, bands, and CTAs of 128 threads. */
+/* The launch geometry lbm_step would use for `scheme`: column strips (32
+ * columns wide, 64 with the PAIR variant), rows per band, bands, and CTAs of
+ * 128 threads. */
 lbm_status lbm_get_launch_geometry(lbm_ctx *ctx, int scheme, int *n_strips,
                                    int *band_rows, int *n_bands, int *grid);
+
+/* The kernel variant lbm_step resolves to (REGISTER, STAGED or PAIR) for the
+ * context's storage type, lattice width and requested variant. */
+lbm_status lbm_get_kernel_variant(lbm_ctx *ctx, int *variant);
 
 /* ---- batched parameter sweeps ------------------------------------------- */
 /*
@@ -228,6 +234,9 @@ typedef struct {
                            _PERSISTENT                                         */
   int rows_per_item;    /* band height of a work-list item; 0 = autotuned      */
   int conv;             /* LBM_CONV_COEX (default) or LBM_CONV_CELL             */
+  int variant;          /* LBM_VARIANT_AUTO (default) or _PAIR: two columns per
+                           lane for even nx; _REGISTER: one column per lane for
+                           every instance.  Results are identical.             */
 } lbm_batch_params;
 
 typedef struct {

@@ -1,9 +1,10 @@
 // Batched parameter sweeps: many independent FP32 lattices advanced together.
 //
-// Every instance runs the fused step body of the single-domain kernel
-// (strip_run in lbm_kernels.cuh) on its own slice of one packed buffer pair.
+// Every instance runs the fused step body of the single-domain kernels
+// (strip_run2, two columns per lane, for even nx, else strip_run; both in
+// lbm_kernels.cuh) on its own slice of one packed buffer pair.
 // A window of `window` steps is one CUDA graph, in one of two launch modes:
-//   work list   -- one launch per step; warps take 32-column x band items of
+//   work list   -- one launch per step; warps take strip x band items of
 //                  all active instances from a prefix table (balanced for any
 //                  mix of sizes);
 //   persistent  -- one launch per window; each CTA owns whole instances
@@ -20,7 +21,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <numeric>
+#include <tuple>
 #include <queue>
 #include <string>
 #include <vector>
@@ -34,7 +37,8 @@ namespace lbm {
 struct BatchInst {
   size_t off;              // element offset of plane 0 in each population buffer
   size_t coff;             // cell offset in the density snapshot
-  int nx, ny, n_strips;
+  int nx, ny, n_strips;     // strips of 64 columns (pair) or 32
+  int pair;                // even nx: two columns per lane (strip_run2)
   int band_rows, n_bands;  // work-list geometry
   int pband_rows, pn_bands;  // persistent geometry
   int scheme;
@@ -50,6 +54,9 @@ struct BatchOut {
 };
 
 constexpr int kWorklistThreads = 128;
+#ifndef LBM_BATCH_PAIR_MIN_BLOCKS
+#define LBM_BATCH_PAIR_MIN_BLOCKS 4  // CTAs per SM of the two-column work list (128 registers)
+#endif
 constexpr int kPersistentThreads = 256;
 constexpr int kReduceCta = 256;
 
@@ -73,33 +80,51 @@ __device__ __forceinline__ StripArgs<StoreF32> inst_args(const BatchInst& I, con
   return A;
 }
 
-template <bool kCoherent>
-__device__ __forceinline__ void run_item(const StripArgs<StoreF32>& A, int scheme, int strip,
-                                         int band, int lane) {
-  switch (scheme) {
-    case kSC: strip_run<StoreF32, kSC, kModeStep, kCoherent>(A, strip, band, lane); break;
-    case kEDM: strip_run<StoreF32, kEDM, kModeStep, kCoherent>(A, strip, band, lane); break;
-    case kImproved:
-      strip_run<StoreF32, kImproved, kModeStep, kCoherent>(A, strip, band, lane);
-      break;
-    case kNoForce: strip_run<StoreF32, kNoForce, kModeStep, kCoherent>(A, strip, band, lane); break;
-    case kEDMMod: strip_run<StoreF32, kEDMMod, kModeStep, kCoherent>(A, strip, band, lane); break;
-    case kLadd: strip_run<StoreF32, kLadd, kModeStep, kCoherent>(A, strip, band, lane); break;
-  }
+template <bool kPair, int SCHEME, bool kCoherent>
+__device__ __forceinline__ void run_scheme(const StripArgs<StoreF32>& A, int strip, int band,
+                                           int lane) {
+  if constexpr (kPair)
+    strip_run2<StoreF32, SCHEME, kModeStep, kCoherent>(A, strip, band, lane);
+  else
+    strip_run<StoreF32, SCHEME, kModeStep, kCoherent>(A, strip, band, lane);
 }
 
-// One step of every active instance; warp w takes items w, w + W, ...
-__global__ void __launch_bounds__(kWorklistThreads, 5)
+template <bool kPair, bool kCoherent>
+__device__ __forceinline__ void run_item(const StripArgs<StoreF32>& A, int scheme, int strip,
+                                         int band, int lane) {
+  // two bodies: the forced schemes share one (scheme read from A.P at run
+  // time); the force-free one never evaluates psi
+  if (scheme == kNoForce)
+    run_scheme<kPair, kNoForce, kCoherent>(A, strip, band, lane);
+  else
+    run_scheme<kPair, kAnyForced, kCoherent>(A, strip, band, lane);
+}
+
+// The active list holds the two-column (even nx) instances first:
+// counts[0] of them, then the others up to counts[1] = all active.  Each
+// class has its own kernel instantiation (kPair), so neither body's register
+// allocation constrains the other's.
+__device__ __forceinline__ void class_range(const int* counts, bool pair, int& a0, int& a1) {
+  a0 = pair ? 0 : counts[0];
+  a1 = pair ? counts[0] : counts[1];
+}
+
+// One step of every active instance of one class; warp w takes items
+// w, w + W, ... of the class's range of the prefix table.
+template <bool kPair>
+__global__ void __launch_bounds__(kWorklistThreads, kPair ? LBM_BATCH_PAIR_MIN_BLOCKS : 5)
 batch_worklist_kernel(const BatchInst* __restrict__ inst, const int* __restrict__ active,
-                      const int* __restrict__ prefix, const int* __restrict__ n_active_p,
+                      const int* __restrict__ prefix, const int* __restrict__ counts,
                       const float* src, float* dst, unsigned* inst_status) {
-  const int lane = threadIdx.x & 31;
+  __shared__ StripArgs<StoreF32> args[kWorklistThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = gridDim.x * (kWorklistThreads / 32);
-  const int na = *n_active_p;
-  const int total = prefix[na];
-  for (int item = (blockIdx.x * kWorklistThreads + threadIdx.x) >> 5; item < total;
+  int a0, a1;
+  class_range(counts, kPair, a0, a1);
+  const int end = prefix[a1];
+  for (int item = prefix[a0] + ((blockIdx.x * kWorklistThreads + threadIdx.x) >> 5); item < end;
        item += nwarps) {
-    int lo = 0, hi = na;  // prefix[lo] <= item < prefix[lo + 1]
+    int lo = a0, hi = a1;  // prefix[lo] <= item < prefix[lo + 1]
     while (hi - lo > 1) {
       const int mid = (lo + hi) >> 1;
       if (prefix[mid] <= item) lo = mid; else hi = mid;
@@ -107,17 +132,24 @@ batch_worklist_kernel(const BatchInst* __restrict__ inst, const int* __restrict_
     const int i = active[lo];
     const BatchInst I = inst[i];
     const int local = item - prefix[lo];
-    const StripArgs<StoreF32> A = inst_args(I, src, dst, inst_status + i, false);
-    run_item<false>(A, I.scheme, local % I.n_strips, local / I.n_strips, lane);
+    // the item's arguments live in shared memory, like kernel parameters in
+    // the constant bank: the body reloads them instead of holding registers
+    __syncwarp();
+    if (lane == 0) args[warp] = inst_args(I, src, dst, inst_status + i, false);
+    __syncwarp();
+    run_item<kPair, false>(args[warp], I.scheme, local % I.n_strips, local / I.n_strips, lane);
   }
 }
 
-// `steps` steps of the instances this CTA owns; buffers alternate, starting
-// from buf0.  The loads bypass L1 because this kernel wrote them.
+// `steps` steps of the instances of one class this CTA owns (cta_begin and
+// cta_list of that class); buffers alternate, starting from buf0.  The loads
+// bypass L1 because this kernel wrote them.
+template <bool kPair>
 __global__ void __launch_bounds__(kPersistentThreads, 2)
 batch_persistent_kernel(const BatchInst* __restrict__ inst, const int* __restrict__ cta_begin,
                         const int* __restrict__ cta_list, int steps, float* buf0, float* buf1,
                         unsigned* inst_status) {
+  __shared__ StripArgs<StoreF32> args;
   const int k0 = cta_begin[blockIdx.x], k1 = cta_begin[blockIdx.x + 1];
   if (k0 >= k1) return;  // block-uniform
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -128,10 +160,12 @@ batch_persistent_kernel(const BatchInst* __restrict__ inst, const int* __restric
     for (int k = k0; k < k1; ++k) {
       const int i = cta_list[k];
       const BatchInst I = inst[i];
-      const StripArgs<StoreF32> A = inst_args(I, src, dst, inst_status + i, true);
+      __syncthreads();  // every warp is done with the previous instance's args
+      if (threadIdx.x == 0) args = inst_args(I, src, dst, inst_status + i, true);
+      __syncthreads();
       const int items = I.n_strips * I.pn_bands;
       for (int item = warp; item < items; item += kWarps)
-        run_item<true>(A, I.scheme, item % I.n_strips, item / I.n_strips, lane);
+        run_item<kPair, true>(args, I.scheme, item % I.n_strips, item / I.n_strips, lane);
     }
     __syncthreads();  // step s of every owned instance is complete
   }
@@ -313,7 +347,7 @@ struct lbm_batch {
   // device work tables and their pinned host staging
   int* d_active = nullptr;
   int* d_prefix = nullptr;
-  int* d_n_active = nullptr;
+  int* d_n_active = nullptr;     // {active two-column instances, all active}
   int* d_cta_begin = nullptr;
   int* d_cta_list = nullptr;
   int* h_active = nullptr;
@@ -329,8 +363,12 @@ struct lbm_batch {
   int sm_count = 0;
   int wl_grid = 0;
   int pers_grid_max = 0;
-  int pers_grid = 0;
-  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};  // indexed by mode
+  cudaStream_t side = nullptr;   // second branch of the window graph
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // window graphs by (mode, grid of the two-column kernel, grid of the
+  // one-column kernel); a grid of 0 leaves that class's kernel out
+  std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;
+  int class_items[2] = {0, 0};  // work-list items of the active instances per class
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool initialized = false;
   // current launch configuration and autotuner state
@@ -339,6 +377,8 @@ struct lbm_batch {
   std::vector<std::pair<int, int>> candidates;
   std::vector<double> cand_cost;  // ns per cell update, <0 = not measured
   size_t tuned_cells = 0;
+  double tuned_cost = 0.0;  // cost per cell update of the chosen candidate
+  double last_cost = 0.0;   // of the last window
   bool tuned = false;
   lbm_batch_stats stats{};
   std::string err;
@@ -378,23 +418,13 @@ void set_geometry(BatchInst& d, int rows) {
   d.pn_bands = (d.ny + d.pband_rows - 1) / d.pband_rows;
 }
 
-// Rebuild the active list, the work-list prefix and the persistent
-// assignment (largest instance first onto the least-loaded CTA).
-lbm_status upload_tables(lbm_batch* b) {
-  const int na = int(b->active.size());
-  int acc = 0;
-  b->h_prefix[0] = 0;
-  for (int k = 0; k < na; ++k) {
-    const BatchInst& d = b->desc[b->active[k]];
-    b->h_active[k] = b->active[k];
-    acc += d.n_strips * d.n_bands;
-    b->h_prefix[k + 1] = acc;
-  }
-  b->h_prefix[b->count + 1] = na;  // n_active rides at the end of the prefix staging
-  const int G = std::max(1, std::min(na, b->pers_grid_max));
-  b->pers_grid = G;
-  std::vector<int> order(b->active);
-  std::sort(order.begin(), order.end(), [&](int x, int y) {
+// Longest-processing-time assignment of `ids` onto at most `grid` CTAs
+// (largest instance first onto the least-loaded CTA), written as CTA ranges
+// begin[0..grid] into list starting at pos.
+void lpt_assign(const lbm_batch* b, std::vector<int> ids, int grid, int* begin, int* list,
+                int& pos) {
+  const int G = std::max(1, std::min(int(ids.size()), grid));
+  std::sort(ids.begin(), ids.end(), [&](int x, int y) {
     const size_t cx = size_t(b->desc[x].nx) * b->desc[x].ny;
     const size_t cy = size_t(b->desc[y].nx) * b->desc[y].ny;
     return cx != cy ? cx > cy : x < y;
@@ -403,28 +433,53 @@ lbm_status upload_tables(lbm_batch* b) {
   std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
   for (int c = 0; c < G; ++c) heap.push({0, c});
   std::vector<std::vector<int>> lists(G);
-  for (int i : order) {
+  for (int i : ids) {
     Load l = heap.top();
     heap.pop();
     lists[l.second].push_back(i);
     heap.push({l.first + size_t(b->desc[i].nx) * b->desc[i].ny, l.second});
   }
-  int pos = 0;
-  for (int c = 0; c <= b->pers_grid_max; ++c) {
-    b->h_cta_begin[c] = pos;
-    if (c < G)
-      for (int i : lists[c]) b->h_cta_list[pos++] = i;
+  for (int c = 0; c <= grid; ++c) {
+    begin[c] = pos;
+    if (c < G && !ids.empty())
+      for (int i : lists[c]) list[pos++] = i;
   }
+}
+
+// Rebuild the active list (two-column instances first), the work-list prefix
+// and the persistent assignment of each class.
+lbm_status upload_tables(lbm_batch* b) {
+  const int na = int(b->active.size());
+  std::vector<int> cls[2];  // [0] two columns per lane, [1] one
+  for (int i : b->active) cls[b->desc[i].pair ? 0 : 1].push_back(i);
+  int acc = 0, k = 0;
+  b->h_prefix[0] = 0;
+  for (int c = 0; c < 2; ++c)
+    for (int i : cls[c]) {
+      const BatchInst& d = b->desc[i];
+      b->h_active[k] = i;
+      acc += d.n_strips * d.n_bands;
+      b->h_prefix[++k] = acc;
+    }
+  b->class_items[0] = b->h_prefix[cls[0].size()];
+  b->class_items[1] = acc - b->class_items[0];
+  // the class counts ride at the end of the prefix staging
+  b->h_prefix[b->count + 1] = int(cls[0].size());
+  b->h_prefix[b->count + 2] = na;
+  const int span = b->pers_grid_max + 1;
+  int pos = 0;
+  for (int c = 0; c < 2; ++c)
+    lpt_assign(b, cls[c], b->pers_grid_max, b->h_cta_begin + c * span, b->h_cta_list, pos);
   LBM_BCUDA(b, cudaMemcpyAsync(b->d_inst, b->desc.data(), b->count * sizeof(BatchInst),
                                cudaMemcpyHostToDevice, b->stream));
   LBM_BCUDA(b, cudaMemcpyAsync(b->d_active, b->h_active, std::max(na, 1) * sizeof(int),
                                cudaMemcpyHostToDevice, b->stream));
   LBM_BCUDA(b, cudaMemcpyAsync(b->d_prefix, b->h_prefix, (na + 1) * sizeof(int),
                                cudaMemcpyHostToDevice, b->stream));
-  LBM_BCUDA(b, cudaMemcpyAsync(b->d_n_active, b->h_prefix + b->count + 1, sizeof(int),
+  LBM_BCUDA(b, cudaMemcpyAsync(b->d_n_active, b->h_prefix + b->count + 1, 2 * sizeof(int),
                                cudaMemcpyHostToDevice, b->stream));
   LBM_BCUDA(b, cudaMemcpyAsync(b->d_cta_begin, b->h_cta_begin,
-                               (b->pers_grid_max + 1) * sizeof(int), cudaMemcpyHostToDevice,
+                               2 * span * sizeof(int), cudaMemcpyHostToDevice,
                                b->stream));
   LBM_BCUDA(b, cudaMemcpyAsync(b->d_cta_list, b->h_cta_list, std::max(pos, 1) * sizeof(int),
                                cudaMemcpyHostToDevice, b->stream));
@@ -433,33 +488,81 @@ lbm_status upload_tables(lbm_batch* b) {
 
 // One window as a CUDA graph (captured once per mode; the kernels read the
 // active set and geometry from device memory, so the graph stays valid).
+// Grid of a class kernel for the current active set: enough CTAs for its
+// items (rounded up to a power of two, so few distinct graphs arise), at
+// most one full wave; 0 when the class has no active instance.
+int class_grid(const lbm_batch* b, int mode, int cls) {
+  if (b->class_items[cls] == 0) return 0;
+  if (mode == LBM_BATCH_PERSISTENT) return b->pers_grid_max;
+  const int need = (b->class_items[cls] + kWorklistThreads / 32 - 1) / (kWorklistThreads / 32);
+  if (need >= b->wl_grid) return b->wl_grid;
+  int g = 1;
+  while (g < need) g <<= 1;
+  return std::min(g, b->wl_grid);
+}
+
 lbm_status window_graph(lbm_batch* b, int mode, cudaGraphExec_t* out) {
-  if (b->graph[mode]) {
-    *out = b->graph[mode];
+  const int g0 = class_grid(b, mode, 0), g1 = class_grid(b, mode, 1);
+  const auto key = std::make_tuple(mode, g0, g1);
+  const auto it = b->graphs.find(key);
+  if (it != b->graphs.end()) {
+    *out = it->second;
     return LBM_OK;
   }
   cudaGraph_t g = nullptr;
   LBM_BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
   const int W = b->p.window;
+  const int span = b->pers_grid_max + 1;
+  // with both classes active they run as two branches of the graph, joined
+  // after each step (work list) or before the reduction (persistent)
+  const bool both = g0 > 0 && g1 > 0;
+  cudaStream_t s1 = both ? b->side : b->stream;
+  auto fork = [&]() {
+    if (!both) return;
+    cudaEventRecord(b->ev_fork, b->stream);
+    cudaStreamWaitEvent(b->side, b->ev_fork, 0);
+  };
+  auto join = [&]() {
+    if (!both) return;
+    cudaEventRecord(b->ev_join, b->side);
+    cudaStreamWaitEvent(b->stream, b->ev_join, 0);
+  };
   if (mode == LBM_BATCH_WORKLIST) {
-    for (int s = 0; s < W; ++s)
-      batch_worklist_kernel<<<b->wl_grid, kWorklistThreads, 0, b->stream>>>(
-          b->d_inst, b->d_active, b->d_prefix, b->d_n_active, b->buf[s & 1],
-          b->buf[(s + 1) & 1], b->d_status);
+    for (int s = 0; s < W; ++s) {
+      fork();
+      if (g0 > 0)
+        batch_worklist_kernel<true><<<g0, kWorklistThreads, 0, b->stream>>>(
+            b->d_inst, b->d_active, b->d_prefix, b->d_n_active, b->buf[s & 1],
+            b->buf[(s + 1) & 1], b->d_status);
+      if (g1 > 0)
+        batch_worklist_kernel<false><<<g1, kWorklistThreads, 0, s1>>>(
+            b->d_inst, b->d_active, b->d_prefix, b->d_n_active, b->buf[s & 1],
+            b->buf[(s + 1) & 1], b->d_status);
+      join();
+    }
   } else {
-    batch_persistent_kernel<<<b->pers_grid_max, kPersistentThreads, 0, b->stream>>>(
-        b->d_inst, b->d_cta_begin, b->d_cta_list, W, b->buf[0], b->buf[1], b->d_status);
+    fork();
+    if (g0 > 0)
+      batch_persistent_kernel<true><<<g0, kPersistentThreads, 0, b->stream>>>(
+          b->d_inst, b->d_cta_begin, b->d_cta_list, W, b->buf[0], b->buf[1], b->d_status);
+    if (g1 > 0)
+      batch_persistent_kernel<false><<<g1, kPersistentThreads, 0, s1>>>(
+          b->d_inst, b->d_cta_begin + span, b->d_cta_list, W, b->buf[0], b->buf[1],
+          b->d_status);
+    join();
   }
   batch_window_reduce<<<b->count, kReduceCta, 0, b->stream>>>(
-      b->d_inst, b->d_active, b->d_n_active, b->buf[0], b->snap, b->rowmean, b->d_out,
+      b->d_inst, b->d_active, b->d_n_active + 1, b->buf[0], b->snap, b->rowmean, b->d_out,
       float(b->p.tol));
   cudaError_t e = cudaStreamEndCapture(b->stream, &g);
   if (e != cudaSuccess) return bfail(b, LBM_E_CUDA, std::string("capture: ") + cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&b->graph[mode], g, 0);
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess)
     return bfail(b, LBM_E_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
-  *out = b->graph[mode];
+  b->graphs[key] = exec;
+  *out = exec;
   return LBM_OK;
 }
 
@@ -477,7 +580,7 @@ size_t max_active_cells(const lbm_batch* b) {
 
 // Window-level autotuner: measure each candidate (mode, rows) on one live
 // window, keep the cheapest per cell update, and tune again once the active
-// work has halved.
+// work has halved or the chosen candidate's cost has risen.
 void choose_config(lbm_batch* b, int& mode, int& rows) {
   if (b->p.mode != LBM_BATCH_AUTO) {
     mode = b->p.mode;
@@ -485,7 +588,10 @@ void choose_config(lbm_batch* b, int& mode, int& rows) {
     return;
   }
   const size_t cells = active_cells(b);
-  if (b->tuned && cells * 2 < b->tuned_cells) {
+  // tune again once the active work has halved, or once the chosen
+  // configuration has become 30 % dearer per cell update (instances leaving
+  // change which band height balances the remaining items best)
+  if (b->tuned && (cells * 2 < b->tuned_cells || b->last_cost > 1.3 * b->tuned_cost)) {
     b->tuned = false;
     std::fill(b->cand_cost.begin(), b->cand_cost.end(), -1.0);
   }
@@ -493,7 +599,8 @@ void choose_config(lbm_batch* b, int& mode, int& rows) {
     for (size_t k = 0; k < b->candidates.size(); ++k) {
       if (b->cand_cost[k] >= 0) continue;
       const auto& c = b->candidates[k];
-      if (b->p.rows_per_item > 0 && c.first == LBM_BATCH_WORKLIST && c.second != b->p.rows_per_item)
+      if (b->p.rows_per_item > 0 && c.first == LBM_BATCH_WORKLIST &&
+          c.second != b->p.rows_per_item)
         continue;
       // a persistent window puts each instance on one SM: only worth trying
       // when the active populations are within a few times the L2 size and
@@ -516,6 +623,8 @@ void choose_config(lbm_batch* b, int& mode, int& rows) {
     b->cur_rows = b->candidates[bk].second;
     b->tuned = true;
     b->tuned_cells = cells;
+    b->tuned_cost = best;
+    b->last_cost = best;
   }
   mode = b->cur_mode;
   rows = b->cur_rows;
@@ -553,6 +662,8 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
   if (p->window < 2 || p->window % 2 || p->max_steps < 1 || !(p->tol >= 0) ||
       p->mode < LBM_BATCH_AUTO || p->mode > LBM_BATCH_PERSISTENT || p->rows_per_item < 0 ||
       p->conv < LBM_CONV_COEX || p->conv > LBM_CONV_CELL ||
+      !(p->variant == LBM_VARIANT_AUTO || p->variant == LBM_VARIANT_PAIR ||
+        p->variant == LBM_VARIANT_REGISTER) ||
       !(p->G < 0) || !(p->a > 0) || !(p->b > 0) || !(p->R > 0) || p->tc_mode < 0 ||
       p->tc_mode > 1)
     return LBM_E_INVAL;
@@ -584,7 +695,8 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
     d.coff = coff;
     d.nx = s.nx;
     d.ny = s.ny;
-    d.n_strips = (s.nx + 31) / 32;
+    d.pair = s.nx % 2 == 0 && p->variant != LBM_VARIANT_REGISTER;
+    d.n_strips = d.pair ? (s.nx + 63) / 64 : (s.nx + 31) / 32;
     d.scheme = s.scheme;
     d.row_off = roff;
     const double T = s.T_over_Tc * Tc;
@@ -597,6 +709,7 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
     d.P.omega = float(1.0 / s.tau);
     d.P.sigma_ups = float(s.sigma / (s.tau - 0.5));
     d.P.guo = float(1.0 - 1.0 / (2.0 * s.tau));
+    d.P.scheme = s.scheme;
     set_geometry(d, 32);
     const size_t cells = size_t(s.nx) * s.ny;
     off += (9 * cells + 31) / 32 * 32;
@@ -623,14 +736,20 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
       return bail(LBM_E_CUDA, "stream");
     b->own_stream = true;
   }
-  int occ_wl = 0, occ_p = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_wl, batch_worklist_kernel,
+  if (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(LBM_E_CUDA, "stream");
+  int occ_wl[2] = {0, 0}, occ_p[2] = {0, 0};
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_wl[0], batch_worklist_kernel<true>,
                                                     kWorklistThreads, 0) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, batch_persistent_kernel,
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_wl[1], batch_worklist_kernel<false>,
+                                                    kWorklistThreads, 0) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p[0], batch_persistent_kernel<true>,
+                                                    kPersistentThreads, 0) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p[1], batch_persistent_kernel<false>,
                                                     kPersistentThreads, 0) != cudaSuccess)
     return bail(LBM_E_CUDA, "occupancy");
-  b->wl_grid = std::max(1, occ_wl) * b->sm_count;
-  b->pers_grid_max = std::max(1, std::max(1, occ_p) * b->sm_count);
+  b->wl_grid = std::max(1, std::min(occ_wl[0], occ_wl[1])) * b->sm_count;
+  b->pers_grid_max = std::max(1, std::min(occ_p[0], occ_p[1])) * b->sm_count;
   bool ok = true;
   ok &= cudaMalloc(&b->buf[0], off * sizeof(float)) == cudaSuccess;
   ok &= cudaMalloc(&b->buf[1], off * sizeof(float)) == cudaSuccess;
@@ -643,17 +762,21 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
   ok &= cudaMalloc(&b->d_tmp, b->tmp_cells * sizeof(double)) == cudaSuccess;
   ok &= cudaMalloc(&b->d_active, count * sizeof(int)) == cudaSuccess;
   ok &= cudaMalloc(&b->d_prefix, (count + 1) * sizeof(int)) == cudaSuccess;
-  ok &= cudaMalloc(&b->d_n_active, sizeof(int)) == cudaSuccess;
-  ok &= cudaMalloc(&b->d_cta_begin, (b->pers_grid_max + 1) * sizeof(int)) == cudaSuccess;
+  ok &= cudaMalloc(&b->d_n_active, 2 * sizeof(int)) == cudaSuccess;
+  ok &= cudaMalloc(&b->d_cta_begin, 2 * (b->pers_grid_max + 1) * sizeof(int)) == cudaSuccess;
   ok &= cudaMalloc(&b->d_cta_list, count * sizeof(int)) == cudaSuccess;
   if (!ok) return bail(LBM_E_NOMEM, "cudaMalloc");
   ok &= cudaMallocHost(&b->h_active, count * sizeof(int)) == cudaSuccess;
-  ok &= cudaMallocHost(&b->h_prefix, (count + 2) * sizeof(int)) == cudaSuccess;
-  ok &= cudaMallocHost(&b->h_cta_begin, (b->pers_grid_max + 1) * sizeof(int)) == cudaSuccess;
+  ok &= cudaMallocHost(&b->h_prefix, (count + 3) * sizeof(int)) == cudaSuccess;
+  ok &= cudaMallocHost(&b->h_cta_begin, 2 * (b->pers_grid_max + 1) * sizeof(int)) ==
+        cudaSuccess;
   ok &= cudaMallocHost(&b->h_cta_list, count * sizeof(int)) == cudaSuccess;
   ok &= cudaMallocHost(&b->h_out, count * sizeof(BatchOut)) == cudaSuccess;
   ok &= cudaMallocHost(&b->h_status, count * sizeof(unsigned)) == cudaSuccess;
   if (!ok) return bail(LBM_E_NOMEM, "cudaMallocHost");
+  if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess)
+    return bail(LBM_E_CUDA, "event");
   if (cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess)
     return bail(LBM_E_CUDA, "event");
   if (cudaMemsetAsync(b->d_status, 0, count * sizeof(unsigned), b->stream) != cudaSuccess ||
@@ -674,8 +797,8 @@ lbm_status lbm_batch_destroy(lbm_batch* b) {
   if (!b) return LBM_OK;
   BDeviceGuard guard(b->p.device);
   if (b->stream) cudaStreamSynchronize(b->stream);
-  for (auto& g : b->graph)
-    if (g) cudaGraphExecDestroy(g);
+  for (auto& kv : b->graphs)
+    if (kv.second) cudaGraphExecDestroy(kv.second);
   cudaFree(b->buf[0]);
   cudaFree(b->buf[1]);
   cudaFree(b->snap);
@@ -698,6 +821,9 @@ lbm_status lbm_batch_destroy(lbm_batch* b) {
   if (b->h_status) cudaFreeHost(b->h_status);
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
+  if (b->side) cudaStreamDestroy(b->side);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
   return LBM_OK;
@@ -808,7 +934,12 @@ lbm_status lbm_batch_run(lbm_batch* b, int max_windows, int* n_active) {
     LBM_BCUDA(b, cudaEventRecord(b->ev0, b->stream));
     LBM_BCUDA(b, cudaGraphLaunch(g, b->stream));
     LBM_BCUDA(b, cudaEventRecord(b->ev1, b->stream));
-    const unsigned long long nl = mode == LBM_BATCH_WORKLIST ? b->p.window + 1 : 2;
+    // two class kernels per step (work list) or per window (persistent), and
+    // the reduction
+    const unsigned long long kernels =
+        (class_grid(b, mode, 0) > 0 ? 1 : 0) + (class_grid(b, mode, 1) > 0 ? 1 : 0);
+    const unsigned long long nl =
+        (mode == LBM_BATCH_WORKLIST ? kernels * b->p.window : kernels) + 1;
     count_launches(nl);
     b->stats.launches += nl;
     LBM_BCUDA(b, cudaMemcpyAsync(b->h_out, b->d_out, b->count * sizeof(BatchOut),
@@ -823,6 +954,8 @@ lbm_status lbm_batch_run(lbm_batch* b, int max_windows, int* n_active) {
     b->stats.mode = mode;
     b->stats.rows_per_item = rows;
     if (b->p.mode == LBM_BATCH_AUTO && !b->tuned) record_cost(b, mode, rows, ms, cells);
+    if (b->p.mode == LBM_BATCH_AUTO && b->tuned)
+      b->last_cost = ms * 1e6 / (double(cells) * b->p.window);
     std::vector<int> still;
     const double floor32 = 8.0 * 1.1920928955078125e-7;
     for (int i : b->active) {

@@ -27,6 +27,10 @@ cudaError_t strip2_launch_f32(int, int, const StripLaunch&, int, cudaStream_t);
 cudaError_t strip2_launch_f64(int, int, const StripLaunch&, int, cudaStream_t);
 cudaError_t strip2_occupancy_f32(int, int, int*);
 cudaError_t strip2_occupancy_f64(int, int, int*);
+cudaError_t strip2_launch_bf16(int, int, const StripLaunch&, int, cudaStream_t);
+cudaError_t strip2_launch_f16(int, int, const StripLaunch&, int, cudaStream_t);
+cudaError_t strip2_occupancy_bf16(int, int, int*);
+cudaError_t strip2_occupancy_f16(int, int, int*);
 cudaError_t strip_tma_launch_f32(int, const StripLaunch&, int, cudaStream_t);
 cudaError_t strip_tma_occupancy_f32(int, int*);
 cudaError_t strip_occupancy_f64(int, int, int*);
@@ -72,11 +76,15 @@ cudaError_t strip2_launch(int precision, int scheme, int mode, const StripLaunch
                           cudaStream_t s) {
   if (precision == kFP32) return strip2_launch_f32(scheme, mode, L, grid, s);
   if (precision == kFP64) return strip2_launch_f64(scheme, mode, L, grid, s);
+  if (precision == kBF16Dev) return strip2_launch_bf16(scheme, mode, L, grid, s);
+  if (precision == kFP16Dev) return strip2_launch_f16(scheme, mode, L, grid, s);
   return cudaErrorNotSupported;
 }
 cudaError_t strip2_occupancy(int precision, int scheme, int mode, int* b) {
   if (precision == kFP32) return strip2_occupancy_f32(scheme, mode, b);
   if (precision == kFP64) return strip2_occupancy_f64(scheme, mode, b);
+  if (precision == kBF16Dev) return strip2_occupancy_bf16(scheme, mode, b);
+  if (precision == kFP16Dev) return strip2_occupancy_f16(scheme, mode, b);
   return cudaErrorNotSupported;
 }
 cudaError_t strip_tma_launch(int precision, int scheme, const StripLaunch& L, int grid,
@@ -221,20 +229,19 @@ StripLaunch base_launch(lbm_ctx* c) {
 // (FP32 steps, nx % 4 == 0 so rows are 16-byte aligned, nx >= 64), else one
 // column per lane.
 int pick_variant(const lbm_ctx* c, int mode) {
-  const bool direct = c->p.precision == LBM_FP32 || c->p.precision == LBM_FP64;
-  const bool pair_ok = direct && c->p.nx % 2 == 0;
+  const bool pair_ok = c->p.nx % 2 == 0;
   const bool staged_ok = mode == kStepMode && c->p.precision == LBM_FP32 && c->p.nx >= 64 &&
                          c->p.nx % 4 == 0;
   if (c->variant == LBM_VARIANT_STAGED && staged_ok) return LBM_VARIANT_STAGED;
-  // AUTO takes PAIR for FP32 only: in FP64 its doubled register state spills
-  if (((c->variant == LBM_VARIANT_AUTO && c->p.precision == LBM_FP32) ||
+  // AUTO takes PAIR except in FP64, where its doubled register state spills
+  if (((c->variant == LBM_VARIANT_AUTO && c->p.precision != LBM_FP64) ||
        c->variant == LBM_VARIANT_PAIR) && pair_ok)
     return LBM_VARIANT_PAIR;
   return LBM_VARIANT_REGISTER;
 }
 bool use_staged(const lbm_ctx* c, int mode) { return pick_variant(c, mode) == LBM_VARIANT_STAGED; }
 
-// Warp-strip geometry: strips of 32 columns, and as many row bands as fill
+// Warp-strip geometry: strips of 32 columns (64 for PAIR), and as many row bands as fill
 // the resident warp slots once (one wave: every warp of a band runs at the
 // same time as its neighbours).
 lbm_status geometry(lbm_ctx* c, int scheme, int mode, StripLaunch& L, int& grid) {
@@ -609,6 +616,12 @@ lbm_status lbm_get_launch_geometry(lbm_ctx* c, int scheme, int* n_strips, int* b
   if (band_rows) *band_rows = L.band_rows;
   if (n_bands) *n_bands = L.n_bands;
   if (grid) *grid = g;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_kernel_variant(lbm_ctx* c, int* variant) {
+  if (!c || !variant) return LBM_E_INVAL;
+  *variant = pick_variant(c, kStepMode);
   return LBM_OK;
 }
 

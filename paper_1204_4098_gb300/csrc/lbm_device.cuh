@@ -69,6 +69,7 @@ struct Phys {
   C omega;      // 1 / tau
   C sigma_ups;  // sigma / (tau - 1/2)  (Eq. 31: v' = v + sigma F / (upsilon psi^2))
   C guo;        // 1 - 1 / (2 tau)  (B_e = C_e of Eq. 13)
+  int scheme;   // forcing scheme, read only by collide<C, kAnyForced>
 };
 
 // Reciprocal and square root for the per-cell physics.  FP64 keeps the IEEE
@@ -102,6 +103,10 @@ __device__ __forceinline__ C psi_of_rho(C rho, const Phys<C>& P, bool& bad) {
 // collision of one cell, Eqs. 1-2 with the forcing schemes of Table I
 // ---------------------------------------------------------------------------
 enum Scheme { kSC = 0, kEDM = 1, kImproved = 2, kNoForce = 3, kEDMMod = 4, kLadd = 5 };
+// Template value: the scheme (one that evaluates psi, i.e. not kNoForce) is
+// read from Phys::scheme at run time.  One inlined body then serves every
+// instance of a mixed batch, instead of one body per scheme.
+constexpr int kAnyForced = -1;
 
 // Every scheme of Table I is BGK towards f_eq(rho, u_eq) plus Guo's general
 // forcing term (Eq. 12) with B = B_e F and C = C_e (V F + F V):
@@ -117,10 +122,13 @@ enum Scheme { kSC = 0, kEDM = 1, kImproved = 2, kNoForce = 3, kEDMMod = 4, kLadd
 //
 // Every operation is explicitly rounded (no compiler contraction), so all
 // kernels that inline this body -- single domain, batch work list, batch
-// persistent -- produce bit-identical populations.
+// persistent -- produce bit-identical populations.  With SCHEME fixed the
+// branches below fold at compile time; with kAnyForced they are taken on
+// P.scheme (uniform across a warp) and compute the same values.
 template <class C, int SCHEME>
 __device__ __forceinline__ void collide(C (&f)[kQ], C rho, C Fx, C Fy, C psi,
                                         const Phys<C>& P) {
+  const int sch = SCHEME == kAnyForced ? P.scheme : SCHEME;
   const C jx = add_rn(add_rn(sub_rn(f[1], f[3]), sub_rn(f[5], f[6])), sub_rn(f[8], f[7]));
   const C jy = sub_rn(add_rn(sub_rn(f[2], f[4]), add_rn(f[5], f[6])), add_rn(f[7], f[8]));
   const C inv_rho = fast_div(C(1), rho);
@@ -129,17 +137,17 @@ __device__ __forceinline__ void collide(C (&f)[kQ], C rho, C Fx, C Fy, C psi,
 
   C qx = ux, qy = uy;  // velocity in f_eq
   C Vx = C(0), Vy = C(0), Be = C(0), Ce = C(0);
-  constexpr bool kForcing = SCHEME != kSC && SCHEME != kNoForce;
-  if constexpr (SCHEME == kSC) {
+  const bool forcing = sch != kSC && sch != kNoForce;
+  if (sch == kSC) {
     const C t = mul_rn(P.tau, inv_rho);
     qx = fma_rn(t, Fx, ux);
     qy = fma_rn(t, Fy, uy);
-  } else if constexpr (SCHEME == kEDM) {
+  } else if (sch == kEDM) {
     Vx = fma_rn(half_inv, Fx, ux);
     Vy = fma_rn(half_inv, Fy, uy);
     Be = C(1);
     Ce = C(1);
-  } else if constexpr (SCHEME == kImproved) {
+  } else if (sch == kImproved) {
     qx = fma_rn(half_inv, Fx, ux);
     qy = fma_rn(half_inv, Fy, uy);
     const C s = fast_div(P.sigma_ups, mul_rn(psi, psi));
@@ -147,12 +155,12 @@ __device__ __forceinline__ void collide(C (&f)[kQ], C rho, C Fx, C Fy, C psi,
     Vy = fma_rn(s, Fy, qy);
     Be = P.guo;
     Ce = P.guo;
-  } else if constexpr (SCHEME == kEDMMod) {
+  } else if (sch == kEDMMod) {
     Vx = fma_rn(half_inv, Fx, ux);
     Vy = fma_rn(half_inv, Fy, uy);
     Be = C(1);
     Ce = P.omega;
-  } else if constexpr (SCHEME == kLadd) {
+  } else if (sch == kLadd) {
     Vx = ux;
     Vy = uy;
     Be = C(1);
@@ -171,7 +179,7 @@ __device__ __forceinline__ void collide(C (&f)[kQ], C rho, C Fx, C Fy, C psi,
     const C wr = mul_rn(w, om_rho);
     C even = mul_rn(wr, fma_rn(mul_rn(C(4.5), eq), eq, base));
     C odd = mul_rn(mul_rn(C(3), wr), eq);
-    if constexpr (kForcing) {
+    if (forcing) {
       even = fma_rn(mul_rn(w, Ce), fma_rn(mul_rn(C(9), eV), eF, -VF3), even);
       odd = fma_rn(mul_rn(mul_rn(C(3), w), Be), eF, odd);
     }

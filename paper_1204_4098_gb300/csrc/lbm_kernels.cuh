@@ -275,14 +275,21 @@ strip_kernel(const StripArgs<S> A) {
 template <class T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<__nv_bfloat16> { using type = __nv_bfloat162; };
+template <> struct Vec2<__half> { using type = __half2; };
 
-template <class S, int SCHEME, int MODE>
+template <bool kCoherent, class V>
+__device__ __forceinline__ V load2(const V* p) {
+  if constexpr (kCoherent) return __ldcg(p);
+  else return __ldg(p);
+}
+
+template <class S, int SCHEME, int MODE, bool kCoherent = false>
 __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int band,
                                            int lane) {
   using C = typename S::C;
   using T = typename S::T;
   using V = typename Vec2<T>::type;
-  static_assert(!S::kDev, "two-column variant is for direct storage");
   constexpr bool kNeedPsi = !(MODE == kModeObserveNoForce ||
                               (MODE == kModeStep && SCHEME == kNoForce));
   const unsigned FULL = 0xffffffffu;
@@ -324,27 +331,41 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
     {
       int qy = y - qey;
       qy = qy < 0 ? qy + ny : (qy >= ny ? qy - ny : qy);
-      h = qlane ? S::to_c(__ldg(A.src + qa * A.plane + size_t(qy) * nx + qsx)) : C(0);
+      h = qlane ? pull_one<S, kCoherent>(A, qa, qy * nx + qsx) : C(0);
+    }
+    // deviation storage: density plane pairs of the three source rows
+    float2 rr[3];
+    if constexpr (S::kDev) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        rr[j] = load2<kCoherent>(
+            reinterpret_cast<const float2*>(A.rho_src + size_t(rows[j]) * nx + ca));
     }
 #pragma unroll
     for (int a = 0; a < kQ; ++a) {
       const int ex = ex_of(a), ey = ey_of(a);
       const int r = rows[1 - ey];  // source row y - ey
-      const V v = __ldg(reinterpret_cast<const V*>(A.src + a * A.plane + size_t(r) * nx + ca));
+      const V v =
+          load2<kCoherent>(reinterpret_cast<const V*>(A.src + a * A.plane + size_t(r) * nx + ca));
+      C lo = S::to_c(v.x), hi = S::to_c(v.y);  // pulled values at columns ca, ca + 1
+      if constexpr (S::kDev) {
+        lo = fma_rn(w_of<C>(a), C(rr[1 - ey].x), lo);
+        hi = fma_rn(w_of<C>(a), C(rr[1 - ey].y), hi);
+      }
       if (ex == 0) {
-        PA[a] = S::to_c(v.x);
-        PB[a] = S::to_c(v.y);
-      } else if (ex == 1) {  // sources x-1: (prev lane's .y, own .x)
+        PA[a] = lo;
+        PB[a] = hi;
+      } else if (ex == 1) {  // sources x-1: (prev lane's upper, own lower)
         const int k = a == 1 ? 9 : (a == 5 ? 10 : 11);
         const C fromL = __shfl_sync(FULL, h, k);
-        const C up = __shfl_up_sync(FULL, S::to_c(v.y), 1);
+        const C up = __shfl_up_sync(FULL, hi, 1);
         PA[a] = lane == 0 ? fromL : up;
-        PB[a] = S::to_c(v.x);
-      } else {  // sources x+1: (own .y, next lane's .x)
+        PB[a] = lo;
+      } else {  // sources x+1: (own upper, next lane's lower)
         const int k = a == 3 ? 25 : (a == 6 ? 26 : 27);
         const C fromR = __shfl_sync(FULL, h, k);
-        const C dn = __shfl_down_sync(FULL, S::to_c(v.x), 1);
-        PA[a] = S::to_c(v.y);
+        const C dn = __shfl_down_sync(FULL, lo, 1);
+        PA[a] = hi;
         PB[a] = lane == 31 ? fromR : dn;
       }
     }
@@ -410,17 +431,31 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
     if constexpr (MODE == kModeStep) {
       collide<C, SCHEME>(PA0, ra0, Fxa, Fya, Caz, A.P);
       collide<C, SCHEME>(PB0, rb0, Fxb, Fyb, Cbz, A.P);
-      if (active_b) {
+      if (active_a) {  // nx even: both cells of an active lane are inside
+        if constexpr (S::kDev) {
+          // the density plane absorbs the 16-bit rounding of the deviations
+          C resa = ra0, resb = rb0;
 #pragma unroll
-        for (int a = 0; a < kQ; ++a) {
-          V v;
-          v.x = S::from_c(PA0[a]);
-          v.y = S::from_c(PB0[a]);
-          *reinterpret_cast<V*>(A.dst + a * A.plane + idx) = v;
+          for (int a = 0; a < kQ; ++a) {
+            const T da = S::from_c(sub_rn(PA0[a], mul_rn(w_of<C>(a), ra0)));
+            const T db = S::from_c(sub_rn(PB0[a], mul_rn(w_of<C>(a), rb0)));
+            V v;
+            v.x = da;
+            v.y = db;
+            *reinterpret_cast<V*>(A.dst + a * A.plane + idx) = v;
+            resa = sub_rn(resa, S::to_c(da));
+            resb = sub_rn(resb, S::to_c(db));
+          }
+          *reinterpret_cast<float2*>(A.rho_dst + idx) = make_float2(float(resa), float(resb));
+        } else {
+#pragma unroll
+          for (int a = 0; a < kQ; ++a) {
+            V v;
+            v.x = S::from_c(PA0[a]);
+            v.y = S::from_c(PB0[a]);
+            *reinterpret_cast<V*>(A.dst + a * A.plane + idx) = v;
+          }
         }
-      } else if (active_a) {
-#pragma unroll
-        for (int a = 0; a < kQ; ++a) A.dst[a * A.plane + idx] = S::from_c(PA0[a]);
       }
     } else {
       auto out = [&](const C (&P)[kQ], C r0, C Fx, C Fy, size_t i) {

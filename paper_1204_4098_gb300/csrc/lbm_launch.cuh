@@ -35,6 +35,7 @@ StripArgs<S> make_args(const StripLaunch& L) {
   A.P.omega = C(L.omega);
   A.P.sigma_ups = C(L.sigma_ups);
   A.P.guo = C(L.guo);
+  A.P.scheme = 0;  // the single-domain kernels fix the scheme at compile time
   return A;
 }
 
@@ -119,7 +120,7 @@ cudaError_t strip_tma_occupancy_t(int scheme, int* b) {
   }
 }
 
-// Two-columns-per-lane kernel: direct storage (FP32, FP64) only.
+// Two-columns-per-lane kernel (every storage type; needs even nx).
 template <class S, int SCHEME, int MODE>
 cudaError_t launch2_one(const StripLaunch& L, int grid, cudaStream_t s) {
   strip2_kernel<S, SCHEME, MODE><<<grid, kStripThreads, 0, s>>>(make_args<S>(L));
@@ -133,9 +134,7 @@ cudaError_t occ2_one(int* b) {
 template <class S>
 cudaError_t strip2_launch_t(int scheme, int mode, const StripLaunch& L, int grid,
                             cudaStream_t s) {
-  if constexpr (S::kDev) {
-    return cudaErrorNotSupported;
-  } else {
+  {
     if (mode == kObserveMode) return launch2_one<S, kSC, kModeObserve>(L, grid, s);
     if (mode == kObserveNoForceMode) return launch2_one<S, kSC, kModeObserveNoForce>(L, grid, s);
     switch (scheme) {
@@ -151,9 +150,7 @@ cudaError_t strip2_launch_t(int scheme, int mode, const StripLaunch& L, int grid
 }
 template <class S>
 cudaError_t strip2_occupancy_t(int scheme, int mode, int* b) {
-  if constexpr (S::kDev) {
-    return cudaErrorNotSupported;
-  } else {
+  {
     if (mode == kObserveMode) return occ2_one<S, kSC, kModeObserve>(b);
     if (mode == kObserveNoForceMode) return occ2_one<S, kSC, kModeObserveNoForce>(b);
     switch (scheme) {

@@ -45,7 +45,8 @@ class lbm_batch_params(ctypes.Structure):
                 ("R", ctypes.c_double), ("G", ctypes.c_double), ("device", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("window", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_steps", ctypes.c_int), ("mode", ctypes.c_int),
-                ("rows_per_item", ctypes.c_int), ("conv", ctypes.c_int)]
+                ("rows_per_item", ctypes.c_int), ("conv", ctypes.c_int),
+                ("variant", ctypes.c_int)]
 
 
 class lbm_result(ctypes.Structure):
@@ -98,6 +99,7 @@ SIGNATURES = {
     "lbm_set_band_rows": (_I, [_P, _I]),
     "lbm_set_kernel_variant": (_I, [_P, _I]),
     "lbm_get_launch_geometry": (_I, [_P, _I, _IP, _IP, _IP, _IP]),
+    "lbm_get_kernel_variant": (_I, [_P, _IP]),
     "lbm_mass_f32_noalloc": (_I, [_P, ctypes.c_size_t, _P, _P]),
     "lbm_batch_default_params": (None, [ctypes.POINTER(lbm_batch_params)]),
     "lbm_batch_create": (_I, [ctypes.POINTER(lbm_batch_params), ctypes.POINTER(lbm_instance),
@@ -292,6 +294,13 @@ class Lattice:
                     "lbm_get_launch_geometry")
         return dict(zip(("n_strips", "band_rows", "n_bands", "grid"), (x.value for x in v)))
 
+    def variant(self):
+        """The kernel variant lbm_step resolves to (VARIANT_REGISTER/STAGED/PAIR)."""
+        v = _I()
+        self._check(lib().lbm_get_kernel_variant(self.ctx, ctypes.byref(v)),
+                    "lbm_get_kernel_variant")
+        return v.value
+
 
 class Batch:
     """A batch of independent instances (lbm_batch_* of the C ABI).
@@ -300,10 +309,12 @@ class Batch:
     """
 
     def __init__(self, instances, window=1000, tol=1e-9, max_steps=200000, mode=BATCH_AUTO,
-                 rows_per_item=0, tc_mode=0, device=0, stream=None, conv=CONV_COEX):
+                 rows_per_item=0, tc_mode=0, device=0, stream=None, conv=CONV_COEX,
+                 variant=VARIANT_AUTO):
         p = lbm_batch_params()
         lib().lbm_batch_default_params(ctypes.byref(p))
         p.window, p.tol, p.max_steps, p.conv = int(window), float(tol), int(max_steps), int(conv)
+        p.variant = int(variant)
         p.mode, p.rows_per_item, p.tc_mode, p.device = int(mode), int(rows_per_item), \
             int(tc_mode), int(device)
         p.cuda_stream = None if stream is None else ctypes.c_void_p(int(stream))

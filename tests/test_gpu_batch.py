@@ -17,6 +17,8 @@ MIXED = [
     dict(nx=100, ny=17, T_over_Tc=0.9, tau=1.2, sigma=0.0, scheme=lbm.EDM_MOD),
     dict(nx=32, ny=32, T_over_Tc=0.95, tau=1.0, sigma=0.0, scheme=lbm.LADD),
     dict(nx=7, ny=129, T_over_Tc=0.9, tau=0.6, sigma=0.0, scheme=lbm.NOFORCE),
+    dict(nx=130, ny=23, T_over_Tc=0.85, tau=0.8, sigma=0.1, scheme=lbm.IMPROVED),
+    dict(nx=2, ny=11, T_over_Tc=0.9, tau=1.0, sigma=0.0, scheme=lbm.SC),
 ]
 
 
@@ -38,6 +40,7 @@ def test_batch_matches_single_domain_bitwise(mode, rows):
     assert b.run(windows) == len(MIXED)
     for k, d in enumerate(MIXED):
         single = lbm.Lattice(d["nx"], d["ny"], d["T_over_Tc"], precision=lbm.FP32)
+        single.set_variant(lbm.VARIANT_REGISTER)  # the batch takes two columns per lane
         single.init_density(rho0[k])
         single.step(windows * window, d["scheme"], d["tau"], d["sigma"])
         want = single.observe()[0]

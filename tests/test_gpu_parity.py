@@ -315,14 +315,15 @@ def test_staged_kernel_fp32_parity_with_oracle():
     assert err < 2e-6 * 20 ** 0.5, err
 
 
-@pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP64])
+@pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP64, lbm.BF16DEV, lbm.FP16DEV])
 @pytest.mark.parametrize("nx,ny", [(2, 9), (4, 4), (40, 21), (64, 33), (66, 40), (100, 17),
                                    (130, 65)])
 def test_pair_kernel_matches_register_kernel_bitwise(precision, nx, ny):
     """Two columns per lane (vector loads, shuffled +-1 pulls, boundary and
     halo elements from extra lanes, wrapped lanes in ragged strips) computes
     exactly what one column per lane does: steps of every scheme and the
-    observed density and velocity."""
+    observed density and velocity, in every storage type (16-bit deviation
+    storage included: deviations and density plane pairs)."""
     t = 0.85
     rho, ux, uy = droplet_state(nx, ny, t)
     for scheme, sigma in ((lbm.SC, 0.0), (lbm.IMPROVED, 0.1), (lbm.EDM, 0.0),
