@@ -463,6 +463,87 @@ def run_warmstart_workload(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_droplets_workload(args, world, rank, local):
+    """Config 2: droplets on 256 x 256 (R0 = 20, 30, 40, 50; W = 5) for every
+    T/Tc in {0.6, 0.7, 0.8, 0.9}, tau in {0.6, 1.0, 1.5} and scheme (Shan-Chen,
+    EDM, improved with sigma = 0, 0.05, 0.1, 0.15, 0.105), 2e4 steps each, in
+    one batch; Laplace fits and coexistence per sweep point."""
+    import torch
+
+    from paper_1204_4098_gb300 import droplets, lbm
+    torch.cuda.set_device(local)
+    inst = droplets.laplace_instances()
+    res, info = droplets.run(inst, args.droplet_steps)
+    fits = droplets.laplace_fits(inst, res)
+    names = {lbm.SC: "SC", lbm.EDM: "EDM", lbm.IMPROVED: "improved"}
+    table = []
+    for (t, tau, sch, sg), f in sorted(fits.items()):
+        runs = [r for d, r in zip(inst, res)
+                if (d["T_over_Tc"], d["tau"], d["scheme"], d["sigma"]) == (t, tau, sch, sg)]
+        row = {"T_over_Tc": t, "tau": tau, "scheme": names[sch], "sigma": sg,
+               "stable": f is not None,
+               "diverged": sum(droplets.unstable(r) for r in runs),
+               "dissolved": sum((not droplets.unstable(r)) and droplets.vanished(r)
+                                for r in runs)}
+        if f is not None:
+            row.update({k: f[k] for k in ("surface_tension", "intercept", "intercept_se",
+                                          "r2", "max_speed")})
+            row["rho_l_R50"], row["rho_g_R50"] = f["rho_in"][-1], f["rho_out"][-1]
+        table.append(row)
+    cells_steps = sum(d["nx"] * d["ny"] * r["steps"] for d, r in zip(inst, res))
+    stable = [r for r in table if r["stable"]]
+    line = {"metric": METRIC, "workload": "droplets and Laplace's law (config 2)",
+            "value": cells_steps / (info["gpu_ms"] * 1e-3) / 1e6, "unit": "MLUPS (batched)",
+            "higher_is_better": True, "n_gpus": world, "data": "synthetic", "dtype": "f32",
+            "runs": len(inst), "steps": args.droplet_steps, "gpu_s": info["gpu_ms"] / 1e3,
+            "wall_s": info["wall"], "status": _status_counts(res),
+            "laplace_points": len(table), "laplace_stable": len(stable),
+            "laplace_min_r2": min((r["r2"] for r in stable), default=None),
+            "laplace_median_r2": float(sorted(r["r2"] for r in stable)[len(stable) // 2])
+            if stable else None,
+            "table": table}
+    print(json.dumps(line), flush=True)
+
+
+def run_stability_workload(args, world, rank, local):
+    """Figs. 1, 2, 7: lowest stable T/Tc of a 200 x 200 droplet (r0 = 30, initial
+    interface width W = 3 by default, Maxwell densities, Tc = 0.094 as
+    printed) per scheme and tau, on a T/Tc ladder 0.95 .. 0.45 in steps of
+    0.01, in one batch."""
+    import json as _json
+
+    import numpy as np
+    import torch
+
+    from paper_1204_4098_gb300 import droplets, lbm
+    torch.cuda.set_device(local)
+    schemes = ((lbm.SC, 0.0), (lbm.EDM, 0.0), (lbm.EDM_MOD, 0.0), (lbm.IMPROVED, 0.0),
+               (lbm.IMPROVED, 0.105))
+    taus = (0.6, 0.7, 0.8, 0.9)
+    temps = np.round(np.arange(0.95, 0.4499, -0.01), 2)
+    inst = droplets.stability_instances(schemes, taus, temps)
+    res, info = droplets.run(inst, args.stability_steps, W=args.stability_width, tc_mode=1)
+    th = droplets.thresholds(inst, res)
+    names = {lbm.SC: "SC", lbm.EDM: "EDM", lbm.EDM_MOD: "EDM_Ce=1/tau",
+             lbm.IMPROVED: "improved"}
+    with open(os.path.join(ROOT, "tests", "golden", "paper_values.json")) as f:
+        paper = _json.load(f)
+    cells_steps = sum(d["nx"] * d["ny"] * r["steps"] for d, r in zip(inst, res))
+    line = {"metric": METRIC, "workload": "droplet stability thresholds (Figs. 1, 2, 7)",
+            "value": cells_steps / (info["gpu_ms"] * 1e-3) / 1e6, "unit": "MLUPS (batched)",
+            "higher_is_better": True, "n_gpus": world, "data": "synthetic", "dtype": "f32",
+            "runs": len(inst), "steps": args.stability_steps, "gpu_s": info["gpu_ms"] / 1e3,
+            "wall_s": info["wall"], "status": _status_counts(res),
+            "criterion": f"diverged, or max |v| > {droplets.UNSTABLE_SPEED} after the budget",
+            "initial_width": args.stability_width,
+            "lowest_stable_T_over_Tc": [
+                {"scheme": names[s], "sigma": sg, "tau": tau, "T_min": t}
+                for (s, sg, tau), t in sorted(th.items())],
+            "paper": {"tau0.6": paper["stability_threshold_tau06"]["value"],
+                      "tau0.7": paper["stability_threshold_modified_edm"]["value"]}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -476,7 +557,11 @@ def main():
     ap.add_argument("--variants", action="store_true", default=True)
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--ref-side", type=int, default=384)
-    ap.add_argument("--workload", choices=("roofline", "sweep", "warmstart"), default="roofline")
+    ap.add_argument("--workload", choices=("roofline", "sweep", "warmstart", "droplets",
+                                           "stability"), default="roofline")
+    ap.add_argument("--droplet-steps", type=int, default=20000)
+    ap.add_argument("--stability-steps", type=int, default=20000)
+    ap.add_argument("--stability-width", type=float, default=3.0)
     ap.add_argument("--sweep-instances", type=int, default=512)
     ap.add_argument("--seq-sample", type=int, default=32)
     ap.add_argument("--train-draws", type=int, default=11000)
@@ -493,6 +578,10 @@ def main():
         run_sweep_workload(args, world, rank, local)
     elif args.workload == "warmstart":
         run_warmstart_workload(args, world, rank, local)
+    elif args.workload == "droplets":
+        run_droplets_workload(args, world, rank, local)
+    elif args.workload == "stability":
+        run_stability_workload(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -219,7 +219,7 @@ enum { LBM_BATCH_AUTO = 0, LBM_BATCH_WORKLIST = 1, LBM_BATCH_PERSISTENT = 2 };
  * interface position of a relaxed slab jitters by ~1e-4 cells per window
  * (rounding noise driving a nearly neutral mode), so CELL is met only by
  * some runs; COEX tests what a sweep reports. */
-enum { LBM_CONV_COEX = 0, LBM_CONV_CELL = 1 };
+enum { LBM_CONV_COEX = 0, LBM_CONV_CELL = 1, LBM_CONV_NONE = 2 /* run to max_steps */ };
 enum { LBM_RUN_ACTIVE = 0, LBM_RUN_CONVERGED = 1, LBM_RUN_DIVERGED = 2, LBM_RUN_CAPPED = 3 };
 
 typedef struct {
@@ -233,7 +233,7 @@ typedef struct {
   int mode;             /* LBM_BATCH_AUTO (window-level autotuning), _WORKLIST,
                            _PERSISTENT                                         */
   int rows_per_item;    /* band height of a work-list item; 0 = autotuned      */
-  int conv;             /* LBM_CONV_COEX (default) or LBM_CONV_CELL             */
+  int conv;             /* LBM_CONV_COEX (default), _CELL or _NONE              */
   int variant;          /* LBM_VARIANT_AUTO (default) or _PAIR: two columns per
                            lane for even nx; _REGISTER: one column per lane for
                            every instance.  Results are identical.             */
@@ -291,6 +291,11 @@ lbm_status lbm_batch_get_result(const lbm_batch *b, int i, lbm_result *r);
 
 /* Density of instance i (FP64 host array of ny*nx). */
 lbm_status lbm_batch_get_density(lbm_batch *b, int i, double *rho);
+
+/* Density and actual velocity v = u + F/(2 rho) (Table I, every scheme) of
+ * instance i, as lbm_get_moments: caller-owned FP64 host arrays of ny*nx,
+ * each may be NULL. */
+lbm_status lbm_batch_get_moments(lbm_batch *b, int i, double *rho, double *vx, double *vy);
 
 lbm_status lbm_batch_get_stats(const lbm_batch *b, lbm_batch_stats *s);
 const char *lbm_batch_last_error(const lbm_batch *b);

@@ -318,6 +318,27 @@ __global__ void batch_density_kernel(const BatchInst* __restrict__ inst, int i, 
     out[c] = double(pulled_rho(cur + I.off, plane, I.nx, I.ny, int(c % I.nx), int(c / I.nx)));
 }
 
+// Density and actual velocity v = u + F/(2 rho) (Table I) of instance i,
+// by the observe body of the single-domain kernel (one column per lane,
+// 8-row bands).
+template <int MODE>
+__global__ void __launch_bounds__(kWorklistThreads)
+batch_observe_kernel(const BatchInst* __restrict__ inst, int i, const float* cur, double* rho,
+                     double* vx, double* vy, unsigned* inst_status) {
+  const BatchInst I = inst[i];
+  StripArgs<StoreF32> A = inst_args(I, cur, nullptr, inst_status + i, false);
+  A.out_rho = rho;
+  A.out_vx = vx;
+  A.out_vy = vy;
+  A.n_strips = (I.nx + 31) / 32;
+  A.band_rows = 8;
+  A.n_bands = (I.ny + 7) / 8;
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * kWorklistThreads + threadIdx.x) >> 5;
+  if (w >= A.n_strips * A.n_bands) return;  // warp-uniform
+  strip_run<StoreF32, kSC, MODE, false>(A, w % A.n_strips, w / A.n_strips, lane);
+}
+
 __global__ void to_float_kernel(const double* in, float* out, size_t n) {
   for (size_t c = blockIdx.x * size_t(blockDim.x) + threadIdx.x; c < n;
        c += size_t(gridDim.x) * blockDim.x)
@@ -661,7 +682,7 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
   *out = nullptr;
   if (p->window < 2 || p->window % 2 || p->max_steps < 1 || !(p->tol >= 0) ||
       p->mode < LBM_BATCH_AUTO || p->mode > LBM_BATCH_PERSISTENT || p->rows_per_item < 0 ||
-      p->conv < LBM_CONV_COEX || p->conv > LBM_CONV_CELL ||
+      p->conv < LBM_CONV_COEX || p->conv > LBM_CONV_NONE ||
       !(p->variant == LBM_VARIANT_AUTO || p->variant == LBM_VARIANT_PAIR ||
         p->variant == LBM_VARIANT_REGISTER) ||
       !(p->G < 0) || !(p->a > 0) || !(p->b > 0) || !(p->R > 0) || p->tc_mode < 0 ||
@@ -759,7 +780,7 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
   ok &= cudaMalloc(&b->d_out, count * sizeof(BatchOut)) == cudaSuccess;
   ok &= cudaMalloc(&b->d_status, count * sizeof(unsigned)) == cudaSuccess;
   ok &= cudaMalloc(&b->d_prof, 3 * count * sizeof(double)) == cudaSuccess;
-  ok &= cudaMalloc(&b->d_tmp, b->tmp_cells * sizeof(double)) == cudaSuccess;
+  ok &= cudaMalloc(&b->d_tmp, 3 * b->tmp_cells * sizeof(double)) == cudaSuccess;
   ok &= cudaMalloc(&b->d_active, count * sizeof(int)) == cudaSuccess;
   ok &= cudaMalloc(&b->d_prefix, (count + 1) * sizeof(int)) == cudaSuccess;
   ok &= cudaMalloc(&b->d_n_active, 2 * sizeof(int)) == cudaSuccess;
@@ -974,7 +995,8 @@ lbm_status lbm_batch_run(lbm_batch* b, int max_windows, int* n_active) {
       r.mass = o.mass;
       r.max_drho = o.max_abs;
       const bool converged =
-          b->p.conv == LBM_CONV_CELL ? o.max_dev < 1.0f : b->calm[i] >= 2;
+          b->p.conv == LBM_CONV_CELL ? o.max_dev < 1.0f
+                                     : (b->p.conv == LBM_CONV_COEX && b->calm[i] >= 2);
       if ((b->h_status[i] & kStatusDivergedFlag) || !o.finite) {
         r.status = LBM_RUN_DIVERGED;
       } else if (converged) {
@@ -1011,6 +1033,34 @@ lbm_status lbm_batch_get_density(lbm_batch* b, int i, double* rho) {
   count_launches(1);
   LBM_BCUDA(b, cudaMemcpyAsync(rho, b->d_tmp, cells * sizeof(double), cudaMemcpyDeviceToHost,
                                b->stream));
+  LBM_BCUDA(b, cudaStreamSynchronize(b->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_get_moments(lbm_batch* b, int i, double* rho, double* vx, double* vy) {
+  if (!b || i < 0 || i >= b->count) return bfail(b, LBM_E_INVAL, "bad argument");
+  if (!b->initialized) return bfail(b, LBM_E_STATE, "batch not initialised");
+  BDeviceGuard guard(b->p.device);
+  const BatchInst& d = b->desc[i];
+  const size_t cells = size_t(d.nx) * d.ny;
+  LBM_BCUDA(b, cudaMemcpyAsync(b->d_inst, b->desc.data(), b->count * sizeof(BatchInst),
+                               cudaMemcpyHostToDevice, b->stream));
+  const int items = ((d.nx + 31) / 32) * ((d.ny + 7) / 8);
+  const int grid = (items + kWorklistThreads / 32 - 1) / (kWorklistThreads / 32);
+  double* o = b->d_tmp;
+  if (d.scheme == LBM_SCHEME_NOFORCE)
+    batch_observe_kernel<kModeObserveNoForce><<<grid, kWorklistThreads, 0, b->stream>>>(
+        b->d_inst, i, b->buf[0], o, o + cells, o + 2 * cells, b->d_status);
+  else
+    batch_observe_kernel<kModeObserve><<<grid, kWorklistThreads, 0, b->stream>>>(
+        b->d_inst, i, b->buf[0], o, o + cells, o + 2 * cells, b->d_status);
+  LBM_BCUDA(b, cudaGetLastError());
+  count_launches(1);
+  double* host[3] = {rho, vx, vy};
+  for (int k = 0; k < 3; ++k)
+    if (host[k])
+      LBM_BCUDA(b, cudaMemcpyAsync(host[k], o + k * cells, cells * sizeof(double),
+                                   cudaMemcpyDeviceToHost, b->stream));
   LBM_BCUDA(b, cudaStreamSynchronize(b->stream));
   return LBM_OK;
 }

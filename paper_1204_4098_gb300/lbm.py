@@ -62,7 +62,7 @@ class lbm_batch_stats(ctypes.Structure):
 
 
 BATCH_AUTO, BATCH_WORKLIST, BATCH_PERSISTENT = range(3)
-CONV_COEX, CONV_CELL = range(2)
+CONV_COEX, CONV_CELL, CONV_NONE = range(3)
 RUN_ACTIVE, RUN_CONVERGED, RUN_DIVERGED, RUN_CAPPED = range(4)
 
 
@@ -109,6 +109,7 @@ SIGNATURES = {
     "lbm_batch_run": (_I, [_P, _I, _IP]),
     "lbm_batch_get_result": (_I, [_P, _I, ctypes.POINTER(lbm_result)]),
     "lbm_batch_get_density": (_I, [_P, _I, _P]),
+    "lbm_batch_get_moments": (_I, [_P, _I, _P, _P, _P]),
     "lbm_batch_get_stats": (_I, [_P, ctypes.POINTER(lbm_batch_stats)]),
     "lbm_batch_last_error": (ctypes.c_char_p, [_P]),
     "lbm_batch_destroy": (_I, [_P]),
@@ -388,6 +389,14 @@ class Batch:
         self._check(lib().lbm_batch_get_density(self.h, int(i), _dptr(rho)),
                     "lbm_batch_get_density")
         return rho
+
+    def moments(self, i):
+        """(rho, vx, vy) of instance i; v is the actual velocity u + F/(2 rho)."""
+        d = self.instances[i]
+        out = [np.empty((d["ny"], d["nx"])) for _ in range(3)]
+        self._check(lib().lbm_batch_get_moments(self.h, int(i), *[_dptr(a) for a in out]),
+                    "lbm_batch_get_moments")
+        return tuple(out)
 
     def stats(self):
         s = lbm_batch_stats()
