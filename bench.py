@@ -544,6 +544,29 @@ def run_stability_workload(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_calibrate_workload(args, world, rank, local):
+    """Sec. IV B automated: sigma*(T) where converged flat-interface slabs of
+    the improved scheme meet the Maxwell vapour density, T/Tc 0.65 .. 0.9."""
+    import numpy as np
+    import torch
+
+    from paper_1204_4098_gb300 import calibrate
+    torch.cuda.set_device(local)
+    temps = np.round(np.arange(0.65, 0.9001, 0.05), 2)
+    t0 = time.perf_counter()
+    out, info = calibrate.sigma_star(temps)
+    stars = [r["sigma_star"] for r in out if r["sigma_star"] is not None]
+    line = {"metric": METRIC, "workload": "sigma calibration against Maxwell (Sec. IV B)",
+            "value": float(np.mean(stars)) if stars else None,
+            "unit": "mean sigma* over T (paper: 0.105)", "higher_is_better": None,
+            "n_gpus": world, "data": "synthetic", "dtype": "f32", "gpu_s": info["gpu_s"],
+            "wall_s": time.perf_counter() - t0,
+            "sigma_star": [{"T_over_Tc": r["T_over_Tc"], "sigma_star": r["sigma_star"],
+                            "eps_star": r["eps_star"]} for r in out],
+            "curves": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -558,7 +581,7 @@ def main():
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--ref-side", type=int, default=384)
     ap.add_argument("--workload", choices=("roofline", "sweep", "warmstart", "droplets",
-                                           "stability"), default="roofline")
+                                           "stability", "calibrate"), default="roofline")
     ap.add_argument("--droplet-steps", type=int, default=20000)
     ap.add_argument("--stability-steps", type=int, default=20000)
     ap.add_argument("--stability-width", type=float, default=3.0)
@@ -582,6 +605,8 @@ def main():
         run_droplets_workload(args, world, rank, local)
     elif args.workload == "stability":
         run_stability_workload(args, world, rank, local)
+    elif args.workload == "calibrate":
+        run_calibrate_workload(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

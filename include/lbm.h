@@ -165,14 +165,15 @@ unsigned long long lbm_kernel_launch_count(void);
  * memory by asynchronous bulk copies several rows ahead (FP32 steps with
  * nx % 4 == 0 and nx >= 64; a bounded wait that gives up makes lbm_step
  * return LBM_E_TIMEOUT).  AUTO (default) = PAIR for even nx except with FP64
- * storage, else REGISTER.  A variant that does not apply falls back to
- * REGISTER. */
+ * storage or on lattices too small for its 64-column strips to occupy the
+ * GPU (about 512 x 512 and below), else REGISTER.  A variant that does not
+ * apply falls back to REGISTER. */
 enum { LBM_VARIANT_AUTO = 0, LBM_VARIANT_REGISTER = 1, LBM_VARIANT_STAGED = 2,
        LBM_VARIANT_PAIR = 3 };
 lbm_status lbm_set_kernel_variant(lbm_ctx *ctx, int variant);
 
 /* Rows per warp band of the step kernel (0 = automatic: one wave of warps,
- * at least 8 rows each).  Changes only speed, never results. */
+ * at least 4 rows each).  Changes only speed, never results. */
 lbm_status lbm_set_band_rows(lbm_ctx *ctx, int band_rows);
 
 /* The launch geometry lbm_step would use for `scheme`: column strips (32
