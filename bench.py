@@ -417,8 +417,18 @@ def run_warmstart_workload(args, world, rank, local):
                                           (args.epochs, 1e-4)), batch=128, seed=1)
     held = inputs.sweep_instances(args.held_out, seed=41, nx_range=(256, 256),
                                   ny_range=(256, 256))
-    warm, winfo = warmstart.run_warm(held, model)
+    warm, winfo = warmstart.run_warm(held, model)  # default rule: check after window 1
     cold, cinfo = warmstart.run_cold_batched(held)
+    other_rules = {}
+    for rule in ("converged", "diverged"):
+        w2, i2 = warmstart.run_warm(held, model, fallback=rule)
+        b2 = [k for k in range(len(held)) if w2[k]["status"] == 1 and cold[k]["status"] == 1]
+        t2, s2 = warmstart.time_to_answer(w2, i2, cold, among=b2)
+        e2, _ = _coex_agreement(w2, cold)
+        other_rules[rule] = {"fallbacks": i2["fallbacks"], "gpu_s": i2["gpu_ms"] / 1e3,
+                             "status": _status_counts(w2), "converged_in_both": len(b2),
+                             "time_to_answer_gpu_s": t2, "mean_steps_to_answer": s2,
+                             "coexistence_max_rel_err_vs_cold": e2}
     g, l = sweep.cold_start_profiles(held)
     ns = args.seq_sample
     seq, seq_wall = sweep.run_sequential(held[:ns], g[:ns], l[:ns], np.zeros(ns))
@@ -459,7 +469,11 @@ def run_warmstart_workload(args, world, rank, local):
             "cold_sequential": {"instances_timed": args.seq_sample, "wall_s": seq_wall,
                                 "wall_s_all": seq_all},
             "coexistence_max_rel_err_warm_vs_cold": err, "converged_in_both": n_both,
-            "speedup_warm_batched_vs_cold_batched": cinfo["wall"] / winfo["wall"]}
+            "speedup_warm_batched_vs_cold_batched": cinfo["wall"] / winfo["wall"],
+            "sweep_gpu_time_ratio_cold_sequential_over_warm_batched":
+                seq_all / (winfo["gpu_ms"] / 1e3),
+            "fallback_rule": "prediction error > 1e-2 after the first window, or divergence",
+            "other_fallback_rules": other_rules}
     print(json.dumps(line), flush=True)
 
 

@@ -216,7 +216,7 @@ enum { LBM_BATCH_AUTO = 0, LBM_BATCH_WORKLIST = 1, LBM_BATCH_PERSISTENT = 2 };
 /* Convergence rules.  CELL: every cell changed by less than
  * max(tol, 8 * 2^-23 * rho) over a window.  COEX: the coexistence densities
  * rho_g and rho_l (FP64 row means) each changed by less than
- * max(tol, 8 * 2^-23 * value) over two consecutive windows.  In FP32 the
+ * max(tol, conv_rel * value) over two consecutive windows.  In FP32 the
  * interface position of a relaxed slab jitters by ~1e-4 cells per window
  * (rounding noise driving a nearly neutral mode), so CELL is met only by
  * some runs; COEX tests what a sweep reports. */
@@ -238,6 +238,9 @@ typedef struct {
   int variant;          /* LBM_VARIANT_AUTO (default) or _PAIR: two columns per
                            lane for even nx; _REGISTER: one column per lane for
                            every instance.  Results are identical.             */
+  double conv_rel;      /* COEX: relative floor, changes below
+                           max(tol, conv_rel * value) count as calm (8 * 2^-23
+                           by default; must be >= 0)                           */
 } lbm_batch_params;
 
 typedef struct {

@@ -674,6 +674,7 @@ void lbm_batch_default_params(lbm_batch_params* p) {
   p->tol = 1e-9;
   p->max_steps = 200000;
   p->mode = LBM_BATCH_AUTO;
+  p->conv_rel = 8.0 * 1.1920928955078125e-7;  // 8 ulp of FP32
 }
 
 lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, int count,
@@ -682,7 +683,7 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
   *out = nullptr;
   if (p->window < 2 || p->window % 2 || p->max_steps < 1 || !(p->tol >= 0) ||
       p->mode < LBM_BATCH_AUTO || p->mode > LBM_BATCH_PERSISTENT || p->rows_per_item < 0 ||
-      p->conv < LBM_CONV_COEX || p->conv > LBM_CONV_NONE ||
+      p->conv < LBM_CONV_COEX || p->conv > LBM_CONV_NONE || !(p->conv_rel >= 0.0) ||
       !(p->variant == LBM_VARIANT_AUTO || p->variant == LBM_VARIANT_PAIR ||
         p->variant == LBM_VARIANT_REGISTER) ||
       !(p->G < 0) || !(p->a > 0) || !(p->b > 0) || !(p->R > 0) || p->tc_mode < 0 ||
@@ -978,7 +979,7 @@ lbm_status lbm_batch_run(lbm_batch* b, int max_windows, int* n_active) {
     if (b->p.mode == LBM_BATCH_AUTO && b->tuned)
       b->last_cost = ms * 1e6 / (double(cells) * b->p.window);
     std::vector<int> still;
-    const double floor32 = 8.0 * 1.1920928955078125e-7;
+    const double floor32 = b->p.conv_rel;
     for (int i : b->active) {
       lbm_result& r = b->res[i];
       const BatchOut& o = b->h_out[i];

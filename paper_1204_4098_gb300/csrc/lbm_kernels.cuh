@@ -323,34 +323,48 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
   const int hbase = lane & 16;
   bool bad = false;
 
-  // pulled populations of row y for both cells, plus this lane's extra element
-  auto load_row = [&](int y, C (&PA)[kQ], C (&PB)[kQ], C& h) {
+  // Row y is fetched in two phases: fetch_row issues the loads (raw vectors,
+  // this lane's extra element, deviation storage's density pairs) and
+  // assemble forms the pulled populations of both cells, which needs the
+  // loaded values in shuffles.  The main loop fetches row y + 2 before
+  // computing row y and assembles it afterwards, so the loads are in flight
+  // during a whole row's arithmetic instead of stalling the shuffles.
+  struct Raw {
+    V v[kQ];
+    C h;
+    float2 rr[3];
+  };
+  auto fetch_row = [&](int y, Raw& R) {
     const int ym = y == 0 ? ny - 1 : y - 1;
     const int yp = y == ny - 1 ? 0 : y + 1;
     const int rows[3] = {ym, y, yp};
     {
       int qy = y - qey;
       qy = qy < 0 ? qy + ny : (qy >= ny ? qy - ny : qy);
-      h = qlane ? pull_one<S, kCoherent>(A, qa, qy * nx + qsx) : C(0);
+      R.h = qlane ? pull_one<S, kCoherent>(A, qa, qy * nx + qsx) : C(0);
     }
-    // deviation storage: density plane pairs of the three source rows
-    float2 rr[3];
     if constexpr (S::kDev) {
 #pragma unroll
       for (int j = 0; j < 3; ++j)
-        rr[j] = load2<kCoherent>(
+        R.rr[j] = load2<kCoherent>(
             reinterpret_cast<const float2*>(A.rho_src + size_t(rows[j]) * nx + ca));
     }
 #pragma unroll
     for (int a = 0; a < kQ; ++a) {
-      const int ex = ex_of(a), ey = ey_of(a);
-      const int r = rows[1 - ey];  // source row y - ey
-      const V v =
+      const int r = rows[1 - ey_of(a)];  // source row y - ey
+      R.v[a] =
           load2<kCoherent>(reinterpret_cast<const V*>(A.src + a * A.plane + size_t(r) * nx + ca));
-      C lo = S::to_c(v.x), hi = S::to_c(v.y);  // pulled values at columns ca, ca + 1
+    }
+  };
+  auto assemble = [&](const Raw& R, C (&PA)[kQ], C (&PB)[kQ], C& h) {
+    h = R.h;
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) {
+      const int ex = ex_of(a), ey = ey_of(a);
+      C lo = S::to_c(R.v[a].x), hi = S::to_c(R.v[a].y);  // pulled values at ca, ca + 1
       if constexpr (S::kDev) {
-        lo = fma_rn(w_of<C>(a), C(rr[1 - ey].x), lo);
-        hi = fma_rn(w_of<C>(a), C(rr[1 - ey].y), hi);
+        lo = fma_rn(w_of<C>(a), C(R.rr[1 - ey].x), lo);
+        hi = fma_rn(w_of<C>(a), C(R.rr[1 - ey].y), hi);
       }
       if (ex == 0) {
         PA[a] = lo;
@@ -369,6 +383,11 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
         PB[a] = lane == 31 ? fromR : dn;
       }
     }
+  };
+  auto load_row = [&](int y, C (&PA)[kQ], C (&PB)[kQ], C& h) {
+    Raw R;
+    fetch_row(y, R);
+    assemble(R, PA, PB, h);
   };
   auto rho_of = [](const C (&P)[kQ]) {
     C r = P[0];
@@ -405,8 +424,8 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
     Fy = mul_rn(gpsi, sy);
   };
 
-  C PA0[kQ], PB0[kQ], PA1[kQ], PB1[kQ], PA2[kQ], PB2[kQ];
-  C h1 = C(0), h2 = C(0);
+  C PA0[kQ], PB0[kQ], PA1[kQ], PB1[kQ];
+  C h1 = C(0);
   // psi ring per row: (Wa, Ca, Cb, Eb) for rows y-1 (m), y (z)
   C Wam = 0, Cam = 0, Cbm = 0, Ebm = 0, Waz = 0, Caz = 0, Cbz = 0, Ebz = 0;
   C ra0, rb0;
@@ -418,8 +437,10 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
     psi_row(PA0, PB0, h1, Waz, Caz, Cbz, Ebz, ra0, rb0);
     load_row(y0 + 1 == ny ? 0 : y0 + 1, PA1, PB1, h1);
   }
+  Raw next;
   for (int y = y0; y < y1; ++y) {
-    if (y + 2 <= y1) load_row(y + 2 >= ny ? y + 2 - ny : y + 2, PA2, PB2, h2);
+    const bool more = y + 2 <= y1;
+    if (more) fetch_row(y + 2 >= ny ? y + 2 - ny : y + 2, next);
     C Wap = 0, Cap = 0, Cbp = 0, Ebp = 0, ra1, rb1;
     psi_row(PA1, PB1, h1, Wap, Cap, Cbp, Ebp, ra1, rb1);
     C Fxa = C(0), Fya = C(0), Fxb = C(0), Fyb = C(0);
@@ -475,16 +496,16 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
     rb0 = rb1;
 #pragma unroll
     for (int a = 0; a < kQ; ++a) {
-      PA0[a] = PA1[a]; PB0[a] = PB1[a];
-      PA1[a] = PA2[a]; PB1[a] = PB2[a];
+      PA0[a] = PA1[a];
+      PB0[a] = PB1[a];
     }
-    h1 = h2;
+    if (more) assemble(next, PA1, PB1, h1);  // warp-uniform
   }
   if (__any_sync(FULL, bad) && lane == 0) atomicOr(A.status, kStatusDiverged);
 }
 
 #ifndef LBM_STRIP2_MIN_BLOCKS
-#define LBM_STRIP2_MIN_BLOCKS 5
+#define LBM_STRIP2_MIN_BLOCKS 4  // 128 registers: the fetched row and the two assembled rows
 #endif
 
 template <class S, int SCHEME, int MODE>

@@ -46,7 +46,7 @@ class lbm_batch_params(ctypes.Structure):
                 ("cuda_stream", ctypes.c_void_p), ("window", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_steps", ctypes.c_int), ("mode", ctypes.c_int),
                 ("rows_per_item", ctypes.c_int), ("conv", ctypes.c_int),
-                ("variant", ctypes.c_int)]
+                ("variant", ctypes.c_int), ("conv_rel", ctypes.c_double)]
 
 
 class lbm_result(ctypes.Structure):
@@ -311,11 +311,13 @@ class Batch:
 
     def __init__(self, instances, window=1000, tol=1e-9, max_steps=200000, mode=BATCH_AUTO,
                  rows_per_item=0, tc_mode=0, device=0, stream=None, conv=CONV_COEX,
-                 variant=VARIANT_AUTO):
+                 variant=VARIANT_AUTO, conv_rel=None):
         p = lbm_batch_params()
         lib().lbm_batch_default_params(ctypes.byref(p))
         p.window, p.tol, p.max_steps, p.conv = int(window), float(tol), int(max_steps), int(conv)
         p.variant = int(variant)
+        if conv_rel is not None:
+            p.conv_rel = float(conv_rel)
         p.mode, p.rows_per_item, p.tc_mode, p.device = int(mode), int(rows_per_item), \
             int(tc_mode), int(device)
         p.cuda_stream = None if stream is None else ctypes.c_void_p(int(stream))

@@ -33,13 +33,13 @@ def cold_start_profiles(instances, tc_mode=0):
 
 def run_batched(instances, rho_g, rho_l, width, window=1000, tol=1e-9, max_steps=200000,
                 mode=lbm.BATCH_AUTO, rows_per_item=0, device=0, stream=None,
-                conv=lbm.CONV_COEX):
+                conv=lbm.CONV_COEX, conv_rel=None):
     """Run every instance to convergence in one batch; returns (results, stats,
     wall seconds).  width <= 0 starts from a sharp slab."""
     t0 = time.perf_counter()
     with lbm.Batch(instances, window=window, tol=tol, max_steps=max_steps, mode=mode,
                    rows_per_item=rows_per_item, device=device, stream=stream,
-                   conv=conv) as b:
+                   conv=conv, conv_rel=conv_rel) as b:
         b.init_slabs(rho_g, rho_l, width)
         b.run()
         res, stats = b.results(), b.stats()
@@ -88,17 +88,21 @@ def _coexistence(rho):
     return 0.5 * (rows[0] + rows[-1]), 0.5 * (rows[lo] + rows[ny // 2])
 
 
-def _calm(new, old, tol):
-    return abs(new - old) < max(tol, 8 * F32_EPS * abs(new))
+COEX_REL = 8 * F32_EPS  # the batch engine's default relative floor
+
+
+def _calm(new, old, tol, rel=COEX_REL):
+    return abs(new - old) < max(tol, rel * abs(new))
 
 
 def run_sequential(instances, rho_g, rho_l, width, window=1000, tol=1e-9, max_steps=200000,
-                   device=0, conv=lbm.CONV_COEX):
+                   device=0, conv=lbm.CONV_COEX, conv_rel=None):
     """Plain runs, one instance after another, through lbm_step; convergence
     is checked on the host with the batch engine's rules (CONV_COEX: rho_g
-    and rho_l each changed by less than max(tol, 8 eps_32 value) over two
+    and rho_l each changed by less than max(tol, conv_rel value) over two
     consecutive windows; CONV_CELL: every cell by less than
     max(tol, 8 eps_32 rho) over a window).  Returns (results, wall seconds)."""
+    rel = COEX_REL if conv_rel is None else conv_rel
     out = []
     t0 = time.perf_counter()
     for k, d in enumerate(instances):
@@ -123,8 +127,8 @@ def run_sequential(instances, rho_g, rho_l, width, window=1000, tol=1e-9, max_st
                     break
                 rho = lat.observe()[0]
                 c = _coexistence(rho)
-                calm = calm + 1 if prev_c is not None and _calm(c[0], prev_c[0], tol) and \
-                    _calm(c[1], prev_c[1], tol) else 0
+                calm = calm + 1 if prev_c is not None and _calm(c[0], prev_c[0], tol, rel) and \
+                    _calm(c[1], prev_c[1], tol, rel) else 0
                 cell = np.all(np.abs(rho - prev) < np.maximum(tol, 8 * F32_EPS * np.abs(rho)))
                 if not np.all(np.isfinite(rho)):
                     status = lbm.RUN_DIVERGED

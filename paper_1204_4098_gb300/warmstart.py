@@ -4,14 +4,16 @@ A 4 -> 64 -> 64 -> 3 network (lbm_mlp_*, trained on the GPU by the
 library's kernels) maps a sweep point (T/Tc, tau, sigma, scheme) to the
 relaxed slab's (rho_l, rho_g, interface width W).  New runs then start from
 the Eq. 36 profile with the predicted values instead of the Maxwell step
-(cold start).  Fallback: when the prediction error exceeds 1e-2 -- the warm
-run's converged rho_l or rho_g differs from the prediction by more than 1e-2
-(relative) -- or the warm run diverges, the instance restarts cold and the
-steps already spent are counted.  (The state after the first window is not
-a usable estimate of that error: the interface relaxing from the initial
-tanh profile moves the bulk densities by ~0.5-1 % for a while even when the
-prediction is right to 1e-3.)  Cold runs remain the judge of the error: the
-tests and the sweep report compare warm and cold coexistence densities.
+(cold start).  Fallback: a warm run that diverges restarts cold, and so
+does one whose prediction error exceeds 1e-2 -- its rho_l or rho_g differs
+from the prediction by more than 1e-2 (relative) -- checked after its first
+window (default), when it has converged, or not at all (run_warm's
+`fallback`); the steps already spent are counted.  (After the first window
+the interface relaxing from the initial tanh profile still moves the bulk
+densities by ~0.5-1 % even when the prediction is right to 1e-3, so the
+first-window check also restarts some good predictions; it is the cheapest
+point to restart.)  Cold runs remain the judge of the error: the tests and
+the sweep report compare warm and cold coexistence densities.
 
 Inputs are scaled to [-1, 1] over the sweep ranges.  The network learns
 the answer relative to the Maxwell construction at the same temperature
@@ -72,14 +74,15 @@ def targets(instances, rho_l, rho_g, width):
                      np.log(np.asarray(width))], 1)
 
 
-def training_data(n_draws, seed=40, ny_range=(128, 512), max_steps=100000, window=1000):
+def training_data(n_draws, seed=40, ny_range=(128, 512), max_steps=100000, window=1000,
+                  conv_rel=None):
     """Cold batched runs of narrow (nx = 32) slabs drawn from the sweep
     distribution; the converged ones give (features, targets).  Slabs are
     x-invariant, so the width of the lattice does not change the answer."""
     inst = inputs.sweep_instances(n_draws, seed=seed, nx_range=(32, 32), ny_range=ny_range)
     g, l = sweep.cold_start_profiles(inst)
     res, stats, wall = sweep.run_batched(inst, g, l, np.zeros(len(inst)), window=window,
-                                         max_steps=max_steps)
+                                         max_steps=max_steps, conv_rel=conv_rel)
     keep = [k for k, r in enumerate(res)
             if r["status"] == lbm.RUN_CONVERGED and r["rho_g"] > 0 and r["width"] > 0]
     kept = [inst[k] for k in keep]
@@ -106,13 +109,20 @@ def train(X, Y, stages=((1500, 2e-3), (1500, 5e-4), (1500, 1e-4)), batch=128, se
 
 
 def run_warm(instances, model, window=1000, tol=1e-9, max_steps=200000, fallback_tol=1e-2,
-             device=0):
+             device=0, conv_rel=None, fallback="first_window"):
     """Warm-started batched runs with the cold-start fallback, checked after
-    every window: a warm run that diverges, or converges to coexistence
-    densities more than fallback_tol away from its prediction, restarts at
-    once from the cold start (its steps so far are counted; a run falls back
-    at most once).  Returns (results, info); results carry per-window
-    histories of the run that produced the answer."""
+    every window.  A warm run that diverges restarts at once from the cold
+    start (its steps so far are counted; a run falls back at most once).  The
+    prediction-error check (relative difference of rho_l or rho_g from the
+    prediction above fallback_tol) is taken, by `fallback`:
+      "first_window" -- after the first window (default: a restart then
+                        wastes one window);
+      "converged"    -- when the warm run has converged;
+      "diverged"     -- never (divergence only).
+    Returns (results, info); results carry per-window histories of the run
+    that produced the answer."""
+    if fallback not in ("converged", "first_window", "diverged"):
+        raise ValueError(f"unknown fallback rule {fallback!r}")
     pl, pg, pw = model.predict(instances)
     cg, cl = sweep.cold_start_profiles(instances)
     # the network never saw unstable points; keep its answers in a plausible
@@ -124,8 +134,9 @@ def run_warm(instances, model, window=1000, tol=1e-9, max_steps=200000, fallback
     n = len(instances)
     hist = [[] for _ in range(n)]
     times = []
-    fallback = set()
-    with lbm.Batch(instances, window=window, tol=tol, max_steps=max_steps, device=device) as b:
+    fell = set()
+    with lbm.Batch(instances, window=window, tol=tol, max_steps=max_steps, device=device,
+                   conv_rel=conv_rel) as b:
         b.init_slabs(pg, pl, pw)
         active = set(range(n))
         while active:
@@ -134,31 +145,33 @@ def run_warm(instances, model, window=1000, tol=1e-9, max_steps=200000, fallback
             for k in list(active):
                 r = b.result(k)
                 hist[k].append((r["steps"], r["rho_g"], r["rho_l"], len(times) - 1))
-                if r["status"] == lbm.RUN_ACTIVE:
-                    continue
-                bad = k not in fallback and (r["status"] == lbm.RUN_DIVERGED or (
-                    r["status"] == lbm.RUN_CONVERGED and
-                    (abs(r["rho_l"] / pl[k] - 1) > fallback_tol or
-                     abs(r["rho_g"] / pg[k] - 1) > fallback_tol)))
+                off = (abs(r["rho_l"] / pl[k] - 1) > fallback_tol or
+                       abs(r["rho_g"] / pg[k] - 1) > fallback_tol)
+                check = (fallback == "converged" and r["status"] == lbm.RUN_CONVERGED) or \
+                    (fallback == "first_window" and len(hist[k]) == 1 and
+                     r["status"] != lbm.RUN_DIVERGED)
+                bad = k not in fell and (r["status"] == lbm.RUN_DIVERGED or (check and off))
                 if bad:
                     d = instances[k]
-                    fallback.add(k)
+                    fell.add(k)
                     hist[k] = []
                     b.init_density(k, inputs.slab_step(d["nx"], d["ny"], cg[k], cl[k]))
-                else:
+                elif r["status"] != lbm.RUN_ACTIVE:
                     active.discard(k)
         res, stats = b.results(), b.stats()
     for k, r in enumerate(res):
-        r["fallback"] = k in fallback
+        r["fallback"] = k in fell
         r["history"] = hist[k]
     return res, dict(gpu_ms=stats["gpu_ms"], wall=time.perf_counter() - t0,
-                     fallbacks=len(fallback), predicted=(pl, pg, pw), window_times=times)
+                     fallbacks=len(fell), predicted=(pl, pg, pw), window_times=times)
 
 
-def run_cold_batched(instances, window=1000, tol=1e-9, max_steps=200000, device=0):
+def run_cold_batched(instances, window=1000, tol=1e-9, max_steps=200000, device=0,
+                     conv_rel=None):
     cg, cl = sweep.cold_start_profiles(instances)
     t0 = time.perf_counter()
-    with lbm.Batch(instances, window=window, tol=tol, max_steps=max_steps, device=device) as b:
+    with lbm.Batch(instances, window=window, tol=tol, max_steps=max_steps, device=device,
+                   conv_rel=conv_rel) as b:
         b.init_slabs(cg, cl, np.zeros(len(instances)))
         hist, times = sweep.run_batch_with_history(b)
         res, stats = b.results(), b.stats()
