@@ -49,6 +49,9 @@ MEASURED_TRAFFIC = {
     # ncu launch list, 25 launches of strip2_kernel<StoreF32, improved, step>
     # at 8192^2: 2.431 GB read + 2.368 GB written per launch
     ("c8b20c715c92ee44", "fp32", 8192): 4.7996e9,
+    # the same after the fetch / assemble split of the row loads (4 CTAs/SM):
+    # 2.431 GB read + 2.368 GB written per launch
+    ("a776dde1b00b0c71", "fp32", 8192): 4.7986e9,
 }
 
 
