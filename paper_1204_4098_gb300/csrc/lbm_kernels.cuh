@@ -278,9 +278,6 @@ template <> struct Vec2<double> { using type = double2; };
 template <> struct Vec2<__nv_bfloat16> { using type = __nv_bfloat162; };
 template <> struct Vec2<__half> { using type = __half2; };
 
-#ifndef LBM_STRIP2_FETCH_AHEAD
-#define LBM_STRIP2_FETCH_AHEAD 1  // rows fetched ahead of the one being assembled
-#endif
 template <bool kCoherent, class V>
 __device__ __forceinline__ V load2(const V* p) {
   if constexpr (kCoherent) return __ldcg(p);
@@ -440,20 +437,10 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
     psi_row(PA0, PB0, h1, Waz, Caz, Cbz, Ebz, ra0, rb0);
     load_row(y0 + 1 == ny ? 0 : y0 + 1, PA1, PB1, h1);
   }
-  auto wrap = [&](int r) { return r >= ny ? r - ny : r; };
   Raw next;
-#if LBM_STRIP2_FETCH_AHEAD == 2
-  // two rows in flight: row y + 3 is fetched at y, assembled at y + 1
-  Raw later;
-  if (y0 + 2 <= y1) fetch_row(wrap(y0 + 2), next);
-#endif
   for (int y = y0; y < y1; ++y) {
     const bool more = y + 2 <= y1;
-#if LBM_STRIP2_FETCH_AHEAD == 2
-    if (y + 3 <= y1) fetch_row(wrap(y + 3), later);
-#else
-    if (more) fetch_row(wrap(y + 2), next);
-#endif
+    if (more) fetch_row(y + 2 >= ny ? y + 2 - ny : y + 2, next);
     C Wap = 0, Cap = 0, Cbp = 0, Ebp = 0, ra1, rb1;
     psi_row(PA1, PB1, h1, Wap, Cap, Cbp, Ebp, ra1, rb1);
     C Fxa = C(0), Fya = C(0), Fxb = C(0), Fyb = C(0);
@@ -513,9 +500,6 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
       PB0[a] = PB1[a];
     }
     if (more) assemble(next, PA1, PB1, h1);  // warp-uniform
-#if LBM_STRIP2_FETCH_AHEAD == 2
-    next = later;
-#endif
   }
   if (__any_sync(FULL, bad) && lane == 0) atomicOr(A.status, kStatusDiverged);
 }
