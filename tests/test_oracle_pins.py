@@ -89,3 +89,29 @@ def test_tau_dependence_sc_vs_improved(lib):
     assert spread["improved"] < 1e-4, spread
     assert rg_at["SC"][0] < rg_at["SC"][1] < rg_at["SC"][2]
     assert rg_at["EDM"][1] == pytest.approx(rg_at["SC"][1], rel=1e-12)
+
+
+def test_laplace_law_on_droplets(lib):
+    """Laplace's law (north star check (b)): relaxed droplets of four radii
+    (Eq. 24 start, 64 x 64, T = 0.8 Tc, improved scheme sigma = 0.1, tau = 1);
+    the pressure jump p_EOS(rho_in) - p_EOS(rho_out) is linear in 1/R, R the
+    equivalent-area radius, with an intercept small against the jumps."""
+    from paper_1204_4098_gb300 import inputs
+    n, t = 64, 0.8
+    eos = th.CarnahanStarling(th.temperature(t))
+    rg, rl, _ = th.maxwell(eos)
+    inv_r, dp = [], []
+    for r0 in (9, 12, 15, 18):
+        lat = oracle.Lattice(n, n, t, lib=lib)
+        lat.init_density(inputs.droplet(n, n, rg, rl, r0, W=5.0))
+        assert lat.step(4000, oracle.IMPROVED, 1.0, 0.1)[0] == 0
+        rho, _, _ = lat.observe()
+        r_in, r_out = rho[n // 2, n // 2], rho[0, 0]
+        inv_r.append(1.0 / np.sqrt((rho - r_out).sum() / (r_in - r_out) / np.pi))
+        dp.append(eos.p(r_in) - eos.p(r_out))
+    x, y = np.array(inv_r), np.array(dp)
+    slope, icpt = np.polyfit(x, y, 1)
+    resid = y - (slope * x + icpt)
+    r2 = 1.0 - resid @ resid / ((y - y.mean()) @ (y - y.mean()))
+    assert slope > 0 and r2 > 0.999, (slope, r2)
+    assert abs(icpt) < 0.05 * slope * x.min(), (icpt, slope)
