@@ -235,6 +235,8 @@ def run_ours(args, world, rank, local):
     cells = n * n
 
     lat = lbm.Lattice(n, n, 0.85, precision=prec, device=local, stream=stream.cuda_stream)
+    lat.set_variant({"auto": lbm.VARIANT_AUTO, "register": lbm.VARIANT_REGISTER,
+                     "pair": lbm.VARIANT_PAIR, "staged": lbm.VARIANT_STAGED}[args.kernel_variant])
     lat.init_density(rho0)
     lat.step_async(args.warmup, lbm.IMPROVED, 0.8, 0.1)
     assert lat.sync() == lbm.LBM_OK
@@ -608,6 +610,8 @@ def main():
     ap.add_argument("--epochs", type=int, default=1500)
     ap.add_argument("--held-out", type=int, default=256)
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--kernel-variant", choices=("auto", "register", "pair", "staged"),
+                    default="auto", help="step kernel of the roofline run")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
