@@ -41,17 +41,18 @@ KERNEL_SOURCES = ["lbm_device.cuh", "lbm_kernels.cuh", "lbm_launch.cuh"]
 STORE_NAMES = {"fp32": "StoreF32", "fp64": "StoreF64", "bf16dev": "StoreBF16",
                "fp16dev": "StoreF16"}
 # DRAM bytes per launch of the step kernel from an ncu capture, keyed by the
-# hash of the kernel sources it was taken on (null once they change).
+# hash of the kernel sources it was taken on (null once they change), the
+# storage type, the lattice side and the kernel variant.
 MEASURED_TRAFFIC = {
     # ncu launch list, 25 launches of strip_kernel<StoreF32, improved, step> at
     # 8192^2: 2.437 GB read + 2.370 GB written per launch
-    ("8a40f73e27882b9d", "fp32", 8192): 4.807e9,
+    ("8a40f73e27882b9d", "fp32", 8192, "register"): 4.807e9,
     # ncu launch list, 25 launches of strip2_kernel<StoreF32, improved, step>
     # at 8192^2: 2.431 GB read + 2.368 GB written per launch
-    ("c8b20c715c92ee44", "fp32", 8192): 4.7996e9,
+    ("c8b20c715c92ee44", "fp32", 8192, "pair"): 4.7996e9,
     # the same after the fetch / assemble split of the row loads (4 CTAs/SM):
     # 2.431 GB read + 2.368 GB written per launch
-    ("a776dde1b00b0c71", "fp32", 8192): 4.7986e9,
+    ("a776dde1b00b0c71", "fp32", 8192, "pair"): 4.7986e9,
 }
 
 
@@ -271,7 +272,9 @@ def run_ours(args, world, rank, local):
     bpc = BYTES_PER_CELL[args.precision]
     achieved = bpc * cells / per_launch_s / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = MEASURED_TRAFFIC.get((kernel_source_hash(), args.precision, n))
+    vname = {lbm.VARIANT_REGISTER: "register", lbm.VARIANT_PAIR: "pair",
+             lbm.VARIANT_STAGED: "staged"}.get(variant_used, "register")
+    traffic = MEASURED_TRAFFIC.get((kernel_source_hash(), args.precision, n, vname))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": {lbm.VARIANT_PAIR: "strip2_kernel", lbm.VARIANT_STAGED:
