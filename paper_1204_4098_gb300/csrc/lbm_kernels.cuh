@@ -19,6 +19,10 @@
 // brought into L2.  Periodic wrap is applied to the indices, so any nx, ny
 // >= 1 works; lanes past the right edge of a ragged strip evaluate the
 // wrapped columns (serving as the right neighbour) and store nothing.
+// strip_run / strip_kernel below is this design with one column per lane;
+// strip_run2 / strip2_kernel gives each lane two adjacent columns of a
+// 64-column strip (even nx), and strip_tma_kernel stages the rows in shared
+// memory with bulk copies.  All three compute the same values bit for bit.
 #pragma once
 
 #include "lbm_device.cuh"
@@ -261,12 +265,13 @@ strip_kernel(const StripArgs<S> A) {
 }
 
 // ---------------------------------------------------------------------------
-// Two columns per lane (direct storage, even nx)
+// Two columns per lane (even nx, every storage type)
 // ---------------------------------------------------------------------------
 // The same computation with lane l owning columns x0 + 2l and x0 + 2l + 1 of
-// a 64-column strip: populations move as 8-byte (float2 / double2) vectors,
-// and the per-row overhead (indices, halo psi, shuffles, loop control) is
-// shared by two cells.  A pull with e_x = +1 takes the left cell's value from
+// a 64-column strip: populations move as vectors of two (float2, double2,
+// bf16x2, half2; deviation storage's density plane as float2), and the
+// per-row overhead (indices, halo psi, shuffles, loop control) is shared by
+// two cells.  A pull with e_x = +1 takes the left cell's value from
 // the previous lane's upper element (shuffle), e_x = -1 the right cell's from
 // the next lane's lower element; the strip's two boundary lanes get those
 // elements, and the halo densities, from one extra load spread over lanes
