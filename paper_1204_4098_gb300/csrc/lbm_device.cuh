@@ -228,6 +228,13 @@ struct StoreBF16 {
   static constexpr bool kDev = true;
   static __device__ __forceinline__ C to_c(T v) { return __bfloat162float(v); }
   static __device__ __forceinline__ T from_c(C v) { return __float2bfloat16_rn(v); }
+  // two at a time (one packed conversion; the same values as to_c / from_c)
+  static __device__ __forceinline__ float2 to_c2(__nv_bfloat162 v) {
+    return __bfloat1622float2(v);
+  }
+  static __device__ __forceinline__ __nv_bfloat162 from_c2(C a, C b) {
+    return __floats2bfloat162_rn(a, b);
+  }
 };
 struct StoreF16 {
   using T = __half;
@@ -235,6 +242,8 @@ struct StoreF16 {
   static constexpr bool kDev = true;
   static __device__ __forceinline__ C to_c(T v) { return __half2float(v); }
   static __device__ __forceinline__ T from_c(C v) { return __float2half_rn(v); }
+  static __device__ __forceinline__ float2 to_c2(__half2 v) { return __half22float2(v); }
+  static __device__ __forceinline__ __half2 from_c2(C a, C b) { return __floats2half2_rn(a, b); }
 };
 
 // Device status bits (same values as the kStatus*Flag constants of the host).

@@ -366,10 +366,14 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
 #pragma unroll
     for (int a = 0; a < kQ; ++a) {
       const int ex = ex_of(a), ey = ey_of(a);
-      C lo = S::to_c(R.v[a].x), hi = S::to_c(R.v[a].y);  // pulled values at ca, ca + 1
+      C lo, hi;  // pulled values at ca, ca + 1
       if constexpr (S::kDev) {
-        lo = fma_rn(w_of<C>(a), C(R.rr[1 - ey].x), lo);
-        hi = fma_rn(w_of<C>(a), C(R.rr[1 - ey].y), hi);
+        const float2 d = S::to_c2(R.v[a]);
+        lo = fma_rn(w_of<C>(a), C(R.rr[1 - ey].x), d.x);
+        hi = fma_rn(w_of<C>(a), C(R.rr[1 - ey].y), d.y);
+      } else {
+        lo = S::to_c(R.v[a].x);
+        hi = S::to_c(R.v[a].y);
       }
       if (ex == 0) {
         PA[a] = lo;
@@ -463,14 +467,12 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
           C resa = ra0, resb = rb0;
 #pragma unroll
           for (int a = 0; a < kQ; ++a) {
-            const T da = S::from_c(sub_rn(PA0[a], mul_rn(w_of<C>(a), ra0)));
-            const T db = S::from_c(sub_rn(PB0[a], mul_rn(w_of<C>(a), rb0)));
-            V v;
-            v.x = da;
-            v.y = db;
+            const V v = S::from_c2(sub_rn(PA0[a], mul_rn(w_of<C>(a), ra0)),
+                                   sub_rn(PB0[a], mul_rn(w_of<C>(a), rb0)));
             *reinterpret_cast<V*>(A.dst + a * A.plane + idx) = v;
-            resa = sub_rn(resa, S::to_c(da));
-            resb = sub_rn(resb, S::to_c(db));
+            const float2 d = S::to_c2(v);
+            resa = sub_rn(resa, d.x);
+            resb = sub_rn(resb, d.y);
           }
           *reinterpret_cast<float2*>(A.rho_dst + idx) = make_float2(float(resa), float(resb));
         } else {
