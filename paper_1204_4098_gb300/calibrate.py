@@ -21,11 +21,15 @@ from . import lbm, sweep
 
 
 def _crossing(sig, val, target):
-    """Linear interpolation of the first crossing of val(sig) = target."""
+    """Linear interpolation of the first crossing of val(sig) = target over
+    the points with a finite value (runs that failed are skipped)."""
+    sig, val = np.asarray(sig, dtype=float), np.asarray(val, dtype=float)
+    keep = np.isfinite(val)
+    sig, val = sig[keep], val[keep]
     for k in range(len(sig) - 1):
         a, b = val[k] - target, val[k + 1] - target
-        if np.isfinite(a) and np.isfinite(b) and a * b <= 0 and a != b:
-            return sig[k] + (sig[k + 1] - sig[k]) * a / (a - b)
+        if a * b <= 0 and a != b:
+            return float(sig[k] + (sig[k + 1] - sig[k]) * a / (a - b))
     return None
 
 

@@ -1,0 +1,92 @@
+"""Host-side logic of the sweep workloads on synthetic inputs (no GPU):
+droplet observables and fits, stability ladders, the sigma crossing, the
+coexistence read-out and convergence test of the sequential baseline."""
+import numpy as np
+import pytest
+
+from oracle import theory as th
+from paper_1204_4098_gb300 import calibrate, droplets, inputs, lbm, sweep, warmstart
+
+
+def test_p_eos_matches_oracle_theory():
+    eos = th.CarnahanStarling(0.08)
+    rho = np.linspace(0.01, 0.45, 37)
+    assert np.allclose(droplets.p_eos(rho, 0.08), eos.p(rho), rtol=1e-14, atol=0)
+
+
+def test_droplet_observables_of_an_eq24_profile():
+    """A sharp Eq. 24 droplet has centre/corner densities rho_l/rho_g and an
+    equivalent-area radius close to r0; its pressure jump is the EOS one."""
+    n, r0, rg, rl, T = 128, 30.0, 0.02, 0.3, 0.08
+    rho = inputs.droplet(n, n, rg, rl, r0, W=0.5)
+    z = np.zeros_like(rho)
+    obs = droplets.observables(rho, z, z, T)
+    assert obs["rho_in"] == pytest.approx(rl, rel=1e-12)
+    assert obs["rho_out"] == pytest.approx(rg, rel=1e-9)
+    assert obs["radius"] == pytest.approx(r0, rel=5e-3)
+    assert obs["dp"] == pytest.approx(droplets.p_eos(rl, T) - droplets.p_eos(rg, T))
+    assert obs["max_speed"] == 0.0
+
+
+def test_laplace_fit_recovers_a_linear_law():
+    inst = droplets.laplace_instances(n=64, radii=(10, 15, 20, 25), temps=(0.8,), taus=(1.0,),
+                                      schemes=((lbm.SC, 0.0),))
+    gamma, c = 3e-3, 1e-6
+    res = [{"status": lbm.RUN_CAPPED, "steps": 10, "rho_in": 0.3, "rho_out": 0.02,
+            "radius": d["r0"] * 0.98, "dp": gamma / (d["r0"] * 0.98) + c, "max_speed": 1e-3}
+           for d in inst]
+    fit = droplets.laplace_fits(inst, res)[(0.8, 1.0, lbm.SC, 0.0)]
+    assert fit["surface_tension"] == pytest.approx(gamma, rel=1e-9)
+    assert fit["intercept"] == pytest.approx(c, rel=1e-6)
+    assert fit["r2"] == pytest.approx(1.0, abs=1e-12)
+    res[1] = {"status": lbm.RUN_DIVERGED, "steps": 10}
+    assert droplets.laplace_fits(inst, res)[(0.8, 1.0, lbm.SC, 0.0)] is None
+    res[1] = dict(res[0], radius=0.0, rho_in=0.02)  # dissolved
+    assert droplets.laplace_fits(inst, res)[(0.8, 1.0, lbm.SC, 0.0)] is None
+
+
+def test_thresholds_take_the_lowest_contiguous_stable_temperature():
+    temps = [0.9, 0.8, 0.7, 0.6, 0.5]
+    inst = droplets.stability_instances(((lbm.EDM, 0.0),), (0.6,), temps)
+    ok = {"status": lbm.RUN_CAPPED, "max_speed": 0.01}
+    bad = {"status": lbm.RUN_DIVERGED}
+    fast = {"status": lbm.RUN_CAPPED, "max_speed": 0.5}  # over the 0.3 criterion
+    res = [ok, ok, bad, ok, ok]  # 0.6 and 0.5 stable again below a failure
+    assert droplets.thresholds(inst, res)[(lbm.EDM, 0.0, 0.6)] == 0.8
+    res = [ok, ok, ok, fast, ok]
+    assert droplets.thresholds(inst, res)[(lbm.EDM, 0.0, 0.6)] == 0.7
+    res = [bad] + [ok] * 4
+    assert droplets.thresholds(inst, res)[(lbm.EDM, 0.0, 0.6)] is None
+
+
+def test_sigma_crossing_interpolates_linearly():
+    sig = np.array([0.08, 0.09, 0.10, 0.11])
+    val = 0.01 + 0.1 * (sig - 0.08)
+    target = 0.01 + 0.1 * (0.0975 - 0.08)
+    assert calibrate._crossing(sig, val, target) == pytest.approx(0.0975, rel=1e-12)
+    val_nan = val.copy()
+    val_nan[1] = np.nan
+    assert calibrate._crossing(sig, val_nan, target) == pytest.approx(0.0975, rel=1e-12)
+    assert calibrate._crossing(sig, val, 1.0) is None
+
+
+def test_coexistence_readout_and_calm_rule():
+    rho = inputs.slab_step(8, 16, 0.02, 0.3)
+    g, l = sweep._coexistence(rho)
+    assert (g, l) == (0.02, 0.3)
+    assert sweep._calm(0.3, 0.3 + 1e-9, 1e-9 * 2)
+    assert not sweep._calm(0.3, 0.3 + 1e-6, 1e-9)
+    assert sweep._calm(0.3, 0.3 + 1e-6, 1e-9, rel=1e-5)
+
+
+def test_warm_start_rejects_an_unknown_fallback_rule():
+    with pytest.raises(ValueError):
+        warmstart.run_warm([], None, fallback="sometimes")
+
+
+def test_shard_balances_cells_and_covers_every_instance():
+    inst = inputs.sweep_instances(40, seed=7)
+    parts = [sweep.shard(inst, 3, r) for r in range(3)]
+    assert sorted(i for p in parts for i in p) == list(range(40))
+    loads = [sum(inst[i]["nx"] * inst[i]["ny"] for i in p) for p in parts]
+    assert max(loads) - min(loads) <= max(d["nx"] * d["ny"] for d in inst)
