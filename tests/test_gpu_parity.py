@@ -340,3 +340,24 @@ def test_pair_kernel_matches_register_kernel_bitwise(precision, nx, ny):
         for o in out[1:]:
             for a, b in zip(o, out[0]):
                 assert np.array_equal(a, b), (scheme, variant)
+
+
+def test_auto_variant_choice():
+    """AUTO: two columns per lane for even nx on lattices large enough to occupy
+    the GPU with 64-column strips, one column per lane otherwise (odd nx, FP64,
+    small lattices); an explicit variant is honoured where it applies."""
+    def variant(nx, ny, precision=lbm.FP32, want=None):
+        g = lbm.Lattice(nx, ny, 0.85, precision=precision)
+        if want is not None:
+            g.set_variant(want)
+        v = g.variant()
+        g.close()
+        return v
+    assert variant(1024, 1024) == lbm.VARIANT_PAIR
+    assert variant(1024, 1024, lbm.BF16DEV) == lbm.VARIANT_PAIR
+    assert variant(1025, 1024) == lbm.VARIANT_REGISTER
+    assert variant(1024, 1024, lbm.FP64) == lbm.VARIANT_REGISTER
+    assert variant(256, 256) == lbm.VARIANT_REGISTER
+    assert variant(256, 256, want=lbm.VARIANT_PAIR) == lbm.VARIANT_PAIR
+    assert variant(1024, 1024, want=lbm.VARIANT_STAGED) == lbm.VARIANT_STAGED
+    assert variant(1026, 64, want=lbm.VARIANT_STAGED) == lbm.VARIANT_REGISTER  # nx % 4 != 0
