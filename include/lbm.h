@@ -346,6 +346,17 @@ lbm_status lbm_mlp_predict(lbm_mlp *m, const float *X, int n, float *Y);
 
 /* ---- allocation-free variant ------------------------------------------- */
 
+/* ---- self-test of the bounded device waits -------------------------------- */
+/* One warp on `device` waits, `polls` times (1 .. 2^20), on a shared-memory
+ * mbarrier that nothing arrives on, gives up, records the timeout in a
+ * device status word and returns -- the path the staged step kernel takes
+ * when its bulk copies do not land.  *result receives LBM_E_TIMEOUT when the
+ * wait gave up (expected) or LBM_OK.  Returns LBM_E_INVAL for bad arguments
+ * (checked before any CUDA call), LBM_E_CUDA / LBM_E_NOMEM on CUDA errors.
+ * Nothing faults or hangs; the context stays usable.  The paper has no
+ * counterpart. */
+lbm_status lbm_selftest_wait_timeout(int device, long long polls, int *result);
+
 /* FP64 sum of n FP32 values in device memory (for an FP32 population buffer
  * [9][ny][nx]: its total mass), written to the caller's device slot *d_out.
  * The paper has no counterpart: this is a deployment helper for callers that

@@ -100,6 +100,7 @@ SIGNATURES = {
     "lbm_set_kernel_variant": (_I, [_P, _I]),
     "lbm_get_launch_geometry": (_I, [_P, _I, _IP, _IP, _IP, _IP]),
     "lbm_get_kernel_variant": (_I, [_P, _IP]),
+    "lbm_selftest_wait_timeout": (_I, [_I, ctypes.c_longlong, _IP]),
     "lbm_mass_f32_noalloc": (_I, [_P, ctypes.c_size_t, _P, _P]),
     "lbm_batch_default_params": (None, [ctypes.POINTER(lbm_batch_params)]),
     "lbm_batch_create": (_I, [ctypes.POINTER(lbm_batch_params), ctypes.POINTER(lbm_instance),
@@ -183,6 +184,16 @@ def maxwell(T, a=1.0, b=4.0, R=1.0):
 
 def temperature(T_over_Tc, tc_mode=0, a=1.0, b=4.0, R=1.0):
     return T_over_Tc * (critical_point(a, b, R)[1] if tc_mode == 0 else 0.094)
+
+
+def selftest_wait_timeout(device=0, polls=1000):
+    """Status of a bounded device wait that nothing completes (LBM_E_TIMEOUT
+    expected); raises on bad arguments or CUDA errors."""
+    r = _I()
+    st = lib().lbm_selftest_wait_timeout(int(device), int(polls), ctypes.byref(r))
+    if st:
+        raise LbmError(st, "lbm_selftest_wait_timeout")
+    return r.value
 
 
 def launch_count():

@@ -77,6 +77,14 @@ def test_null_context_calls_are_rejected(L):
     assert L.lbm_destroy(None) == lbm.LBM_OK
 
 
+def test_wait_selftest_rejects_bad_arguments_without_cuda(L):
+    r = ctypes.c_int(-1)
+    assert L.lbm_selftest_wait_timeout(0, 0, ctypes.byref(r)) == lbm.LBM_E_INVAL
+    assert L.lbm_selftest_wait_timeout(0, (1 << 20) + 1, ctypes.byref(r)) == lbm.LBM_E_INVAL
+    assert L.lbm_selftest_wait_timeout(0, 10, None) == lbm.LBM_E_INVAL
+    assert r.value == -1
+
+
 def test_critical_point_matches_oracle(L):
     a = lbm.critical_point()
     b = th.critical_point()

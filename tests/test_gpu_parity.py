@@ -361,3 +361,16 @@ def test_auto_variant_choice():
     assert variant(256, 256, want=lbm.VARIANT_PAIR) == lbm.VARIANT_PAIR
     assert variant(1024, 1024, want=lbm.VARIANT_STAGED) == lbm.VARIANT_STAGED
     assert variant(1026, 64, want=lbm.VARIANT_STAGED) == lbm.VARIANT_REGISTER  # nx % 4 != 0
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """A device wait on an mbarrier nothing arrives on gives up after its poll
+    limit and reports LBM_E_TIMEOUT (no fault, no hang); the device is usable
+    afterwards."""
+    assert lbm.selftest_wait_timeout(0, polls=1000) == lbm.LBM_E_TIMEOUT
+    nx, ny, t = 40, 36, 0.85
+    rho, ux, uy = droplet_state(nx, ny, t)
+    g = lbm.Lattice(nx, ny, t, precision=lbm.FP32)
+    g.init_density(rho, ux, uy)
+    g.step(10, lbm.IMPROVED, 0.8, 0.1)
+    assert np.all(np.isfinite(g.observe()[0]))
