@@ -374,3 +374,22 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     g.init_density(rho, ux, uy)
     g.step(10, lbm.IMPROVED, 0.8, 0.1)
     assert np.all(np.isfinite(g.observe()[0]))
+
+
+@pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP64, lbm.BF16DEV])
+def test_uniform_density_is_a_fixed_point(precision):
+    """Degenerate case: a uniform density at rest has F = 0 (the psi stencil's
+    weights cancel in pairs) and f = f_eq, so every scheme leaves it exactly
+    unchanged (odd and even widths, both kernel variants)."""
+    for nx in (64, 33):
+        rho = np.full((24, nx), 0.2)
+        for scheme, sigma in ((lbm.SC, 0.0), (lbm.EDM, 0.0), (lbm.IMPROVED, 0.1),
+                              (lbm.EDM_MOD, 0.0), (lbm.LADD, 0.0)):
+            g = lbm.Lattice(nx, 24, 0.85, precision=precision)
+            g.init_density(rho)
+            f0 = g.populations()
+            g.step(50, scheme, 0.7, sigma)
+            assert np.array_equal(g.populations(), f0), (nx, scheme)
+            r, vx, vy = g.observe()
+            assert np.all(r == r[0, 0]) and not np.any(vx) and not np.any(vy)
+            g.close()
