@@ -377,19 +377,24 @@ def test_bounded_wait_reports_timeout_and_context_survives():
 
 
 @pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP64, lbm.BF16DEV])
-def test_uniform_density_is_a_fixed_point(precision):
-    """Degenerate case: a uniform density at rest has F = 0 (the psi stencil's
-    weights cancel in pairs) and f = f_eq, so every scheme leaves it exactly
-    unchanged (odd and even widths, both kernel variants)."""
+def test_uniform_density_stays_uniform_at_rest(precision):
+    """Degenerate case: at a uniform density every cell sees the same
+    neighbours, so psi's stencil gives F = 0 exactly and opposite populations
+    stay equal: for every scheme (odd and even widths, both kernel variants)
+    the state stays uniform cell for cell, the velocity exactly zero, and the
+    density at its value to rounding (the collision's (1 - omega) f + omega
+    f_eq need not round back to f)."""
+    tol = {lbm.FP32: 1e-6, lbm.FP64: 1e-14, lbm.BF16DEV: 1e-6}[precision]
     for nx in (64, 33):
         rho = np.full((24, nx), 0.2)
         for scheme, sigma in ((lbm.SC, 0.0), (lbm.EDM, 0.0), (lbm.IMPROVED, 0.1),
                               (lbm.EDM_MOD, 0.0), (lbm.LADD, 0.0)):
             g = lbm.Lattice(nx, 24, 0.85, precision=precision)
             g.init_density(rho)
-            f0 = g.populations()
             g.step(50, scheme, 0.7, sigma)
-            assert np.array_equal(g.populations(), f0), (nx, scheme)
+            f = g.populations()
+            assert np.all(f == f[:, :1, :1]), (nx, scheme)
             r, vx, vy = g.observe()
-            assert np.all(r == r[0, 0]) and not np.any(vx) and not np.any(vy)
+            assert not np.any(vx) and not np.any(vy), (nx, scheme)
+            assert np.max(np.abs(r / 0.2 - 1)) < tol, (nx, scheme)
             g.close()
