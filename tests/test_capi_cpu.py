@@ -113,7 +113,9 @@ def test_batch_create_rejects_bad_arguments_without_cuda(L):
         with pytest.raises(lbm.LbmError) as e:
             lbm.Batch([good, {**good, **bad}])
         assert e.value.status == lbm.LBM_E_INVAL
-    for kw in (dict(window=3), dict(window=0), dict(max_steps=0), dict(mode=7), dict(conv=5)):
+    for kw in (dict(window=3), dict(window=0), dict(max_steps=0), dict(mode=7), dict(conv=5),
+               dict(conv_rel=-1e-6), dict(conv_rel=float("nan")), dict(variant=lbm.VARIANT_STAGED),
+               dict(variant=9), dict(rows_per_item=-1)):
         with pytest.raises(lbm.LbmError) as e:
             lbm.Batch([good], **kw)
         assert e.value.status == lbm.LBM_E_INVAL
