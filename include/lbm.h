@@ -193,10 +193,14 @@ lbm_status lbm_get_kernel_variant(lbm_ctx *ctx, int *variant);
  * converges, diverges or reaches a step cap.  Each instance is the method of
  * lbm_step (the same fused kernel body); the batch packs all populations in
  * one buffer pair and runs windows of `window` steps as one CUDA graph:
- * either one launch per step over a work list of all active instances'
- * 32-column x band items, or one persistent launch per window in which each
- * CTA owns whole instances and synchronises only its own threads between
- * steps.  After every window an FP64 reduction per instance gives the
+ * WORKLIST: one launch per step and instance class (two columns per lane
+ * for even nx, one for odd nx) over a work list of the active instances'
+ * strip x band items; PERSISTENT: one launch per window in which each CTA
+ * owns whole instances and synchronises only its own threads between steps;
+ * COOPERATIVE: one cooperative launch per window (every CTA resident) whose
+ * warps take the work-list items of each step and meet at a bounded grid
+ * barrier between steps (LBM_E_TIMEOUT if it ever gives up).  AUTO times the
+ * candidates on live windows and keeps the fastest.  After every window an FP64 reduction per instance gives the
  * coexistence densities of the flat interface (Eq. 36 slab: rho_g from rows
  * 0 and ny-1, rho_l from rows ny/2-1 and ny/2), the interface width
  * (rho_l - rho_g) / max_y |d rho_row / dy|, the mass, and the largest density
@@ -212,7 +216,8 @@ typedef struct {
   int scheme;        /* LBM_SCHEME_*                                         */
 } lbm_instance;
 
-enum { LBM_BATCH_AUTO = 0, LBM_BATCH_WORKLIST = 1, LBM_BATCH_PERSISTENT = 2 };
+enum { LBM_BATCH_AUTO = 0, LBM_BATCH_WORKLIST = 1, LBM_BATCH_PERSISTENT = 2,
+       LBM_BATCH_COOPERATIVE = 3 };
 /* Convergence rules.  CELL: every cell changed by less than
  * max(tol, 8 * 2^-23 * rho) over a window.  COEX: the coexistence densities
  * rho_g and rho_l (FP64 row means) each changed by less than
@@ -232,7 +237,7 @@ typedef struct {
   double tol;           /* density-change tolerance per window (1e-9)          */
   int max_steps;        /* step cap per instance (200000)                      */
   int mode;             /* LBM_BATCH_AUTO (window-level autotuning), _WORKLIST,
-                           _PERSISTENT                                         */
+                           _PERSISTENT, _COOPERATIVE                           */
   int rows_per_item;    /* band height of a work-list item; 0 = autotuned      */
   int conv;             /* LBM_CONV_COEX (default), _CELL or _NONE              */
   int variant;          /* LBM_VARIANT_AUTO (default) or _PAIR: two columns per

@@ -141,6 +141,78 @@ batch_worklist_kernel(const BatchInst* __restrict__ inst, const int* __restrict_
   }
 }
 
+// Grid barrier of the cooperative window: sync[0] counts arrivals, sync[1] is
+// the generation, sync[2] the error word.  Every CTA is resident (cooperative
+// launch), so the barrier completes; the wait is still bounded, and a CTA
+// that gives up sets kStatusTimeout in sync[2] and the caller returns.
+constexpr long long kBarrierSpinLimit = 1ll << 22;  // ~0.3-1 s of 64-ns sleeps
+
+__device__ __forceinline__ bool grid_barrier(unsigned* sync) {
+  __shared__ int ok_s;
+  __syncthreads();  // every warp of this CTA finished the step
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = sync + 1;
+    const unsigned g = *gen;  // read before arriving: the last arrival bumps it
+    __threadfence();          // this CTA's stores of the step are visible device-wide
+    bool ok = true;
+    if (atomicAdd(sync, 1u) + 1u == gridDim.x) {
+      atomicExch(sync, 0u);   // reset before releasing anyone
+      __threadfence();
+      atomicAdd(sync + 1, 1u);
+    } else {
+      long long it = 0;
+      while (*gen == g && ++it < kBarrierSpinLimit) __nanosleep(64);
+      ok = it < kBarrierSpinLimit;
+      if (!ok) atomicOr(sync + 2, kStatusTimeout);
+    }
+    __threadfence();
+    ok_s = ok && *(volatile unsigned*)(sync + 2) == 0u;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// `steps` steps of every active instance in one cooperative launch: in each
+// step warps take items of both classes from the prefix table (the item body
+// is chosen per instance), then all CTAs meet at the grid barrier.  Loads
+// bypass L1 because other CTAs of this launch wrote them.
+__global__ void __launch_bounds__(kWorklistThreads, LBM_BATCH_PAIR_MIN_BLOCKS)
+batch_coop_kernel(const BatchInst* __restrict__ inst, const int* __restrict__ active,
+                  const int* __restrict__ prefix, const int* __restrict__ counts, int steps,
+                  float* buf0, float* buf1, unsigned* inst_status, unsigned* sync) {
+  __shared__ StripArgs<StoreF32> args[kWorklistThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = gridDim.x * (kWorklistThreads / 32);
+  const int na = counts[1];
+  const int total = prefix[na];
+  for (int s = 0; s < steps; ++s) {
+    const float* src = (s & 1) ? buf1 : buf0;
+    float* dst = (s & 1) ? buf0 : buf1;
+    for (int item = (blockIdx.x * kWorklistThreads + threadIdx.x) >> 5; item < total;
+         item += nwarps) {
+      int lo = 0, hi = na;  // prefix[lo] <= item < prefix[lo + 1]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= item) lo = mid; else hi = mid;
+      }
+      const int i = active[lo];
+      const BatchInst I = inst[i];
+      const int local = item - prefix[lo];
+      __syncwarp();
+      // work-list geometry (the prefix table counts its items); coherent loads
+      if (lane == 0) args[warp] = inst_args(I, src, dst, inst_status + i, false);
+      __syncwarp();
+      if (I.pair)  // warp-uniform
+        run_item<true, true>(args[warp], I.scheme, local % I.n_strips, local / I.n_strips,
+                             lane);
+      else
+        run_item<false, true>(args[warp], I.scheme, local % I.n_strips, local / I.n_strips,
+                              lane);
+    }
+    if (!grid_barrier(sync)) return;
+  }
+}
+
 // `steps` steps of the instances of one class this CTA owns (cta_begin and
 // cta_list of that class); buffers alternate, starting from buf0.  The loads
 // bypass L1 because this kernel wrote them.
@@ -384,6 +456,8 @@ struct lbm_batch {
   int sm_count = 0;
   int wl_grid = 0;
   int pers_grid_max = 0;
+  int coop_grid = 0;             // resident CTAs of the cooperative kernel (0: unsupported)
+  unsigned* d_sync = nullptr;    // grid barrier: arrivals, generation, error
   cudaStream_t side = nullptr;   // second branch of the window graph
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // window graphs by (mode, grid of the two-column kernel, grid of the
@@ -523,7 +597,9 @@ int class_grid(const lbm_batch* b, int mode, int cls) {
 }
 
 lbm_status window_graph(lbm_batch* b, int mode, cudaGraphExec_t* out) {
-  const int g0 = class_grid(b, mode, 0), g1 = class_grid(b, mode, 1);
+  const bool coop = mode == LBM_BATCH_COOPERATIVE;
+  const int g0 = coop ? b->coop_grid : class_grid(b, mode, 0);
+  const int g1 = coop ? 0 : class_grid(b, mode, 1);
   const auto key = std::make_tuple(mode, g0, g1);
   const auto it = b->graphs.find(key);
   if (it != b->graphs.end()) {
@@ -548,7 +624,32 @@ lbm_status window_graph(lbm_batch* b, int mode, cudaGraphExec_t* out) {
     cudaEventRecord(b->ev_join, b->side);
     cudaStreamWaitEvent(b->stream, b->ev_join, 0);
   };
-  if (mode == LBM_BATCH_WORKLIST) {
+  if (coop) {
+    // one cooperative launch for the whole window (barrier state reset first)
+    cudaMemsetAsync(b->d_sync, 0, 3 * sizeof(unsigned), b->stream);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(b->coop_grid));
+    cfg.blockDim = dim3(kWorklistThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = b->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t le = cudaLaunchKernelEx(
+        &cfg, batch_coop_kernel, static_cast<const BatchInst*>(b->d_inst),
+        static_cast<const int*>(b->d_active), static_cast<const int*>(b->d_prefix),
+        static_cast<const int*>(b->d_n_active), W, b->buf[0], b->buf[1], b->d_status,
+        b->d_sync);
+    if (le != cudaSuccess) {
+      cudaGraph_t dead = nullptr;
+      cudaStreamEndCapture(b->stream, &dead);
+      if (dead) cudaGraphDestroy(dead);
+      cudaGetLastError();
+      return bfail(b, LBM_E_CUDA, std::string("cooperative launch: ") + cudaGetErrorString(le));
+    }
+  } else if (mode == LBM_BATCH_WORKLIST) {
     for (int s = 0; s < W; ++s) {
       fork();
       if (g0 > 0)
@@ -576,12 +677,17 @@ lbm_status window_graph(lbm_batch* b, int mode, cudaGraphExec_t* out) {
       b->d_inst, b->d_active, b->d_n_active + 1, b->buf[0], b->snap, b->rowmean, b->d_out,
       float(b->p.tol));
   cudaError_t e = cudaStreamEndCapture(b->stream, &g);
-  if (e != cudaSuccess) return bfail(b, LBM_E_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return bfail(b, LBM_E_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+  }
   cudaGraphExec_t exec = nullptr;
   e = cudaGraphInstantiate(&exec, g, 0);
   cudaGraphDestroy(g);
-  if (e != cudaSuccess)
+  if (e != cudaSuccess) {
+    cudaGetLastError();
     return bfail(b, LBM_E_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+  }
   b->graphs[key] = exec;
   *out = exec;
   return LBM_OK;
@@ -629,6 +735,7 @@ void choose_config(lbm_batch* b, int& mode, int& rows) {
       if (c.first == LBM_BATCH_PERSISTENT &&
           (cells * 72 > size_t(512) << 20 || max_active_cells(b) > 65536))
         continue;
+      if (c.first == LBM_BATCH_COOPERATIVE && b->coop_grid == 0) continue;
       mode = c.first;
       rows = c.second;
       return;
@@ -682,7 +789,7 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
   if (!p || !in || !out || count < 1) return LBM_E_INVAL;
   *out = nullptr;
   if (p->window < 2 || p->window % 2 || p->max_steps < 1 || !(p->tol >= 0) ||
-      p->mode < LBM_BATCH_AUTO || p->mode > LBM_BATCH_PERSISTENT || p->rows_per_item < 0 ||
+      p->mode < LBM_BATCH_AUTO || p->mode > LBM_BATCH_COOPERATIVE || p->rows_per_item < 0 ||
       p->conv < LBM_CONV_COEX || p->conv > LBM_CONV_NONE || !(p->conv_rel >= 0.0) ||
       !(p->variant == LBM_VARIANT_AUTO || p->variant == LBM_VARIANT_PAIR ||
         p->variant == LBM_VARIANT_REGISTER) ||
@@ -787,6 +894,7 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
   ok &= cudaMalloc(&b->d_n_active, 2 * sizeof(int)) == cudaSuccess;
   ok &= cudaMalloc(&b->d_cta_begin, 2 * (b->pers_grid_max + 1) * sizeof(int)) == cudaSuccess;
   ok &= cudaMalloc(&b->d_cta_list, count * sizeof(int)) == cudaSuccess;
+  ok &= cudaMalloc(&b->d_sync, 3 * sizeof(unsigned)) == cudaSuccess;
   if (!ok) return bail(LBM_E_NOMEM, "cudaMalloc");
   ok &= cudaMallocHost(&b->h_active, count * sizeof(int)) == cudaSuccess;
   ok &= cudaMallocHost(&b->h_prefix, (count + 3) * sizeof(int)) == cudaSuccess;
@@ -808,6 +916,19 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
     return bail(LBM_E_CUDA, "memset");
   for (int rows : {8, 16, 32, 64, 128}) b->candidates.push_back({LBM_BATCH_WORKLIST, rows});
   b->candidates.push_back({LBM_BATCH_PERSISTENT, 0});
+  {
+    // cooperative windows: every CTA resident, one launch per window
+    int coop = 0, occ = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, p->device) == cudaSuccess &&
+        coop &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_coop_kernel,
+                                                      kWorklistThreads, 0) == cudaSuccess &&
+        occ > 0)
+      b->coop_grid = occ * b->sm_count;
+    cudaGetLastError();
+    if (b->coop_grid > 0)
+      for (int rows : {16, 32, 64}) b->candidates.push_back({LBM_BATCH_COOPERATIVE, rows});
+  }
   b->cand_cost.assign(b->candidates.size(), -1.0);
   for (int i = 0; i < count; ++i) b->active.push_back(i);
   b->stats.n_active = count;
@@ -835,6 +956,7 @@ lbm_status lbm_batch_destroy(lbm_batch* b) {
   cudaFree(b->d_n_active);
   cudaFree(b->d_cta_begin);
   cudaFree(b->d_cta_list);
+  cudaFree(b->d_sync);
   if (b->h_active) cudaFreeHost(b->h_active);
   if (b->h_prefix) cudaFreeHost(b->h_prefix);
   if (b->h_cta_begin) cudaFreeHost(b->h_cta_begin);
@@ -951,6 +1073,14 @@ lbm_status lbm_batch_run(lbm_batch* b, int max_windows, int* n_active) {
     if (st != LBM_OK) return st;
     cudaGraphExec_t g = nullptr;
     st = window_graph(b, mode, &g);
+    if (st != LBM_OK && mode == LBM_BATCH_COOPERATIVE && b->p.mode == LBM_BATCH_AUTO) {
+      // cooperative windows unavailable here: drop them and use the work list
+      b->coop_grid = 0;
+      for (size_t k = 0; k < b->candidates.size(); ++k)
+        if (b->candidates[k].first == LBM_BATCH_COOPERATIVE) b->cand_cost[k] = 1e300;
+      mode = LBM_BATCH_WORKLIST;
+      st = window_graph(b, mode, &g);
+    }
     if (st != LBM_OK) return st;
     const size_t cells = active_cells(b);
     LBM_BCUDA(b, cudaEventRecord(b->ev0, b->stream));
@@ -958,8 +1088,11 @@ lbm_status lbm_batch_run(lbm_batch* b, int max_windows, int* n_active) {
     LBM_BCUDA(b, cudaEventRecord(b->ev1, b->stream));
     // two class kernels per step (work list) or per window (persistent), and
     // the reduction
+    // (one cooperative kernel per window)
     const unsigned long long kernels =
-        (class_grid(b, mode, 0) > 0 ? 1 : 0) + (class_grid(b, mode, 1) > 0 ? 1 : 0);
+        mode == LBM_BATCH_COOPERATIVE
+            ? 1
+            : (class_grid(b, mode, 0) > 0 ? 1 : 0) + (class_grid(b, mode, 1) > 0 ? 1 : 0);
     const unsigned long long nl =
         (mode == LBM_BATCH_WORKLIST ? kernels * b->p.window : kernels) + 1;
     count_launches(nl);
@@ -969,6 +1102,11 @@ lbm_status lbm_batch_run(lbm_batch* b, int max_windows, int* n_active) {
     LBM_BCUDA(b, cudaMemcpyAsync(b->h_status, b->d_status, b->count * sizeof(unsigned),
                                  cudaMemcpyDeviceToHost, b->stream));
     LBM_BCUDA(b, cudaStreamSynchronize(b->stream));
+    if (mode == LBM_BATCH_COOPERATIVE) {
+      unsigned sync_err = 0;
+      LBM_BCUDA(b, cudaMemcpy(&sync_err, b->d_sync + 2, sizeof(unsigned), cudaMemcpyDeviceToHost));
+      if (sync_err) return bfail(b, LBM_E_TIMEOUT, "grid barrier of a cooperative window gave up");
+    }
     float ms = 0.f;
     LBM_BCUDA(b, cudaEventElapsedTime(&ms, b->ev0, b->ev1));
     b->stats.gpu_ms += ms;

@@ -251,7 +251,6 @@ int pick_variant(const lbm_ctx* c, int mode) {
     return LBM_VARIANT_PAIR;
   return LBM_VARIANT_REGISTER;
 }
-bool use_staged(const lbm_ctx* c, int mode) { return pick_variant(c, mode) == LBM_VARIANT_STAGED; }
 
 // Warp-strip geometry: strips of 32 columns (64 for PAIR), and as many row bands as fill
 // the resident warp slots once (one wave: every warp of a band runs at the
