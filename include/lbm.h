@@ -204,8 +204,8 @@ lbm_status lbm_get_kernel_variant(lbm_ctx *ctx, int *variant);
  * coexistence densities of the flat interface (Eq. 36 slab: rho_g from rows
  * 0 and ny-1, rho_l from rows ny/2-1 and ny/2), the interface width
  * (rho_l - rho_g) / max_y |d rho_row / dy|, the mass, and the largest density
- * change since the previous window.  An instance has converged when every
- * cell changed by less than max(tol, 8 * 2^-23 * rho) over a window.
+ * change since the previous window.  When an instance has converged is set
+ * by the convergence rule (conv, below: COEX by default).
  */
 
 typedef struct {
