@@ -316,8 +316,8 @@ def test_staged_kernel_fp32_parity_with_oracle():
 
 
 @pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP64, lbm.BF16DEV, lbm.FP16DEV])
-@pytest.mark.parametrize("nx,ny", [(2, 9), (4, 4), (40, 21), (64, 33), (66, 40), (100, 17),
-                                   (130, 65)])
+@pytest.mark.parametrize("nx,ny", [(2, 9), (4, 4), (2, 1), (64, 1), (66, 2), (40, 21), (64, 33),
+                                   (66, 40), (100, 17), (130, 65)])
 def test_pair_kernel_matches_register_kernel_bitwise(precision, nx, ny):
     """Two columns per lane (vector loads, shuffled +-1 pulls, boundary and
     halo elements from extra lanes, wrapped lanes in ragged strips) computes
