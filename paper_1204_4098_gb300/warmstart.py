@@ -12,7 +12,7 @@ window (default), when it has converged, or not at all (run_warm's
 the interface relaxing from the initial tanh profile still moves the bulk
 densities by ~0.5-1 % even when the prediction is right to 1e-3, so the
 first-window check also restarts some good predictions; it is the cheapest
-point to restart.)  Cold runs remain the judge of the error: the tests and
+point to restart.)  Cold runs remain the reference for the error: the tests and
 the sweep report compare warm and cold coexistence densities.
 
 Inputs are scaled to [-1, 1] over the sweep ranges.  The network learns
