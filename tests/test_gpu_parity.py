@@ -56,6 +56,25 @@ def test_populations_fp32(scheme, sigma, steps):
 
 
 @pytest.mark.parametrize("scheme,sigma", SCHEMES)
+@pytest.mark.parametrize("precision,tol", [(lbm.FP32, 2e-6), (lbm.FP64, 1e-13)])
+def test_pair_kernel_populations_against_oracle(scheme, sigma, precision, tol):
+    """The two-columns-per-lane kernel (the bench's kernel) against the oracle
+    directly: 200 x 67 is three full 64-column strips and a ragged one."""
+    nx, ny, t, steps = 200, 67, 0.9, 20
+    rho, ux, uy = droplet_state(nx, ny, t)
+    gpu = lbm.Lattice(nx, ny, t, precision=precision)
+    gpu.set_variant(lbm.VARIANT_PAIR)
+    assert gpu.variant() == lbm.VARIANT_PAIR
+    gpu.init_density(rho, ux, uy)
+    gpu.step(steps, scheme, 0.8, sigma)
+    ref = oracle.Lattice(nx, ny, t)
+    ref.init_density(rho, ux, uy)
+    assert ref.step(steps, scheme, 0.8, sigma)[0] == 0
+    err = np.max(np.abs(gpu.populations() - ref.f)) / np.max(np.abs(ref.f))
+    assert err < tol * steps ** 0.5, err
+
+
+@pytest.mark.parametrize("scheme,sigma", SCHEMES)
 def test_populations_fp64(scheme, sigma):
     nx, ny, t = 45, 37, 0.9
     rho, ux, uy = droplet_state(nx, ny, t)
