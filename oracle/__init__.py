@@ -29,7 +29,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _LIB = os.path.join(_HERE, "liblbm_oracle.so")
 
-SC, EDM, IMPROVED, NOFORCE, EDM_MOD, LADD = range(6)
+SC, EDM, IMPROVED, NOFORCE, EDM_MOD, LADD, MRT = range(7)
 Q = 9
 EX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
 EY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
@@ -56,6 +56,7 @@ def _declare(lib):
         "oracle_psi_field": (i, [i, i, p, d, d, d, d, p]),
         "oracle_force": (None, [i, i, d, p, p, p]),
         "oracle_collide_cell": (i, [i, d, d, p, d, d, d, p]),
+        "oracle_set_mrt_rates": (None, [d, d, d]),
         "oracle_stream": (None, [i, i, p, p]),
         "oracle_step": (i, [i, i, p, i, d, d, d, d, d, d]),
         "oracle_run": (i, [i, i, p, i, i, d, d, d, d, d, d, p]),
@@ -113,6 +114,13 @@ def feq(rho, ux, uy, lib=None):
     out = np.zeros(Q)
     lib.oracle_feq(float(rho), float(ux), float(uy), _ptr(out))
     return out
+
+
+def set_mrt_rates(s_e=0.0, s_eps=0.0, s_q=0.0, lib=None):
+    """Relaxation rates of the MRT scheme's energy, energy-square and
+    energy-flux moments (<= 0: 1/tau); process-wide."""
+    lib = lib or load()
+    lib.oracle_set_mrt_rates(float(s_e), float(s_eps), float(s_q))
 
 
 def collide_cell(scheme, tau, sigma, f, Fx, Fy, psi_c=1.0, lib=None):

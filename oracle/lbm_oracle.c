@@ -43,7 +43,9 @@ enum {
   OR_IMPROVED = 2,  /* improved scheme, Eq. 31 (sigma = 0: Guo)       */
   OR_NOFORCE = 3,   /* plain BGK, F = 0                               */
   OR_EDM_MOD = 4,   /* EDM with C_e = 1/tau (Sec. III C)              */
-  OR_LADD = 5       /* Ladd, Table I                                  */
+  OR_LADD = 5,      /* Ladd, Table I                                  */
+  OR_MRT = 6        /* improved forcing in multiple-relaxation-time form
+                       (the extension stated at the end of Sec. IV)     */
 };
 
 static double cs2(void) { return 1.0 / 3.0; }
@@ -154,6 +156,93 @@ static double guo_term(int a, double Be, double Ce, double vx, double vy,
   return wq[a] * (Be * Fe / cs2() + Cee / (2.0 * cs2() * cs2()));
 }
 
+/* ---- multiple-relaxation-time form of the improved scheme --------------- */
+/* The paper states (end of Sec. IV) that the improved scheme extends to the
+ * MRT model without giving the form; this is the reading used here.  The
+ * D2Q9 moments are m = M f with the rows (c = e_a, |c|^2 = e.e)
+ *   1, -4 + 3|c|^2, 4 - 21|c|^2/2 + 9|c|^4/2, c_x, (-5 + 3|c|^2) c_x,
+ *   c_y, (-5 + 3|c|^2) c_y, c_x^2 - c_y^2, c_x c_y
+ * (density, energy, energy square, momentum, energy flux, stresses).  The
+ * collision relaxes each moment with its own rate towards the moments of
+ * f_eq(rho, v) and adds the moments of the improved forcing term with the
+ * half-rate factor, m* = m - S (m - M f_eq) + (I - S/2) M Fhat, where
+ * Fhat_a = w_a [3 (e_a - v').F + 9 (e_a.v') (e_a.F)] is the bracket of
+ * Eq. 31 (so that S = I / tau gives Eq. 31 itself), and f* = M^-1 m*.
+ * Rates: stresses 1/tau, energy s_e, energy square s_eps, energy flux s_q
+ * (density and momentum: any, their f_eq and forcing moments fix them).
+ * A rate <= 0 means 1/tau. */
+static double mrt_rates[3] = {0.0, 0.0, 0.0};
+
+void oracle_set_mrt_rates(double s_e, double s_eps, double s_q) {
+  mrt_rates[0] = s_e;
+  mrt_rates[1] = s_eps;
+  mrt_rates[2] = s_q;
+}
+
+static void mrt_matrix(double M[Q][Q]) {
+  for (int a = 0; a < Q; ++a) {
+    double cx = ex[a], cy = ey[a], c2 = cx * cx + cy * cy;
+    M[0][a] = 1.0;
+    M[1][a] = -4.0 + 3.0 * c2;
+    M[2][a] = 4.0 - 10.5 * c2 + 4.5 * c2 * c2;
+    M[3][a] = cx;
+    M[4][a] = (-5.0 + 3.0 * c2) * cx;
+    M[5][a] = cy;
+    M[6][a] = (-5.0 + 3.0 * c2) * cy;
+    M[7][a] = cx * cx - cy * cy;
+    M[8][a] = cx * cy;
+  }
+}
+
+static int collide_mrt(double tau, double sigma, const double *f, double Fx, double Fy,
+                       double psi, double *fout) {
+  double M[Q][Q];
+  mrt_matrix(M);
+  double rho = 0.0, jx = 0.0, jy = 0.0;
+  for (int a = 0; a < Q; ++a) {
+    rho += f[a];
+    jx += f[a] * ex[a];
+    jy += f[a] * ey[a];
+  }
+  double ux = jx / rho, uy = jy / rho;
+  double vx = ux + Fx / (2.0 * rho), vy = uy + Fy / (2.0 * rho);
+  double ups = tau - 0.5;
+  double vpx = vx + sigma * Fx / (ups * psi * psi);
+  double vpy = vy + sigma * Fy / (ups * psi * psi);
+  double feq[Q], fhat[Q];
+  oracle_feq(rho, vx, vy, feq);
+  for (int a = 0; a < Q; ++a) {
+    double Fe = Fx * ex[a] + Fy * ey[a];
+    double evp = ex[a] * vpx + ey[a] * vpy;
+    fhat[a] = wq[a] * (((ex[a] - vpx) * Fx + (ey[a] - vpy) * Fy) / cs2() +
+                       evp * Fe / (cs2() * cs2()));
+  }
+  double sv = 1.0 / tau;
+  double se = mrt_rates[0] > 0.0 ? mrt_rates[0] : sv;
+  double seps = mrt_rates[1] > 0.0 ? mrt_rates[1] : sv;
+  double sq = mrt_rates[2] > 0.0 ? mrt_rates[2] : sv;
+  double S[Q] = {sv, se, seps, sv, sq, sv, sq, sv, sv};
+  double mstar[Q], norm[Q];
+  for (int k = 0; k < Q; ++k) {
+    double m = 0.0, meq = 0.0, mf = 0.0;
+    norm[k] = 0.0;
+    for (int a = 0; a < Q; ++a) {
+      m += M[k][a] * f[a];
+      meq += M[k][a] * feq[a];
+      mf += M[k][a] * fhat[a];
+      norm[k] += M[k][a] * M[k][a];
+    }
+    mstar[k] = m - S[k] * (m - meq) + (1.0 - 0.5 * S[k]) * mf;
+  }
+  /* the rows of M are orthogonal: M^-1 = M^T diag(1 / |row|^2) */
+  for (int a = 0; a < Q; ++a) {
+    double v = 0.0;
+    for (int k = 0; k < Q; ++k) v += M[k][a] * mstar[k] / norm[k];
+    fout[a] = v;
+  }
+  return 0;
+}
+
 /* Post-collision populations fout from the pre-collision populations f at one
  * cell, given the interaction force F there and psi there (improved scheme
  * only).  Returns 0, or 1 for an unknown scheme. */
@@ -218,6 +307,8 @@ int oracle_collide_cell(int scheme, double tau, double sigma, const double *f,
                   guo_term(a, 1.0, 1.0, ux, uy, Fx, Fy);
       return 0;
     }
+    case OR_MRT:
+      return collide_mrt(tau, sigma, f, Fx, Fy, psi, fout);
   }
   return 1;
 }
