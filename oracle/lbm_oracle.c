@@ -156,6 +156,27 @@ static double guo_term(int a, double Be, double Ce, double vx, double vy,
   return wq[a] * (Be * Fe / cs2() + Cee / (2.0 * cs2() * cs2()));
 }
 
+/* Velocities of the improved scheme (Eq. 31, Table I): the actual velocity
+ * v = u + F/(2 rho) and v' = v + sigma F / (upsilon psi^2), upsilon = tau - 1/2. */
+static void improved_velocities(double rho, double ux, double uy, double Fx, double Fy,
+                                double tau, double sigma, double psi, double *vx,
+                                double *vy, double *vpx, double *vpy) {
+  *vx = ux + Fx / (2.0 * rho);
+  *vy = uy + Fy / (2.0 * rho);
+  double ups = tau - 0.5;
+  *vpx = *vx + sigma * Fx / (ups * psi * psi);
+  *vpy = *vy + sigma * Fy / (ups * psi * psi);
+}
+
+/* The bracket of the second line of Eq. 31 for direction a:
+ * w_a [(e_a - v')/c_s^2 + (e_a.v') e_a / c_s^4] . F */
+static double improved_bracket(int a, double vpx, double vpy, double Fx, double Fy) {
+  double Fe = Fx * ex[a] + Fy * ey[a];
+  double evp = ex[a] * vpx + ey[a] * vpy;
+  return wq[a] * (((ex[a] - vpx) * Fx + (ey[a] - vpy) * Fy) / cs2() +
+                  evp * Fe / (cs2() * cs2()));
+}
+
 /* ---- multiple-relaxation-time form of the improved scheme --------------- */
 /* The paper states (end of Sec. IV) that the improved scheme extends to the
  * MRT model without giving the form; this is the reading used here.  The
@@ -196,27 +217,19 @@ static void mrt_matrix(double M[Q][Q]) {
 
 static int collide_mrt(double tau, double sigma, const double *f, double Fx, double Fy,
                        double psi, double *fout) {
-  double M[Q][Q];
+  double M[Q][Q], m[Q];
   mrt_matrix(M);
-  double rho = 0.0, jx = 0.0, jy = 0.0;
-  for (int a = 0; a < Q; ++a) {
-    rho += f[a];
-    jx += f[a] * ex[a];
-    jy += f[a] * ey[a];
+  for (int k = 0; k < Q; ++k) {
+    m[k] = 0.0;
+    for (int a = 0; a < Q; ++a) m[k] += M[k][a] * f[a];
   }
-  double ux = jx / rho, uy = jy / rho;
-  double vx = ux + Fx / (2.0 * rho), vy = uy + Fy / (2.0 * rho);
-  double ups = tau - 0.5;
-  double vpx = vx + sigma * Fx / (ups * psi * psi);
-  double vpy = vy + sigma * Fy / (ups * psi * psi);
+  double rho = m[0];                          /* density moment */
+  double ux = m[3] / rho, uy = m[5] / rho;    /* momentum moments / rho */
+  double vx, vy, vpx, vpy;
+  improved_velocities(rho, ux, uy, Fx, Fy, tau, sigma, psi, &vx, &vy, &vpx, &vpy);
   double feq[Q], fhat[Q];
   oracle_feq(rho, vx, vy, feq);
-  for (int a = 0; a < Q; ++a) {
-    double Fe = Fx * ex[a] + Fy * ey[a];
-    double evp = ex[a] * vpx + ey[a] * vpy;
-    fhat[a] = wq[a] * (((ex[a] - vpx) * Fx + (ey[a] - vpy) * Fy) / cs2() +
-                       evp * Fe / (cs2() * cs2()));
-  }
+  for (int a = 0; a < Q; ++a) fhat[a] = improved_bracket(a, vpx, vpy, Fx, Fy);
   double sv = 1.0 / tau;
   double se = mrt_rates[0] > 0.0 ? mrt_rates[0] : sv;
   double seps = mrt_rates[1] > 0.0 ? mrt_rates[1] : sv;
@@ -224,15 +237,14 @@ static int collide_mrt(double tau, double sigma, const double *f, double Fx, dou
   double S[Q] = {sv, se, seps, sv, sq, sv, sq, sv, sv};
   double mstar[Q], norm[Q];
   for (int k = 0; k < Q; ++k) {
-    double m = 0.0, meq = 0.0, mf = 0.0;
+    double meq = 0.0, mf = 0.0;
     norm[k] = 0.0;
     for (int a = 0; a < Q; ++a) {
-      m += M[k][a] * f[a];
       meq += M[k][a] * feq[a];
       mf += M[k][a] * fhat[a];
       norm[k] += M[k][a] * M[k][a];
     }
-    mstar[k] = m - S[k] * (m - meq) + (1.0 - 0.5 * S[k]) * mf;
+    mstar[k] = m[k] - S[k] * (m[k] - meq) + (1.0 - 0.5 * S[k]) * mf;
   }
   /* the rows of M are orthogonal: M^-1 = M^T diag(1 / |row|^2) */
   for (int a = 0; a < Q; ++a) {
@@ -271,18 +283,12 @@ int oracle_collide_cell(int scheme, double tau, double sigma, const double *f,
       return 0;
     }
     case OR_IMPROVED: { /* Eq. 31: Guo with v' = v + sigma F / (upsilon psi^2) */
-      double vx = ux + Fx / (2.0 * rho), vy = uy + Fy / (2.0 * rho);
-      double ups = tau - 0.5;
-      double vpx = vx + sigma * Fx / (ups * psi * psi);
-      double vpy = vy + sigma * Fy / (ups * psi * psi);
+      double vx, vy, vpx, vpy;
+      improved_velocities(rho, ux, uy, Fx, Fy, tau, sigma, psi, &vx, &vy, &vpx, &vpy);
       oracle_feq(rho, vx, vy, feq); /* Guo: f_eq at the actual velocity v */
       for (int a = 0; a < Q; ++a) {
-        double Fe = Fx * ex[a] + Fy * ey[a];
-        double evp = ex[a] * vpx + ey[a] * vpy;
         /* second line of Eq. 31: w (1 - 1/2tau) [(e - v')/c_s^2 + (e.v') e / c_s^4] . F */
-        double Fa = wq[a] * (1.0 - 1.0 / (2.0 * tau)) *
-                    (((ex[a] - vpx) * Fx + (ey[a] - vpy) * Fy) / cs2() +
-                     evp * Fe / (cs2() * cs2()));
+        double Fa = (1.0 - 1.0 / (2.0 * tau)) * improved_bracket(a, vpx, vpy, Fx, Fy);
         fout[a] = f[a] - (f[a] - feq[a]) / tau + Fa;
       }
       return 0;

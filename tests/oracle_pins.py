@@ -427,10 +427,78 @@ def pin_static_interface_actual_velocity(lib):
     return fails
 
 
+# ---------------------------------------------------------------------------
+# multiple-relaxation-time form of the improved scheme (end of Sec. IV)
+# ---------------------------------------------------------------------------
+
+def _mrt_basis():
+    """D2Q9 moment basis (Lallemand-Luo): density, energy, energy square,
+    momentum x, energy flux x, momentum y, energy flux y, two stresses."""
+    ex, ey = EX.astype(float), EY.astype(float)
+    c2 = ex ** 2 + ey ** 2
+    return np.array([np.ones(Q), -4 + 3 * c2, 4 - 10.5 * c2 + 4.5 * c2 ** 2, ex,
+                     (-5 + 3 * c2) * ex, ey, (-5 + 3 * c2) * ey, ex ** 2 - ey ** 2, ex * ey])
+
+
+def pin_mrt_reduces_to_improved(lib):
+    """With every rate 1/tau the MRT form must be Eq. 31 itself."""
+    fails = []
+    rng = np.random.default_rng(31)
+    lib.oracle_set_mrt_rates(0.0, 0.0, 0.0)
+    for _ in range(10):
+        f = _random_cell(rng)
+        Fx, Fy = rng.uniform(-2e-3, 2e-3, 2)
+        psi = rng.uniform(0.1, 0.5)
+        for tau in (0.6, 1.3):
+            a = oracle.collide_cell(oracle.MRT, tau, 0.1, f, Fx, Fy, psi, lib=lib)
+            b = oracle.collide_cell(oracle.IMPROVED, tau, 0.1, f, Fx, Fy, psi, lib=lib)
+            fails += _close("MRT at rates 1/tau vs Eq. 31", a, b, rtol=1e-13, atol=1e-17)
+    return fails
+
+
+def pin_mrt_moment_relaxation(lib):
+    """Post-collision moments against the closed-form D2Q9 moments of
+    f_eq(rho, v) and of the improved forcing term: m* = m - s (m - m_eq) +
+    (1 - s/2) S with m_eq = (rho, -2rho + 3rho|v|^2, rho - 3rho|v|^2, rho v_x,
+    -rho v_x, rho v_y, -rho v_y, rho (v_x^2 - v_y^2), rho v_x v_y) and S = (0,
+    6 v'.F, -6 v'.F, F_x, -F_x, F_y, -F_y, 2 (v'_x F_x - v'_y F_y),
+    v'_x F_y + v'_y F_x)."""
+    fails = []
+    M = _mrt_basis()
+    rng = np.random.default_rng(32)
+    se, seps, sq, tau, sigma = 0.8, 1.1, 1.3, 0.7, 0.1
+    lib.oracle_set_mrt_rates(se, seps, sq)
+    try:
+        for _ in range(10):
+            f = _random_cell(rng)
+            Fx, Fy = rng.uniform(-2e-3, 2e-3, 2)
+            psi = rng.uniform(0.1, 0.5)
+            out = oracle.collide_cell(oracle.MRT, tau, sigma, f, Fx, Fy, psi, lib=lib)
+            m, mo = M @ f, M @ out
+            rho = m[0]
+            vx, vy = m[3] / rho + Fx / (2 * rho), m[5] / rho + Fy / (2 * rho)
+            vpx = vx + sigma * Fx / ((tau - 0.5) * psi ** 2)
+            vpy = vy + sigma * Fy / ((tau - 0.5) * psi ** 2)
+            v2 = vx * vx + vy * vy
+            meq = np.array([rho, -2 * rho + 3 * rho * v2, rho - 3 * rho * v2, rho * vx,
+                            -rho * vx, rho * vy, -rho * vy, rho * (vx * vx - vy * vy),
+                            rho * vx * vy])
+            vF = vpx * Fx + vpy * Fy
+            S = np.array([0.0, 6 * vF, -6 * vF, Fx, -Fx, Fy, -Fy, 2 * (vpx * Fx - vpy * Fy),
+                          vpx * Fy + vpy * Fx])
+            rate = np.array([1 / tau, se, seps, 1 / tau, sq, 1 / tau, sq, 1 / tau, 1 / tau])
+            fails += _close("MRT moments", mo, m - rate * (m - meq) + (1 - rate / 2) * S,
+                            atol=4e-15)
+    finally:
+        lib.oracle_set_mrt_rates(0.0, 0.0, 0.0)
+    return fails
+
+
 ALL_FAST_PINS = [
     pin_feq_moments, pin_force_stencil_taylor, pin_force_pair_antisymmetry,
     pin_stream_moves_along_e, pin_table1_forcing_moments, pin_paper_rewrites,
     pin_collision_momentum, pin_eos_and_psi, pin_step_conservation,
     pin_uniform_fixed_point, pin_shear_wave_decay, pin_taylor_green_decay,
     pin_guo_flat_interface_is_eps0, pin_static_interface_actual_velocity,
+    pin_mrt_reduces_to_improved, pin_mrt_moment_relaxation,
 ]

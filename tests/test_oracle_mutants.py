@@ -28,10 +28,10 @@ MUTANTS = {
     "upsilon = c_s^2 (tau - 1/2)": ("double ups = tau - 0.5;", "double ups = (tau - 0.5) / 3.0;"),
     "improved f_eq at u": ("oracle_feq(rho, vx, vy, feq); /* Guo",
                            "oracle_feq(rho, ux, uy, feq); /* Guo"),
-    "improved without (1 - 1/2tau)": ("double Fa = wq[a] * (1.0 - 1.0 / (2.0 * tau)) *",
-                                      "double Fa = wq[a] *"),
-    "v' with psi not psi^2": ("double vpx = vx + sigma * Fx / (ups * psi * psi);",
-                              "double vpx = vx + sigma * Fx / (ups * psi);"),
+    "improved without (1 - 1/2tau)": ("double Fa = (1.0 - 1.0 / (2.0 * tau)) * improved_bracket(",
+                                      "double Fa = improved_bracket("),
+    "v' with psi not psi^2": ("*vpx = *vx + sigma * Fx / (ups * psi * psi);",
+                              "*vpx = *vx + sigma * Fx / (ups * psi);"),
     "f_eq drops c_s^2 u.u": ("(eu * eu - cs2() * uu)", "(eu * eu - uu)"),
     "weight 1/36 -> 1/18": ("1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};",
                             "1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 18.0};"),
@@ -48,6 +48,12 @@ MUTANTS = {
     "Guo term B_e <- C_e": ("return wq[a] * (Be * Fe / cs2()", "return wq[a] * (Ce * Fe / cs2()"),
     "actual velocity u + F/rho": ("vy[c] = uy[c] + Fy[c] / (2.0 * rho[c]);",
                                   "vy[c] = uy[c] + Fy[c] / rho[c];"),
+    "MRT without the half-rate factor": ("(1.0 - 0.5 * S[k]) * mf", "mf"),
+    "MRT energy rates swapped": ("double S[Q] = {sv, se, seps, sv, sq, sv, sq, sv, sv};",
+                                 "double S[Q] = {sv, seps, se, sv, sq, sv, sq, sv, sv};"),
+    "MRT energy row 3|c|^2 -> 2|c|^2": ("M[1][a] = -4.0 + 3.0 * c2;", "M[1][a] = -4.0 + 2.0 * c2;"),
+    "MRT f_eq moments at u": ("oracle_feq(rho, vx, vy, feq);\n  for (int a = 0; a < Q; ++a) fhat",
+                              "oracle_feq(rho, ux, uy, feq);\n  for (int a = 0; a < Q; ++a) fhat"),
     "SC relaxation 1/tau -> tau": ("for (int a = 0; a < Q; ++a) fout[a] = f[a] - (f[a] - feq[a]) / tau;\n      return 0;\n    }\n    case OR_EDM: {",
                                    "for (int a = 0; a < Q; ++a) fout[a] = f[a] - (f[a] - feq[a]) * tau;\n      return 0;\n    }\n    case OR_EDM: {"),
 }

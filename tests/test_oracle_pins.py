@@ -116,61 +116,3 @@ def test_laplace_law_on_droplets(lib):
     assert slope > 0 and r2 > 0.999, (slope, r2)
     assert abs(icpt) < 0.05 * slope * x.min(), (icpt, slope)
 
-
-def _mrt_cell(seed):
-    rng = np.random.default_rng(seed)
-    rho = rng.uniform(0.1, 0.4)
-    f = oracle.feq(rho, rng.uniform(-0.05, 0.05), rng.uniform(-0.05, 0.05))
-    f = f * (1 + 0.05 * rng.uniform(-1, 1, 9))
-    return f, rng.uniform(-2e-3, 2e-3), rng.uniform(-2e-3, 2e-3), rng.uniform(0.1, 0.5)
-
-
-def test_mrt_with_equal_rates_is_the_improved_scheme(lib):
-    """With every rate 1/tau the MRT form is Eq. 31 itself."""
-    oracle.set_mrt_rates(0.0, 0.0, 0.0, lib=lib)
-    for seed in range(20):
-        f, Fx, Fy, psi = _mrt_cell(seed)
-        for tau in (0.6, 0.8, 1.3):
-            a = oracle.collide_cell(oracle.MRT, tau, 0.1, f, Fx, Fy, psi, lib=lib)
-            b = oracle.collide_cell(oracle.IMPROVED, tau, 0.1, f, Fx, Fy, psi, lib=lib)
-            assert np.max(np.abs(a - b)) <= 1e-15 * np.max(np.abs(b)) * 16
-
-
-def test_mrt_relaxes_each_moment_towards_its_closed_form(lib):
-    """Post-collision moments against the closed forms of the D2Q9 moments
-    of f_eq(rho, v) and of the improved forcing term (Lallemand-Luo basis):
-    m* = m - s (m - m_eq) + (1 - s/2) S, with m_eq = (rho, -2rho + 3rho|v|^2,
-    rho - 3rho|v|^2, rho v_x, -rho v_x, rho v_y, -rho v_y, rho (v_x^2 - v_y^2),
-    rho v_x v_y) and S = (0, 6 v'.F, -6 v'.F, F_x, -F_x, F_y, -F_y,
-    2 (v'_x F_x - v'_y F_y), v'_x F_y + v'_y F_x); density conserved, momentum
-    rho u + F."""
-    ex, ey = np.array(oracle.EX, float), np.array(oracle.EY, float)
-    c2 = ex ** 2 + ey ** 2
-    M = np.array([np.ones(9), -4 + 3 * c2, 4 - 10.5 * c2 + 4.5 * c2 ** 2, ex, (-5 + 3 * c2) * ex,
-                  ey, (-5 + 3 * c2) * ey, ex ** 2 - ey ** 2, ex * ey])
-    se, seps, sq, tau, sigma = 0.8, 1.1, 1.3, 0.7, 0.1
-    oracle.set_mrt_rates(se, seps, sq, lib=lib)
-    try:
-        for seed in range(20):
-            f, Fx, Fy, psi = _mrt_cell(100 + seed)
-            out = oracle.collide_cell(oracle.MRT, tau, sigma, f, Fx, Fy, psi, lib=lib)
-            m, mo = M @ f, M @ out
-            rho = m[0]
-            ux, uy = m[3] / rho, m[5] / rho
-            vx, vy = ux + Fx / (2 * rho), uy + Fy / (2 * rho)
-            vpx = vx + sigma * Fx / ((tau - 0.5) * psi ** 2)
-            vpy = vy + sigma * Fy / ((tau - 0.5) * psi ** 2)
-            v2 = vx * vx + vy * vy
-            meq = np.array([rho, -2 * rho + 3 * rho * v2, rho - 3 * rho * v2, rho * vx, -rho * vx,
-                            rho * vy, -rho * vy, rho * (vx * vx - vy * vy), rho * vx * vy])
-            vF = vpx * Fx + vpy * Fy
-            S = np.array([0.0, 6 * vF, -6 * vF, Fx, -Fx, Fy, -Fy, 2 * (vpx * Fx - vpy * Fy),
-                          vpx * Fy + vpy * Fx])
-            rate = np.array([1 / tau, se, seps, 1 / tau, sq, 1 / tau, sq, 1 / tau, 1 / tau])
-            want = m - rate * (m - meq) + (1 - rate / 2) * S
-            assert np.allclose(mo, want, rtol=0, atol=1e-15 * 40), (seed, mo - want)
-            assert mo[0] == pytest.approx(rho, rel=1e-14)
-            assert mo[3] == pytest.approx(rho * ux + Fx, abs=1e-16 * 40)
-            assert mo[5] == pytest.approx(rho * uy + Fy, abs=1e-16 * 40)
-    finally:
-        oracle.set_mrt_rates(0.0, 0.0, 0.0, lib=lib)
