@@ -56,6 +56,9 @@ MEASURED_TRAFFIC = {
     # the same kernel after comment edits and packed 16-bit conversions
     # (FP32 code unchanged): 2.431 GB read + 2.368 GB written per launch
     ("187a00600d401039", "fp32", 8192, "pair"): 4.7984e9,
+    # after adding the MRT scheme (three rates in the kernel arguments):
+    # 2.431 GB read + 2.368 GB written per launch
+    ("7bc3668251e0d237", "fp32", 8192, "pair"): 4.7986e9,
 }
 
 

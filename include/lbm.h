@@ -58,8 +58,15 @@ enum {
                               sigma = 0 is Guo's scheme (Eqs. 12-13)         */
   LBM_SCHEME_NOFORCE = 3,  /* F = 0: plain BGK (force-free checks)           */
   LBM_SCHEME_EDM_MOD = 4,  /* EDM with C_e = 1/tau (Sec. III C)             */
-  LBM_SCHEME_LADD = 5      /* Ladd: u in f_eq and in F_a, B_e = C_e = 1
+  LBM_SCHEME_LADD = 5,     /* Ladd: u in f_eq and in F_a, B_e = C_e = 1
                               (Table I)                                      */
+  LBM_SCHEME_MRT = 6       /* the improved scheme in multiple-relaxation-time
+                              form (the extension stated at the end of
+                              Sec. IV; the paper gives no formula, see
+                              lbm_set_mrt_rates): D2Q9 moments relax at their
+                              own rates towards f_eq(rho, v), with the improved
+                              forcing term's moments (v') added at (1 - s/2);
+                              single lattices only, not lbm_batch_*          */
 };
 
 /* Storage precision of the populations. */
@@ -171,6 +178,13 @@ unsigned long long lbm_kernel_launch_count(void);
 enum { LBM_VARIANT_AUTO = 0, LBM_VARIANT_REGISTER = 1, LBM_VARIANT_STAGED = 2,
        LBM_VARIANT_PAIR = 3 };
 lbm_status lbm_set_kernel_variant(lbm_ctx *ctx, int variant);
+
+/* Relaxation rates of LBM_SCHEME_MRT for the energy, energy-square and
+ * energy-flux moments (Lallemand-Luo D2Q9 basis); the stresses relax at
+ * 1/tau, and a rate <= 0 (the default) means 1/tau, which makes the scheme
+ * identical to LBM_SCHEME_IMPROVED (up to rounding).  Rates must be < 2.
+ * Applies to later lbm_step calls. */
+lbm_status lbm_set_mrt_rates(lbm_ctx *ctx, double s_e, double s_eps, double s_q);
 
 /* Rows per warp band of the step kernel (0 = automatic: one wave of warps,
  * at least 4 rows each).  Changes only speed, never results. */

@@ -839,6 +839,7 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
     d.P.sigma_ups = float(s.sigma / (s.tau - 0.5));
     d.P.guo = float(1.0 - 1.0 / (2.0 * s.tau));
     d.P.scheme = s.scheme;
+    d.P.s_e = d.P.s_eps = d.P.s_q = d.P.omega;  // unused: the batch has no MRT scheme
     set_geometry(d, 32);
     const size_t cells = size_t(s.nx) * s.ny;
     off += (9 * cells + 31) / 32 * 32;

@@ -164,6 +164,7 @@ struct lbm_ctx {
   int last_scheme = LBM_SCHEME_SC;
   int sm_count = 0;
   int band_rows_override = 0;
+  double mrt[3] = {0.0, 0.0, 0.0};  // s_e, s_eps, s_q of the MRT scheme (<= 0: 1/tau)
   int variant = LBM_VARIANT_AUTO;
   std::string err;
 };
@@ -301,7 +302,7 @@ lbm_status ensure_tmp(lbm_ctx* c, double** buf, size_t count) {
 lbm_status queue_steps(lbm_ctx* c, int n, int scheme, double tau, double sigma) {
   if (!c) return LBM_E_INVAL;
   if (n < 0) return fail(c, LBM_E_INVAL, "n must be >= 0");
-  if (scheme < 0 || scheme > LBM_SCHEME_LADD) return fail(c, LBM_E_INVAL, "unknown scheme");
+  if (scheme < 0 || scheme > LBM_SCHEME_MRT) return fail(c, LBM_E_INVAL, "unknown scheme");
   if (!(tau > 0.5) || !std::isfinite(tau)) return fail(c, LBM_E_INVAL, "tau must be > 1/2");
   if (!std::isfinite(sigma)) return fail(c, LBM_E_INVAL, "sigma must be finite");
   if (!c->initialized) return fail(c, LBM_E_STATE, "state not initialised");
@@ -311,6 +312,9 @@ lbm_status queue_steps(lbm_ctx* c, int n, int scheme, double tau, double sigma) 
   L.omega = 1.0 / tau;
   L.sigma_ups = sigma / (tau - 0.5);
   L.guo = 1.0 - 1.0 / (2.0 * tau);
+  L.s_e = c->mrt[0] > 0.0 ? c->mrt[0] : 1.0 / tau;
+  L.s_eps = c->mrt[1] > 0.0 ? c->mrt[1] : 1.0 / tau;
+  L.s_q = c->mrt[2] > 0.0 ? c->mrt[2] : 1.0 / tau;
   int grid = 0;
   lbm_status st = geometry(c, scheme, kStepMode, L, grid);
   if (st != LBM_OK) return st;
@@ -607,6 +611,16 @@ lbm_status lbm_set_kernel_variant(lbm_ctx* c, int variant) {
   return LBM_OK;
 }
 
+lbm_status lbm_set_mrt_rates(lbm_ctx* c, double s_e, double s_eps, double s_q) {
+  if (!c) return LBM_E_INVAL;
+  for (double s : {s_e, s_eps, s_q})
+    if (!std::isfinite(s) || !(s < 2.0)) return fail(c, LBM_E_INVAL, "MRT rates must be < 2");
+  c->mrt[0] = s_e;
+  c->mrt[1] = s_eps;
+  c->mrt[2] = s_q;
+  return LBM_OK;
+}
+
 lbm_status lbm_set_band_rows(lbm_ctx* c, int band_rows) {
   if (!c) return LBM_E_INVAL;
   if (band_rows < 0) return fail(c, LBM_E_INVAL, "band_rows must be >= 0");
@@ -617,7 +631,7 @@ lbm_status lbm_set_band_rows(lbm_ctx* c, int band_rows) {
 lbm_status lbm_get_launch_geometry(lbm_ctx* c, int scheme, int* n_strips, int* band_rows,
                                    int* n_bands, int* grid) {
   if (!c) return LBM_E_INVAL;
-  if (scheme < 0 || scheme > LBM_SCHEME_LADD) return fail(c, LBM_E_INVAL, "unknown scheme");
+  if (scheme < 0 || scheme > LBM_SCHEME_MRT) return fail(c, LBM_E_INVAL, "unknown scheme");
   DeviceGuard guard(c->p.device);
   StripLaunch L = base_launch(c);
   int g = 0;

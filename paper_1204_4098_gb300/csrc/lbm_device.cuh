@@ -70,6 +70,7 @@ struct Phys {
   C sigma_ups;  // sigma / (tau - 1/2)  (Eq. 31: v' = v + sigma F / (upsilon psi^2))
   C guo;        // 1 - 1 / (2 tau)  (B_e = C_e of Eq. 13)
   int scheme;   // forcing scheme, read only by collide<C, kAnyForced>
+  C s_e, s_eps, s_q;  // MRT rates of the energy, energy-square, energy-flux moments
 };
 
 // Reciprocal and square root for the per-cell physics.  FP64 keeps the IEEE
@@ -102,7 +103,7 @@ __device__ __forceinline__ C psi_of_rho(C rho, const Phys<C>& P, bool& bad) {
 // ---------------------------------------------------------------------------
 // collision of one cell, Eqs. 1-2 with the forcing schemes of Table I
 // ---------------------------------------------------------------------------
-enum Scheme { kSC = 0, kEDM = 1, kImproved = 2, kNoForce = 3, kEDMMod = 4, kLadd = 5 };
+enum Scheme { kSC = 0, kEDM = 1, kImproved = 2, kNoForce = 3, kEDMMod = 4, kLadd = 5, kMRT = 6 };
 // Template value: the scheme (one that evaluates psi, i.e. not kNoForce) is
 // read from Phys::scheme at run time.  One inlined body then serves every
 // instance of a mixed batch, instead of one body per scheme.
@@ -125,9 +126,89 @@ constexpr int kAnyForced = -1;
 // persistent -- produce bit-identical populations.  With SCHEME fixed the
 // branches below fold at compile time; with kAnyForced they are taken on
 // P.scheme (uniform across a warp) and compute the same values.
+// Multiple-relaxation-time form of the improved scheme (the extension the
+// paper states at the end of Sec. IV).  D2Q9 moments in the Lallemand-Luo
+// basis: density rho, energy e, energy square eps, momentum j, energy flux q,
+// stresses pxx = f.(cx^2 - cy^2), pxy = f.(cx cy).  Each non-conserved moment
+// relaxes with its own rate s towards its value at f_eq(rho, v) and receives
+// (1 - s/2) times the improved forcing term's moment:
+//   e:   -2 rho + 3 rho |v|^2,  6 v'.F        eps: rho - 3 rho |v|^2, -6 v'.F
+//   q:   -rho v,               -F             pxx: rho (vx^2 - vy^2), 2 (v'x Fx - v'y Fy)
+//   pxy: rho vx vy,             v'x Fy + v'y Fx
+// (stresses at 1/tau, e / eps / q at P.s_e / P.s_eps / P.s_q); the momentum
+// becomes j + F.  Equal rates 1/tau give Eq. 31.  The populations follow
+// from the orthogonal basis (row norms 9, 36, 36, 6, 12, 6, 12, 4, 4), the
+// rest population as the remainder of rho.
+template <class C>
+__device__ __forceinline__ void collide_mrt(C (&f)[kQ], C rho, C Fx, C Fy, C psi,
+                                            const Phys<C>& P) {
+  const C ax = sub_rn(f[1], f[3]), ay = sub_rn(f[2], f[4]);  // axis odd parts
+  const C bx = add_rn(sub_rn(f[5], f[6]), sub_rn(f[8], f[7]));  // diagonal x odd part
+  const C by = sub_rn(add_rn(f[5], f[6]), add_rn(f[7], f[8]));  // diagonal y odd part
+  const C s1 = add_rn(add_rn(f[1], f[3]), add_rn(f[2], f[4]));  // axis sum
+  const C s2 = add_rn(add_rn(f[5], f[7]), add_rn(f[6], f[8]));  // diagonal sum
+  const C jx = add_rn(ax, bx), jy = add_rn(ay, by);
+  const C qx = fma_rn(C(-2), ax, bx), qy = fma_rn(C(-2), ay, by);
+  const C e = fma_rn(C(2), s2, -fma_rn(C(4), f[0], s1));
+  const C eps = fma_rn(C(-2), s1, fma_rn(C(4), f[0], s2));
+  const C pxx = sub_rn(add_rn(f[1], f[3]), add_rn(f[2], f[4]));
+  const C pxy = sub_rn(add_rn(f[5], f[7]), add_rn(f[6], f[8]));
+
+  const C inv_rho = fast_div(C(1), rho);
+  const C half_inv = mul_rn(C(0.5), inv_rho);
+  const C vx = fma_rn(half_inv, Fx, mul_rn(jx, inv_rho));
+  const C vy = fma_rn(half_inv, Fy, mul_rn(jy, inv_rho));
+  const C sg = fast_div(P.sigma_ups, mul_rn(psi, psi));
+  const C wx = fma_rn(sg, Fx, vx), wy = fma_rn(sg, Fy, vy);  // v'
+  const C v2 = fma_rn(vx, vx, mul_rn(vy, vy));
+  const C rv2 = mul_rn(C(3), mul_rn(rho, v2));
+  const C wF6 = mul_rn(C(6), fma_rn(wx, Fx, mul_rn(wy, Fy)));
+
+  auto relax = [](C m, C meq, C s, C force) {
+    return fma_rn(sub_rn(C(1), mul_rn(C(0.5), s)), force, fma_rn(-s, sub_rn(m, meq), m));
+  };
+  const C sv = P.omega;
+  const C e_s = relax(e, fma_rn(C(-2), rho, rv2), P.s_e, wF6);
+  const C eps_s = relax(eps, sub_rn(rho, rv2), P.s_eps, -wF6);
+  const C qx_s = relax(qx, -mul_rn(rho, vx), P.s_q, -Fx);
+  const C qy_s = relax(qy, -mul_rn(rho, vy), P.s_q, -Fy);
+  const C pxx_s = relax(pxx, mul_rn(rho, fma_rn(vx, vx, -mul_rn(vy, vy))), sv,
+                        mul_rn(C(2), fma_rn(wx, Fx, -mul_rn(wy, Fy))));
+  const C pxy_s = relax(pxy, mul_rn(rho, mul_rn(vx, vy)), sv, fma_rn(wx, Fy, mul_rn(wy, Fx)));
+  const C jx_s = add_rn(jx, Fx), jy_s = add_rn(jy, Fy);
+
+  const C r9 = mul_rn(rho, C(1) / C(9));
+  const C base_ax = fma_rn(C(-1) / C(36), e_s, fma_rn(C(-1) / C(18), eps_s, r9));
+  const C base_dg = fma_rn(C(1) / C(18), e_s, fma_rn(C(1) / C(36), eps_s, r9));
+  const C px4 = mul_rn(C(0.25), pxx_s), pd4 = mul_rn(C(0.25), pxy_s);
+  const C ox = mul_rn(C(1) / C(6), sub_rn(jx_s, qx_s));   // axis x odd part
+  const C oy = mul_rn(C(1) / C(6), sub_rn(jy_s, qy_s));
+  const C dx = fma_rn(C(1) / C(12), qx_s, mul_rn(C(1) / C(6), jx_s));  // diagonal parts
+  const C dy = fma_rn(C(1) / C(12), qy_s, mul_rn(C(1) / C(6), jy_s));
+  const C ex_even = add_rn(base_ax, px4), ey_even = sub_rn(base_ax, px4);
+  f[1] = add_rn(ex_even, ox);
+  f[3] = sub_rn(ex_even, ox);
+  f[2] = add_rn(ey_even, oy);
+  f[4] = sub_rn(ey_even, oy);
+  const C d57 = add_rn(base_dg, pd4), d68 = sub_rn(base_dg, pd4);
+  const C pp = add_rn(dx, dy), pm = sub_rn(dx, dy);
+  f[5] = add_rn(d57, pp);  // e5 = (1, 1)
+  f[7] = sub_rn(d57, pp);  // e7 = (-1, -1)
+  f[8] = add_rn(d68, pm);  // e8 = (1, -1)
+  f[6] = sub_rn(d68, pm);  // e6 = (-1, 1)
+  C rest = f[1];
+#pragma unroll
+  for (int a = 2; a < kQ; ++a) rest = add_rn(rest, f[a]);
+  f[0] = sub_rn(rho, rest);
+}
+
 template <class C, int SCHEME>
 __device__ __forceinline__ void collide(C (&f)[kQ], C rho, C Fx, C Fy, C psi,
                                         const Phys<C>& P) {
+  if constexpr (SCHEME == kMRT) {
+    collide_mrt<C>(f, rho, Fx, Fy, psi, P);
+    return;
+  }
   const int sch = SCHEME == kAnyForced ? P.scheme : SCHEME;
   const C jx = add_rn(add_rn(sub_rn(f[1], f[3]), sub_rn(f[5], f[6])), sub_rn(f[8], f[7]));
   const C jy = sub_rn(add_rn(sub_rn(f[2], f[4]), add_rn(f[5], f[6])), add_rn(f[7], f[8]));

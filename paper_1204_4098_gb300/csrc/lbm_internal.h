@@ -22,6 +22,7 @@ struct StripLaunch {
   size_t plane;
   // physics (converted to the compute type by each translation unit)
   double RT, a, b4, two_over_G, minus_G, tau, omega, sigma_ups, guo;
+  double s_e, s_eps, s_q;  // MRT rates (scheme 6)
 };
 
 enum Precision { kFP32 = 0, kFP64 = 1, kBF16Dev = 2, kFP16Dev = 3 };

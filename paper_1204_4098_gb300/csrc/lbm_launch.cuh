@@ -36,6 +36,9 @@ StripArgs<S> make_args(const StripLaunch& L) {
   A.P.sigma_ups = C(L.sigma_ups);
   A.P.guo = C(L.guo);
   A.P.scheme = 0;  // the single-domain kernels fix the scheme at compile time
+  A.P.s_e = C(L.s_e);
+  A.P.s_eps = C(L.s_eps);
+  A.P.s_q = C(L.s_q);
   return A;
 }
 
@@ -64,6 +67,7 @@ cudaError_t strip_launch_t(int scheme, int mode, const StripLaunch& L, int grid,
     case kNoForce: return launch_one<S, kNoForce, kModeStep>(L, grid, s);
     case kEDMMod: return launch_one<S, kEDMMod, kModeStep>(L, grid, s);
     case kLadd: return launch_one<S, kLadd, kModeStep>(L, grid, s);
+    case kMRT: return launch_one<S, kMRT, kModeStep>(L, grid, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -79,6 +83,7 @@ cudaError_t strip_occupancy_t(int scheme, int mode, int* b) {
     case kNoForce: return occ_one<S, kNoForce, kModeStep>(b);
     case kEDMMod: return occ_one<S, kEDMMod, kModeStep>(b);
     case kLadd: return occ_one<S, kLadd, kModeStep>(b);
+    case kMRT: return occ_one<S, kMRT, kModeStep>(b);
   }
   return cudaErrorInvalidValue;
 }
@@ -97,6 +102,7 @@ cudaError_t strip_tma_launch_t(int scheme, const StripLaunch& L, int grid, cudaS
       case kNoForce: strip_tma_kernel<kNoForce><<<grid, kStripThreads, 0, s>>>(A); break;
       case kEDMMod: strip_tma_kernel<kEDMMod><<<grid, kStripThreads, 0, s>>>(A); break;
       case kLadd: strip_tma_kernel<kLadd><<<grid, kStripThreads, 0, s>>>(A); break;
+      case kMRT: strip_tma_kernel<kMRT><<<grid, kStripThreads, 0, s>>>(A); break;
       default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -115,6 +121,7 @@ cudaError_t strip_tma_occupancy_t(int scheme, int* b) {
       case kNoForce: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, strip_tma_kernel<kNoForce>, kStripThreads, 0);
       case kEDMMod: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, strip_tma_kernel<kEDMMod>, kStripThreads, 0);
       case kLadd: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, strip_tma_kernel<kLadd>, kStripThreads, 0);
+      case kMRT: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, strip_tma_kernel<kMRT>, kStripThreads, 0);
     }
     return cudaErrorInvalidValue;
   }
@@ -144,6 +151,7 @@ cudaError_t strip2_launch_t(int scheme, int mode, const StripLaunch& L, int grid
       case kNoForce: return launch2_one<S, kNoForce, kModeStep>(L, grid, s);
       case kEDMMod: return launch2_one<S, kEDMMod, kModeStep>(L, grid, s);
       case kLadd: return launch2_one<S, kLadd, kModeStep>(L, grid, s);
+      case kMRT: return launch2_one<S, kMRT, kModeStep>(L, grid, s);
     }
     return cudaErrorInvalidValue;
   }
@@ -160,6 +168,7 @@ cudaError_t strip2_occupancy_t(int scheme, int mode, int* b) {
       case kNoForce: return occ2_one<S, kNoForce, kModeStep>(b);
       case kEDMMod: return occ2_one<S, kEDMMod, kModeStep>(b);
       case kLadd: return occ2_one<S, kLadd, kModeStep>(b);
+      case kMRT: return occ2_one<S, kMRT, kModeStep>(b);
     }
     return cudaErrorInvalidValue;
   }

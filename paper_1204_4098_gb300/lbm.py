@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "liblbm_gb300.so")
 LBM_OK, LBM_E_INVAL, LBM_E_NOMEM, LBM_E_CUDA, LBM_E_DIVERGED, LBM_E_TIMEOUT, LBM_E_STATE = range(7)
 STATUS_NAMES = {0: "LBM_OK", 1: "LBM_E_INVAL", 2: "LBM_E_NOMEM", 3: "LBM_E_CUDA",
                 4: "LBM_E_DIVERGED", 5: "LBM_E_TIMEOUT", 6: "LBM_E_STATE"}
-SC, EDM, IMPROVED, NOFORCE, EDM_MOD, LADD = range(6)
+SC, EDM, IMPROVED, NOFORCE, EDM_MOD, LADD, MRT = range(7)
 FP32, FP64, BF16DEV, FP16DEV = range(4)
 VARIANT_AUTO, VARIANT_REGISTER, VARIANT_STAGED, VARIANT_PAIR = range(4)
 
@@ -100,6 +100,7 @@ SIGNATURES = {
     "lbm_set_kernel_variant": (_I, [_P, _I]),
     "lbm_get_launch_geometry": (_I, [_P, _I, _IP, _IP, _IP, _IP]),
     "lbm_get_kernel_variant": (_I, [_P, _IP]),
+    "lbm_set_mrt_rates": (_I, [_P, _D, _D, _D]),
     "lbm_selftest_wait_timeout": (_I, [_I, ctypes.c_longlong, _IP]),
     "lbm_mass_f32_noalloc": (_I, [_P, ctypes.c_size_t, _P, _P]),
     "lbm_batch_default_params": (None, [ctypes.POINTER(lbm_batch_params)]),
@@ -305,6 +306,12 @@ class Lattice:
                                                   *[ctypes.byref(x) for x in v]),
                     "lbm_get_launch_geometry")
         return dict(zip(("n_strips", "band_rows", "n_bands", "grid"), (x.value for x in v)))
+
+    def set_mrt_rates(self, s_e=0.0, s_eps=0.0, s_q=0.0):
+        """Rates of the MRT scheme's energy, energy-square and energy-flux
+        moments (<= 0: 1/tau)."""
+        self._check(lib().lbm_set_mrt_rates(self.ctx, float(s_e), float(s_eps), float(s_q)),
+                    "lbm_set_mrt_rates")
 
     def variant(self):
         """The kernel variant lbm_step resolves to (VARIANT_REGISTER/STAGED/PAIR)."""

@@ -74,6 +74,7 @@ def test_create_rejects_bad_arguments_without_cuda(L):
 
 def test_null_context_calls_are_rejected(L):
     assert L.lbm_step(None, 1, 0, 1.0, 0.0) == lbm.LBM_E_INVAL
+    assert L.lbm_set_mrt_rates(None, 1.0, 1.0, 1.0) == lbm.LBM_E_INVAL
     assert L.lbm_destroy(None) == lbm.LBM_OK
 
 
