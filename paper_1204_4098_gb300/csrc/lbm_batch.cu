@@ -2,16 +2,22 @@
 //
 // Every instance runs the fused step body of the single-domain kernels
 // (strip_run2, two columns per lane, for even nx, else strip_run; both in
-// lbm_kernels.cuh) on its own slice of one packed buffer pair.
-// A window of `window` steps is one CUDA graph, in one of two launch modes:
-//   work list   -- one launch per step; warps take strip x band items of
-//                  all active instances from a prefix table (balanced for any
-//                  mix of sizes);
-//   persistent  -- one launch per window; each CTA owns whole instances
-//                  (longest-processing-time assignment) and only
+// lbm_kernels.cuh) on its own slice of one packed buffer pair.  Instances
+// fall in two classes by that body, each with kernels of its own (separate
+// register budgets).  A window of `window` steps is one CUDA graph, in one of
+// three launch modes:
+//   work list   -- per step, one launch per class; warps take strip x band
+//                  items of the class's active instances from a prefix table
+//                  (balanced for any mix of sizes); the two class kernels are
+//                  two branches of the graph;
+//   persistent  -- one launch per window and class; each CTA owns whole
+//                  instances (longest-processing-time assignment) and only
 //                  __syncthreads() separates its steps, so no CTA ever waits
-//                  for another.  Small active sets then stay in L2.
-// Both give bit-identical results (the band height never changes a value),
+//                  for another.  Small active sets then stay in L2;
+//   cooperative -- one cooperative launch per window (every CTA resident);
+//                  each step, warps take the work-list items of both classes,
+//                  then all CTAs meet at a bounded grid barrier.
+// All give bit-identical results (the band height never changes a value),
 // so the window-level autotuner can try configurations on live windows.
 // After each window one CTA per active instance reduces, in FP64, the row
 // means (coexistence densities, width, mass) and the largest density change
