@@ -9,7 +9,9 @@
  *   (3) the potential psi(rho) of Eq. 8 with the Carnahan-Starling p_EOS of
  *       Eq. 23 (a, b, R; c = 1, delta_t = 1, G < 0),
  *   (4) the interaction force of Eq. 3 with w(1) = 1/3, w(2) = 1/12,
- *   (5) BGK collision (Eqs. 1-2) with the chosen forcing scheme.
+ *   (5) BGK collision (Eqs. 1-2) with the chosen forcing scheme (or, for
+ *       LBM_SCHEME_MRT, the multiple-relaxation-time form of the improved
+ *       scheme).
  * All of it runs in one fused CUDA kernel per step; the host only validates
  * arguments, launches, and copies data in and out.
  *
