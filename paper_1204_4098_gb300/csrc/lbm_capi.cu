@@ -341,6 +341,25 @@ lbm_status queue_steps(lbm_ctx* c, int n, int scheme, double tau, double sigma) 
 
 }  // namespace
 
+namespace {
+
+// Device address of a page-locked, mapped host array (pinned memory under
+// unified addressing), or nullptr for pageable memory.  Kernels read and
+// write such arrays directly (over the CPU-GPU link), without a staging
+// buffer and a separate copy.
+template <class T>
+T* mapped_view(T* host) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type != cudaMemoryTypeHost || at.devicePointer == nullptr) return nullptr;
+  return static_cast<T*>(at.devicePointer);
+}
+
+}  // namespace
+
 extern "C" {
 
 void lbm_default_params(lbm_params* p) {
@@ -474,12 +493,19 @@ lbm_status lbm_init_density(lbm_ctx* c, const double* rho, const double* ux,
   lbm_status st = ensure_tmp(c, &c->d_tmp, 3 * c->plane);
   if (st != LBM_OK) return st;
   const size_t bytes = c->plane * sizeof(double);
-  double* d_rho = c->d_tmp;
-  double* d_ux = ux ? c->d_tmp + c->plane : nullptr;
-  double* d_uy = uy ? c->d_tmp + 2 * c->plane : nullptr;
-  LBM_CUDA(c, cudaMemcpyAsync(d_rho, rho, bytes, cudaMemcpyHostToDevice, c->stream));
-  if (ux) LBM_CUDA(c, cudaMemcpyAsync(d_ux, ux, bytes, cudaMemcpyHostToDevice, c->stream));
-  if (uy) LBM_CUDA(c, cudaMemcpyAsync(d_uy, uy, bytes, cudaMemcpyHostToDevice, c->stream));
+  // pinned inputs are read in place by the kernel; pageable ones are staged
+  const double* in[3] = {rho, ux, uy};
+  const double* dev[3] = {nullptr, nullptr, nullptr};
+  for (int k = 0; k < 3; ++k) {
+    if (!in[k]) continue;
+    dev[k] = mapped_view(in[k]);
+    if (!dev[k]) {
+      double* stage = c->d_tmp + k * c->plane;
+      LBM_CUDA(c, cudaMemcpyAsync(stage, in[k], bytes, cudaMemcpyHostToDevice, c->stream));
+      dev[k] = stage;
+    }
+  }
+  const double *d_rho = dev[0], *d_ux = dev[1], *d_uy = dev[2];
   LBM_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream));
   LBM_CUDA(c, set_state_launch(c->p.precision, c->f[c->cur], c->rho[c->cur], c->p.nx, c->p.ny,
                                c->plane, d_rho, d_ux, d_uy, nullptr, eos_check(c), c->stream));
@@ -536,9 +562,19 @@ lbm_status lbm_get_moments(lbm_ctx* c, double* rho, double* vx, double* vy) {
   StripLaunch L = base_launch(c);
   L.src = c->f[c->cur];
   L.rho_src = c->rho[c->cur];
-  L.out_rho = c->d_tmp;
-  L.out_vx = c->d_tmp + c->plane;
-  L.out_vy = c->d_tmp + 2 * c->plane;
+  // pinned outputs are written in place by the kernel; others go through
+  // staging slices and a copy (a NULL output is still written, to staging)
+  double* out[3] = {rho, vx, vy};
+  double* dev[3];
+  bool staged[3];
+  for (int k = 0; k < 3; ++k) {
+    dev[k] = out[k] ? mapped_view(out[k]) : nullptr;
+    staged[k] = dev[k] == nullptr;
+    if (staged[k]) dev[k] = c->d_tmp + k * c->plane;
+  }
+  L.out_rho = dev[0];
+  L.out_vx = dev[1];
+  L.out_vy = dev[2];
   const int mode = c->last_scheme == LBM_SCHEME_NOFORCE ? kObserveNoForceMode : kObserveMode;
   int grid = 0;
   st = geometry(c, LBM_SCHEME_SC, mode, L, grid);
@@ -550,9 +586,9 @@ lbm_status lbm_get_moments(lbm_ctx* c, double* rho, double* vx, double* vy) {
     LBM_CUDA(c, strip_launch(c->p.precision, LBM_SCHEME_SC, mode, L, grid, c->stream));
   count_launches(1);
   const size_t bytes = c->plane * sizeof(double);
-  if (rho) LBM_CUDA(c, cudaMemcpyAsync(rho, L.out_rho, bytes, cudaMemcpyDeviceToHost, c->stream));
-  if (vx) LBM_CUDA(c, cudaMemcpyAsync(vx, L.out_vx, bytes, cudaMemcpyDeviceToHost, c->stream));
-  if (vy) LBM_CUDA(c, cudaMemcpyAsync(vy, L.out_vy, bytes, cudaMemcpyDeviceToHost, c->stream));
+  for (int k = 0; k < 3; ++k)
+    if (out[k] && staged[k])
+      LBM_CUDA(c, cudaMemcpyAsync(out[k], dev[k], bytes, cudaMemcpyDeviceToHost, c->stream));
   return lbm_sync_status(c);
 }
 
