@@ -378,6 +378,15 @@ lbm_status lbm_mlp_predict(lbm_mlp *m, const float *X, int n, float *Y);
  * counterpart. */
 lbm_status lbm_selftest_wait_timeout(int device, long long polls, int *result);
 
+/* The same for the grid barrier of the batch engine's cooperative windows:
+ * a cooperative launch of 4 CTAs in which CTA 0 never arrives; the other
+ * three give up after the barrier's spin limit (well under a few seconds),
+ * record the timeout and return.  *result receives LBM_E_TIMEOUT (expected)
+ * or LBM_OK.  LBM_E_INVAL for a NULL result, LBM_E_CUDA when the device has
+ * no cooperative launch or a CUDA call fails.  The paper has no
+ * counterpart. */
+lbm_status lbm_selftest_grid_barrier_timeout(int device, int *result);
+
 /* FP64 sum of n FP32 values in device memory (for an FP32 population buffer
  * [9][ny][nx]: its total mass), written to the caller's device slot *d_out.
  * The paper has no counterpart: this is a deployment helper for callers that

@@ -178,6 +178,14 @@ __device__ __forceinline__ bool grid_barrier(unsigned* sync) {
   return ok_s != 0;
 }
 
+// Self-test of the grid barrier's bounded wait: CTA 0 leaves without
+// arriving (the arrival nothing makes), the others wait, give up after the
+// spin limit, flag kStatusTimeout in sync[2] and return.
+__global__ void __launch_bounds__(32) barrier_selftest_kernel(unsigned* sync) {
+  if (blockIdx.x == 0) return;  // block-uniform
+  grid_barrier(sync);
+}
+
 // `steps` steps of every active instance in one cooperative launch: in each
 // step warps take items of both classes from the prefix table (the item body
 // is chosen per instance), then all CTAs meet at the grid barrier.  Loads
@@ -1209,6 +1217,35 @@ lbm_status lbm_batch_get_moments(lbm_batch* b, int i, double* rho, double* vx, d
                                    cudaMemcpyDeviceToHost, b->stream));
   LBM_BCUDA(b, cudaStreamSynchronize(b->stream));
   return LBM_OK;
+}
+
+lbm_status lbm_selftest_grid_barrier_timeout(int device, int* result) {
+  if (!result) return LBM_E_INVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return LBM_E_CUDA;
+  }
+  BDeviceGuard guard(device);
+  int coop = 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess || !coop)
+    return LBM_E_CUDA;
+  unsigned* d_sync = nullptr;
+  if (cudaMalloc(&d_sync, 3 * sizeof(unsigned)) != cudaSuccess) return LBM_E_NOMEM;
+  lbm_status st = LBM_OK;
+  unsigned h[3] = {0, 0, 0};
+  void* args[] = {&d_sync};
+  if (cudaMemset(d_sync, 0, 3 * sizeof(unsigned)) != cudaSuccess ||
+      cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(barrier_selftest_kernel),
+                                  dim3(4), dim3(32), args, 0, nullptr) != cudaSuccess ||
+      cudaMemcpy(h, d_sync, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    st = LBM_E_CUDA;
+  }
+  count_launches(1);
+  cudaFree(d_sync);
+  if (st == LBM_OK) *result = (h[2] & kStatusTimeout) ? LBM_E_TIMEOUT : LBM_OK;
+  return st;
 }
 
 lbm_status lbm_batch_get_stats(const lbm_batch* b, lbm_batch_stats* s) {

@@ -102,6 +102,7 @@ SIGNATURES = {
     "lbm_get_kernel_variant": (_I, [_P, _IP]),
     "lbm_set_mrt_rates": (_I, [_P, _D, _D, _D]),
     "lbm_selftest_wait_timeout": (_I, [_I, ctypes.c_longlong, _IP]),
+    "lbm_selftest_grid_barrier_timeout": (_I, [_I, _IP]),
     "lbm_mass_f32_noalloc": (_I, [_P, ctypes.c_size_t, _P, _P]),
     "lbm_batch_default_params": (None, [ctypes.POINTER(lbm_batch_params)]),
     "lbm_batch_create": (_I, [ctypes.POINTER(lbm_batch_params), ctypes.POINTER(lbm_instance),
@@ -194,6 +195,16 @@ def selftest_wait_timeout(device=0, polls=1000):
     st = lib().lbm_selftest_wait_timeout(int(device), int(polls), ctypes.byref(r))
     if st:
         raise LbmError(st, "lbm_selftest_wait_timeout")
+    return r.value
+
+
+def selftest_grid_barrier_timeout(device=0):
+    """Status of the batch grid barrier when one CTA never arrives
+    (LBM_E_TIMEOUT expected)."""
+    r = _I()
+    st = lib().lbm_selftest_grid_barrier_timeout(int(device), ctypes.byref(r))
+    if st:
+        raise LbmError(st, "lbm_selftest_grid_barrier_timeout")
     return r.value
 
 

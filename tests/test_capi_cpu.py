@@ -83,6 +83,7 @@ def test_wait_selftest_rejects_bad_arguments_without_cuda(L):
     assert L.lbm_selftest_wait_timeout(0, 0, ctypes.byref(r)) == lbm.LBM_E_INVAL
     assert L.lbm_selftest_wait_timeout(0, (1 << 20) + 1, ctypes.byref(r)) == lbm.LBM_E_INVAL
     assert L.lbm_selftest_wait_timeout(0, 10, None) == lbm.LBM_E_INVAL
+    assert L.lbm_selftest_grid_barrier_timeout(0, None) == lbm.LBM_E_INVAL
     assert r.value == -1
 
 

@@ -382,6 +382,16 @@ def test_auto_variant_choice():
     assert variant(1026, 64, want=lbm.VARIANT_STAGED) == lbm.VARIANT_REGISTER  # nx % 4 != 0
 
 
+def test_grid_barrier_reports_timeout_and_context_survives():
+    """The batch engine's grid barrier, with one CTA that never arrives, gives
+    up after its spin limit and reports LBM_E_TIMEOUT; the device stays usable."""
+    assert lbm.selftest_grid_barrier_timeout(0) == lbm.LBM_E_TIMEOUT
+    g = lbm.Lattice(32, 32, 0.85, precision=lbm.FP32)
+    g.init_density(np.full((32, 32), 0.2))
+    g.step(5, lbm.SC, 1.0)
+    assert np.all(np.isfinite(g.observe()[0]))
+
+
 def test_bounded_wait_reports_timeout_and_context_survives():
     """A device wait on an mbarrier nothing arrives on gives up after its poll
     limit and reports LBM_E_TIMEOUT (no fault, no hang); the device is usable
