@@ -260,7 +260,7 @@ def test_invalid_arguments():
 
 # --- full size: 8192 x 8192 spinodal decomposition, improved scheme -------------
 
-def _one_step_rho_at(rho0, RT, y, x, tau, sigma):
+def _one_step_rho_at(rho0, RT, y, x, tau, sigma, scheme=oracle.IMPROVED):
     """rho(x, t=1) from f(., 0) = f_eq(rho0, 0), by the oracle's own primitives
     on the 5x5 neighbourhood (psi radius 2 -> F radius 1 -> pull)."""
     ny, nx = rho0.shape
@@ -273,30 +273,44 @@ def _one_step_rho_at(rho0, RT, y, x, tau, sigma):
     for a in range(9):
         sy, sx = 2 - oracle.EY[a], 2 - oracle.EX[a]  # source cell x - e_a in the window
         fs = oracle.feq(win[sy, sx], 0.0, 0.0)
-        post = oracle.collide_cell(oracle.IMPROVED, tau, sigma, fs, Fx[sy, sx], Fy[sy, sx],
+        post = oracle.collide_cell(scheme, tau, sigma, fs, Fx[sy, sx], Fy[sy, sx],
                                    psi[sy, sx])
         total += post[a]
     return total
 
 
-def test_full_size_8192_sampled_against_oracle():
-    n, t, tau, sigma = 8192, 0.85, 0.8, 0.1
+@pytest.mark.parametrize("scheme,sigma", [(lbm.IMPROVED, 0.1), (lbm.SC, 0.0), (lbm.EDM, 0.0),
+                                          (lbm.MRT, 0.1)])
+def test_full_size_8192_sampled_against_oracle(scheme, sigma):
+    """The bench's lattice and kernel (8192^2, two columns per lane): the
+    density after one step at sampled cells -- corners, strip and band edges,
+    random cells -- against the oracle's step on each cell's neighbourhood."""
+    n, t, tau = 8192, 0.85, 0.8
+    rates = (0.8, 1.1, 1.3)
     rg, rl = maxwell(t)
     rho0 = inputs.spinodal(n, n, 0.5 * (rg + rl), amp=0.01, seed=3)
     gpu = lbm.Lattice(n, n, t, precision=lbm.FP32)
+    assert gpu.variant() == lbm.VARIANT_PAIR
+    gpu.set_mrt_rates(*rates)
     gpu.init_density(rho0)
     m0 = gpu.mass()
-    gpu.step(1, lbm.IMPROVED, tau, sigma)
+    gpu.step(1, scheme, tau, sigma)
     rho1, _, _ = gpu.observe()
     RT = th.temperature(t)
     rng = np.random.default_rng(8)
-    cells = [(0, 0), (0, n - 1), (n - 1, 0), (n - 1, n - 1), (4095, 31), (17, 32)]
+    cells = [(0, 0), (0, n - 1), (n - 1, 0), (n - 1, n - 1), (4095, 31), (17, 32), (100, 63),
+             (101, 64), (431, 127), (432, 128)]
     cells += [tuple(v) for v in rng.integers(0, n, (150, 2))]
-    for y, x in cells:
-        want = _one_step_rho_at(rho0, RT, y, x, tau, sigma)
-        assert rho1[y, x] == pytest.approx(want, rel=2e-6), (y, x)
-    gpu.step(9, lbm.IMPROVED, tau, sigma)
+    oracle.set_mrt_rates(*rates)
+    try:
+        for y, x in cells:
+            want = _one_step_rho_at(rho0, RT, y, x, tau, sigma, scheme)
+            assert rho1[y, x] == pytest.approx(want, rel=2e-6), (y, x)
+    finally:
+        oracle.set_mrt_rates(0.0, 0.0, 0.0)
+    gpu.step(9, scheme, tau, sigma)
     assert abs(gpu.mass() / m0 - 1) < 1e-9
+    gpu.close()
 
 
 @pytest.mark.parametrize("nx,ny", [(64, 40), (68, 37), (100, 33), (128, 65), (132, 8)])
