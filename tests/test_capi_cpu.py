@@ -111,7 +111,7 @@ def test_maxwell_rejects_supercritical(L):
 def test_batch_create_rejects_bad_arguments_without_cuda(L):
     good = dict(nx=8, ny=8, T_over_Tc=0.8, tau=1.0, sigma=0.0, scheme=0)
     for bad in (dict(nx=0), dict(ny=-1), dict(T_over_Tc=0.0), dict(tau=0.5), dict(scheme=9),
-                dict(sigma=float("nan"))):
+                dict(scheme=lbm.MRT), dict(sigma=float("nan"))):
         with pytest.raises(lbm.LbmError) as e:
             lbm.Batch([good, {**good, **bad}])
         assert e.value.status == lbm.LBM_E_INVAL
