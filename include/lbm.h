@@ -229,7 +229,7 @@ typedef struct {
   double T_over_Tc;  /* reduced temperature, > 0                             */
   double tau;        /* relaxation time, > 1/2                               */
   double sigma;      /* improved-scheme constant (read by scheme 2 only)     */
-  int scheme;        /* LBM_SCHEME_*                                         */
+  int scheme;        /* LBM_SCHEME_SC .. LBM_SCHEME_LADD (no MRT in batches)  */
 } lbm_instance;
 
 enum { LBM_BATCH_AUTO = 0, LBM_BATCH_WORKLIST = 1, LBM_BATCH_PERSISTENT = 2,
