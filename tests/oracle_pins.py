@@ -373,8 +373,9 @@ def pin_improved_flat_interface(lib, temps=(0.8, 0.9), steps=30000):
     coexistence densities follow the mechanical-stability solution (Eq. 26)
     at eps = 16 sigma (eps = -2(alpha + 24 G sigma)/beta, alpha = 0, beta = 3,
     G = -1): sigma = 0.0625 -> eps = 1, 0.125 -> eps = 2.  The theory keeps
-    terms to second order only; the paper reports "good agreement", read here
-    as rho_l within 0.1 % and rho_g within 2 % (measured: 1e-4 and 1.1 %)."""
+    terms to second order only and the paper compares the two only by eye,
+    read here as rho_l within 0.1 % and rho_g within 2 % (measured: 1e-4 and
+    1.1 %)."""
     fails = []
     for t in temps:
         eos = th.CarnahanStarling(th.temperature(t))
