@@ -92,8 +92,8 @@ def test_tau_dependence_sc_vs_improved(lib):
 
 
 def test_laplace_law_on_droplets(lib):
-    """Laplace's law (north star check (b)): relaxed droplets of four radii
-    (Eq. 24 start, 64 x 64, T = 0.8 Tc, improved scheme sigma = 0.1, tau = 1);
+    """Laplace's law on the circular droplets of Secs. III C and IV B: relaxed
+    droplets of four radii (Eq. 24 start, 64 x 64, T = 0.8 Tc, improved scheme sigma = 0.1, tau = 1);
     the pressure jump p_EOS(rho_in) - p_EOS(rho_out) is linear in 1/R, R the
     equivalent-area radius, with an intercept small against the jumps."""
     from paper_1204_4098_gb300 import inputs
