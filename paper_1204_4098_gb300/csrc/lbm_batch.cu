@@ -63,6 +63,9 @@ constexpr int kWorklistThreads = 128;
 #ifndef LBM_BATCH_PAIR_MIN_BLOCKS
 #define LBM_BATCH_PAIR_MIN_BLOCKS 4  // CTAs per SM of the two-column work list (128 registers)
 #endif
+#ifndef LBM_BATCH_ODD_MIN_BLOCKS
+#define LBM_BATCH_ODD_MIN_BLOCKS 6  // CTAs per SM of the one-column work list (80 registers)
+#endif
 constexpr int kPersistentThreads = 256;
 constexpr int kReduceCta = 256;
 
@@ -118,7 +121,8 @@ __device__ __forceinline__ void class_range(const int* counts, bool pair, int& a
 // One step of every active instance of one class; warp w takes items
 // w, w + W, ... of the class's range of the prefix table.
 template <bool kPair>
-__global__ void __launch_bounds__(kWorklistThreads, kPair ? LBM_BATCH_PAIR_MIN_BLOCKS : 5)
+__global__ void __launch_bounds__(kWorklistThreads,
+                                  kPair ? LBM_BATCH_PAIR_MIN_BLOCKS : LBM_BATCH_ODD_MIN_BLOCKS)
 batch_worklist_kernel(const BatchInst* __restrict__ inst, const int* __restrict__ active,
                       const int* __restrict__ prefix, const int* __restrict__ counts,
                       const float* src, float* dst, unsigned* inst_status) {
@@ -468,7 +472,7 @@ struct lbm_batch {
   std::vector<char> fresh;   // (re)initialised since the last window
   std::vector<int> active;
   int sm_count = 0;
-  int wl_grid = 0;
+  int wl_grid[2] = {0, 0};  // resident CTAs of each class's work-list kernel
   int pers_grid_max = 0;
   int coop_grid = 0;             // resident CTAs of the cooperative kernel (0: unsupported)
   unsigned* d_sync = nullptr;    // grid barrier: arrivals, generation, error
@@ -604,10 +608,10 @@ int class_grid(const lbm_batch* b, int mode, int cls) {
   if (b->class_items[cls] == 0) return 0;
   if (mode == LBM_BATCH_PERSISTENT) return b->pers_grid_max;
   const int need = (b->class_items[cls] + kWorklistThreads / 32 - 1) / (kWorklistThreads / 32);
-  if (need >= b->wl_grid) return b->wl_grid;
+  if (need >= b->wl_grid[cls]) return b->wl_grid[cls];
   int g = 1;
   while (g < need) g <<= 1;
-  return std::min(g, b->wl_grid);
+  return std::min(g, b->wl_grid[cls]);
 }
 
 lbm_status window_graph(lbm_batch* b, int mode, cudaGraphExec_t* out) {
@@ -719,6 +723,8 @@ size_t max_active_cells(const lbm_batch* b) {
   return m;
 }
 
+constexpr double kSkipped = 1e299;  // cost of a candidate left out of a tuning
+
 // Window-level autotuner: measure each candidate (mode, rows) on one live
 // window, keep the cheapest per cell update, and tune again once the active
 // work has halved or the chosen candidate's cost has risen.
@@ -733,8 +739,21 @@ void choose_config(lbm_batch* b, int& mode, int& rows) {
   // configuration has become 30 % dearer per cell update (instances leaving
   // change which band height balances the remaining items best)
   if (b->tuned && (cells * 2 < b->tuned_cells || b->last_cost > 1.3 * b->tuned_cost)) {
+    // every tuning window is a live window, but a slow candidate wastes part
+    // of it: one that was over 30 % dearer than the best last time is left
+    // out of this tuning (and timed again at the next one); the persistent
+    // candidate, which suits the small active sets of a sweep's end, always
+    // runs
     b->tuned = false;
-    std::fill(b->cand_cost.begin(), b->cand_cost.end(), -1.0);
+    double best = 1e300;
+    for (double c : b->cand_cost)
+      if (c >= 0 && c < best) best = c;
+    for (size_t k = 0; k < b->cand_cost.size(); ++k) {
+      const double c = b->cand_cost[k];
+      const bool slow = c >= 0 && c < kSkipped && c > 1.3 * best &&
+                        b->candidates[k].first != LBM_BATCH_PERSISTENT;
+      b->cand_cost[k] = slow ? kSkipped : -1.0;
+    }
   }
   if (!b->tuned) {
     for (size_t k = 0; k < b->candidates.size(); ++k) {
@@ -757,10 +776,20 @@ void choose_config(lbm_batch* b, int& mode, int& rows) {
     double best = 1e300;
     int bk = 0;
     for (size_t k = 0; k < b->candidates.size(); ++k)
-      if (b->cand_cost[k] >= 0 && b->cand_cost[k] < best) {
+      if (b->cand_cost[k] >= 0 && b->cand_cost[k] < std::min(best, kSkipped)) {
         best = b->cand_cost[k];
         bk = int(k);
       }
+    if (best >= kSkipped) {
+      // every candidate timed last time was left out: time them again
+      bool again = false;
+      for (double& c : b->cand_cost)
+        if (c == kSkipped) {
+          c = -1.0;
+          again = true;
+        }
+      if (again) return choose_config(b, mode, rows);
+    }
     b->cur_mode = b->candidates[bk].first;
     b->cur_rows = b->candidates[bk].second;
     b->tuned = true;
@@ -892,7 +921,7 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p[1], batch_persistent_kernel<false>,
                                                     kPersistentThreads, 0) != cudaSuccess)
     return bail(LBM_E_CUDA, "occupancy");
-  b->wl_grid = std::max(1, std::min(occ_wl[0], occ_wl[1])) * b->sm_count;
+  for (int c = 0; c < 2; ++c) b->wl_grid[c] = std::max(1, occ_wl[c]) * b->sm_count;
   b->pers_grid_max = std::max(1, std::min(occ_p[0], occ_p[1])) * b->sm_count;
   bool ok = true;
   ok &= cudaMalloc(&b->buf[0], off * sizeof(float)) == cudaSuccess;
