@@ -18,6 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbm_gb300.so")
+REPORT = os.path.join(BUILD, "ptxas_report.txt")  # -Xptxas -v output of the last build
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
@@ -55,6 +56,8 @@ def build_library(verbose: bool = False) -> str:
     if verbose:
         for _, log in results:
             sys.stderr.write(log)
+    with open(REPORT, "w") as f:  # registers / spills / shared memory per kernel
+        f.write("".join(log for _, log in results))
     objs = [o for o, _ in results]
     tmp = LIB + ".tmp"
     cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
