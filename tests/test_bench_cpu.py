@@ -27,3 +27,42 @@ def test_workload_config_names_the_workload():
     cfg = bench.workload_config(A)
     assert cfg["workload"].startswith("8192x8192 periodic D2Q9 spinodal decomposition")
     assert cfg["nx"] == cfg["ny"] == 8192 and "L2" in cfg["l2"]
+
+
+def _reference_lines(cmd):
+    import json
+    import subprocess
+    env = dict(os.environ, MASTER_ADDR="127.0.0.1")
+    r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return [json.loads(s) for s in r.stdout.splitlines() if s.startswith("{")]
+
+
+REF_ARGS = ["bench.py", "--impl", "reference", "--steps", "3", "--warmup", "3",
+            "--ref-side", "32"]
+
+
+def _check_reference_line(d, n_gpus):
+    assert d["impl"] == "reference" and d["n_gpus"] == n_gpus
+    assert d["unit"] == "MLUPS" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["steps"] == 3 and d["warmup"] == 3
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"].startswith("8192x8192 periodic D2Q9")
+
+
+def test_reference_arm_prints_one_line():
+    lines = _reference_lines([sys.executable, *REF_ARGS])
+    assert len(lines) == 1
+    _check_reference_line(lines[0], 1)
+
+
+def test_reference_arm_under_torchrun_two_ranks():
+    """Launched as for N = 2 (gloo on the host): rank 0 alone runs the oracle
+    and prints; the other rank exits 0 without work."""
+    lines = _reference_lines([sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+                              "--nproc-per-node", "2", "--master-addr", "127.0.0.1",
+                              "--master-port", "29531", *REF_ARGS, "--gpus", "2"])
+    assert len(lines) == 1
+    _check_reference_line(lines[0], 2)
