@@ -66,3 +66,35 @@ def test_reference_arm_under_torchrun_two_ranks():
                               "--master-port", "29531", *REF_ARGS, "--gpus", "2"])
     assert len(lines) == 1
     _check_reference_line(lines[0], 2)
+
+
+def _timing_worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE=str(world),
+                      RANK=str(rank), LOCAL_RANK=str(rank))
+    w, r, _ = bench.dist_setup()
+    bench.dist_barrier(w)
+    slowest = bench.dist_max(10.0 + r, w)  # each rank's own time
+    q.put((r, w, slowest))
+    import torch.distributed as dist
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_with_two_gloo_ranks():
+    """The multi-rank timing of the bench: each rank's time is reduced to the
+    slowest on the host (gloo), so rank 0 reports whole-job time."""
+    import multiprocessing as mp
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_timing_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert got == [(0, 2, 11.0), (1, 2, 11.0)]
