@@ -284,6 +284,9 @@ typedef struct {
 
 typedef struct lbm_batch lbm_batch;
 
+/* Fill *p with the defaults named above (a = 1, b = 4, R = 1, G = -1, exact
+ * Tc, window 1000, tol 1e-9, max_steps 200000, AUTO mode, COEX rule,
+ * conv_rel 8 * 2^-23, AUTO variant, device 0, own stream).  NULL is ignored. */
 void lbm_batch_default_params(lbm_batch_params *p);
 
 /* Allocate a batch of `count` instances.  LBM_E_INVAL for count < 1 or any
@@ -312,6 +315,9 @@ lbm_status lbm_batch_init_slabs(lbm_batch *b, const double *rho_g, const double 
  * number still active is written to *n_active (may be NULL). */
 lbm_status lbm_batch_run(lbm_batch *b, int max_windows, int *n_active);
 
+/* Copy instance i's result (status, steps, and the observables of its last
+ * window) to *r.  Host only (no device work); LBM_E_INVAL for a NULL argument
+ * or i outside [0, count). */
 lbm_status lbm_batch_get_result(const lbm_batch *b, int i, lbm_result *r);
 
 /* Density of instance i (FP64 host array of ny*nx). */
@@ -322,8 +328,17 @@ lbm_status lbm_batch_get_density(lbm_batch *b, int i, double *rho);
  * each may be NULL. */
 lbm_status lbm_batch_get_moments(lbm_batch *b, int i, double *rho, double *vx, double *vy);
 
+/* Copy the batch's counters (windows, launches, device time, the launch mode
+ * of the last window, instances still active) to *s.  Host only;
+ * LBM_E_INVAL for a NULL argument. */
 lbm_status lbm_batch_get_stats(const lbm_batch *b, lbm_batch_stats *s);
+
+/* Message of the batch's last failed call ("" for NULL or none); owned by
+ * the batch, valid until its next call. */
 const char *lbm_batch_last_error(const lbm_batch *b);
+
+/* Wait for the batch's stream, then free every device and pinned host
+ * buffer, graph, event and owned stream.  Accepts NULL. */
 lbm_status lbm_batch_destroy(lbm_batch *b);
 
 /* ---- warm-start network ------------------------------------------------- */
@@ -339,9 +354,20 @@ lbm_status lbm_batch_destroy(lbm_batch *b);
  */
 typedef struct lbm_mlp lbm_mlp;
 
+/* Number of FP32 parameters of the network (4675). */
 int lbm_mlp_num_params(void);
+
+/* Network on `device` with all parameters and Adam moments zero; it works on
+ * cuda_stream (NULL: it creates and owns a stream).  LBM_E_INVAL for a NULL
+ * out, LBM_E_CUDA for a bad device or stream failure, LBM_E_NOMEM when its
+ * device buffers cannot be allocated (nothing is left allocated then). */
 lbm_status lbm_mlp_create(int device, void *cuda_stream, lbm_mlp **out);
+
+/* Wait for the network's stream and free its buffers (and owned stream).
+ * Accepts NULL. */
 lbm_status lbm_mlp_destroy(lbm_mlp *m);
+
+/* Message of the network's last failed call ("" for NULL or none). */
 const char *lbm_mlp_last_error(const lbm_mlp *m);
 
 /* Set the parameters (and reset the Adam state) / read them back. */
