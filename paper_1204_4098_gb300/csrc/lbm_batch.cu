@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "lbm.h"
+#include "lbm_batch_host.h"
 #include "lbm_internal.h"
 #include "lbm_kernels.cuh"
 
@@ -484,15 +485,7 @@ struct lbm_batch {
   int class_items[2] = {0, 0};  // work-list items of the active instances per class
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool initialized = false;
-  // current launch configuration and autotuner state
-  int cur_mode = LBM_BATCH_WORKLIST;
-  int cur_rows = 32;
-  std::vector<std::pair<int, int>> candidates;
-  std::vector<double> cand_cost;  // ns per cell update, <0 = not measured
-  size_t tuned_cells = 0;
-  double tuned_cost = 0.0;  // cost per cell update of the chosen candidate
-  double last_cost = 0.0;   // of the last window
-  bool tuned = false;
+  WindowTuner tuner;  // launch configuration of LBM_BATCH_AUTO
   lbm_batch_stats stats{};
   std::string err;
 };
@@ -531,34 +524,6 @@ void set_geometry(BatchInst& d, int rows) {
   d.pn_bands = (d.ny + d.pband_rows - 1) / d.pband_rows;
 }
 
-// Longest-processing-time assignment of `ids` onto at most `grid` CTAs
-// (largest instance first onto the least-loaded CTA), written as CTA ranges
-// begin[0..grid] into list starting at pos.
-void lpt_assign(const lbm_batch* b, std::vector<int> ids, int grid, int* begin, int* list,
-                int& pos) {
-  const int G = std::max(1, std::min(int(ids.size()), grid));
-  std::sort(ids.begin(), ids.end(), [&](int x, int y) {
-    const size_t cx = size_t(b->desc[x].nx) * b->desc[x].ny;
-    const size_t cy = size_t(b->desc[y].nx) * b->desc[y].ny;
-    return cx != cy ? cx > cy : x < y;
-  });
-  using Load = std::pair<size_t, int>;
-  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-  for (int c = 0; c < G; ++c) heap.push({0, c});
-  std::vector<std::vector<int>> lists(G);
-  for (int i : ids) {
-    Load l = heap.top();
-    heap.pop();
-    lists[l.second].push_back(i);
-    heap.push({l.first + size_t(b->desc[i].nx) * b->desc[i].ny, l.second});
-  }
-  for (int c = 0; c <= grid; ++c) {
-    begin[c] = pos;
-    if (c < G && !ids.empty())
-      for (int i : lists[c]) list[pos++] = i;
-  }
-}
-
 // Rebuild the active list (two-column instances first), the work-list prefix
 // and the persistent assignment of each class.
 lbm_status upload_tables(lbm_batch* b) {
@@ -580,9 +545,11 @@ lbm_status upload_tables(lbm_batch* b) {
   b->h_prefix[b->count + 1] = int(cls[0].size());
   b->h_prefix[b->count + 2] = na;
   const int span = b->pers_grid_max + 1;
+  const auto inst_cells = [b](int i) { return size_t(b->desc[i].nx) * b->desc[i].ny; };
   int pos = 0;
   for (int c = 0; c < 2; ++c)
-    lpt_assign(b, cls[c], b->pers_grid_max, b->h_cta_begin + c * span, b->h_cta_list, pos);
+    lpt_assign(cls[c], inst_cells, b->pers_grid_max, b->h_cta_begin + c * span, b->h_cta_list,
+               pos);
   LBM_BCUDA(b, cudaMemcpyAsync(b->d_inst, b->desc.data(), b->count * sizeof(BatchInst),
                                cudaMemcpyHostToDevice, b->stream));
   LBM_BCUDA(b, cudaMemcpyAsync(b->d_active, b->h_active, std::max(na, 1) * sizeof(int),
@@ -599,21 +566,17 @@ lbm_status upload_tables(lbm_batch* b) {
   return LBM_OK;
 }
 
-// One window as a CUDA graph (captured once per mode; the kernels read the
-// active set and geometry from device memory, so the graph stays valid).
-// Grid of a class kernel for the current active set: enough CTAs for its
-// items (rounded up to a power of two, so few distinct graphs arise), at
-// most one full wave; 0 when the class has no active instance.
+// Grid of a class kernel for the current active set (worklist_grid for the
+// work list); 0 when the class has no active instance.
 int class_grid(const lbm_batch* b, int mode, int cls) {
   if (b->class_items[cls] == 0) return 0;
   if (mode == LBM_BATCH_PERSISTENT) return b->pers_grid_max;
-  const int need = (b->class_items[cls] + kWorklistThreads / 32 - 1) / (kWorklistThreads / 32);
-  if (need >= b->wl_grid[cls]) return b->wl_grid[cls];
-  int g = 1;
-  while (g < need) g <<= 1;
-  return std::min(g, b->wl_grid[cls]);
+  return worklist_grid(b->class_items[cls], kWorklistThreads / 32, b->wl_grid[cls]);
 }
 
+// One window as a CUDA graph, captured once per (mode, class grids) and
+// cached: the kernels read the active set and geometry from device memory,
+// so the graph stays valid as instances leave.
 lbm_status window_graph(lbm_batch* b, int mode, cudaGraphExec_t* out) {
   const bool coop = mode == LBM_BATCH_COOPERATIVE;
   const int g0 = coop ? b->coop_grid : class_grid(b, mode, 0);
@@ -723,11 +686,8 @@ size_t max_active_cells(const lbm_batch* b) {
   return m;
 }
 
-constexpr double kSkipped = 1e299;  // cost of a candidate left out of a tuning
-
-// Window-level autotuner: measure each candidate (mode, rows) on one live
-// window, keep the cheapest per cell update, and tune again once the active
-// work has halved or the chosen candidate's cost has risen.
+// Launch configuration of the next window: the requested one, or the
+// autotuner's (WindowTuner) under LBM_BATCH_AUTO.
 void choose_config(lbm_batch* b, int& mode, int& rows) {
   if (b->p.mode != LBM_BATCH_AUTO) {
     mode = b->p.mode;
@@ -735,78 +695,22 @@ void choose_config(lbm_batch* b, int& mode, int& rows) {
     return;
   }
   const size_t cells = active_cells(b);
-  // tune again once the active work has halved, or once the chosen
-  // configuration has become 30 % dearer per cell update (instances leaving
-  // change which band height balances the remaining items best)
-  if (b->tuned && (cells * 2 < b->tuned_cells || b->last_cost > 1.3 * b->tuned_cost)) {
-    // every tuning window is a live window, but a slow candidate wastes part
-    // of it: one that was over 30 % dearer than the best last time is left
-    // out of this tuning (and timed again at the next one); the persistent
-    // candidate, which suits the small active sets of a sweep's end, always
-    // runs
-    b->tuned = false;
-    double best = 1e300;
-    for (double c : b->cand_cost)
-      if (c >= 0 && c < best) best = c;
-    for (size_t k = 0; k < b->cand_cost.size(); ++k) {
-      const double c = b->cand_cost[k];
-      const bool slow = c >= 0 && c < kSkipped && c > 1.3 * best &&
-                        b->candidates[k].first != LBM_BATCH_PERSISTENT;
-      b->cand_cost[k] = slow ? kSkipped : -1.0;
-    }
-  }
-  if (!b->tuned) {
-    for (size_t k = 0; k < b->candidates.size(); ++k) {
-      if (b->cand_cost[k] >= 0) continue;
-      const auto& c = b->candidates[k];
-      if (b->p.rows_per_item > 0 && c.first == LBM_BATCH_WORKLIST &&
-          c.second != b->p.rows_per_item)
-        continue;
-      // a persistent window puts each instance on one SM: only worth trying
-      // when the active populations are within a few times the L2 size and
-      // no single instance is large
-      if (c.first == LBM_BATCH_PERSISTENT &&
-          (cells * 72 > size_t(512) << 20 || max_active_cells(b) > 65536))
-        continue;
-      if (c.first == LBM_BATCH_COOPERATIVE && b->coop_grid == 0) continue;
-      mode = c.first;
-      rows = c.second;
-      return;
-    }
-    double best = 1e300;
-    int bk = 0;
-    for (size_t k = 0; k < b->candidates.size(); ++k)
-      if (b->cand_cost[k] >= 0 && b->cand_cost[k] < std::min(best, kSkipped)) {
-        best = b->cand_cost[k];
-        bk = int(k);
-      }
-    if (best >= kSkipped) {
-      // every candidate timed last time was left out: time them again
-      bool again = false;
-      for (double& c : b->cand_cost)
-        if (c == kSkipped) {
-          c = -1.0;
-          again = true;
-        }
-      if (again) return choose_config(b, mode, rows);
-    }
-    b->cur_mode = b->candidates[bk].first;
-    b->cur_rows = b->candidates[bk].second;
-    b->tuned = true;
-    b->tuned_cells = cells;
-    b->tuned_cost = best;
-    b->last_cost = best;
-  }
-  mode = b->cur_mode;
-  rows = b->cur_rows;
-}
-
-void record_cost(lbm_batch* b, int mode, int rows, double ms, size_t cells) {
-  for (size_t k = 0; k < b->candidates.size(); ++k)
-    if (b->candidates[k].first == mode &&
-        (mode == LBM_BATCH_PERSISTENT || b->candidates[k].second == rows) &&
-        b->cand_cost[k] < 0)
-      b->cand_cost[k] = ms * 1e6 / (double(cells) * b->p.window);
+  const auto eligible = [&](size_t k) {
+    const auto& c = b->tuner.candidates[k];
+    if (b->p.rows_per_item > 0 && c.first == LBM_BATCH_WORKLIST &&
+        c.second != b->p.rows_per_item)
+      return false;
+    // a persistent window puts each instance on one SM: only worth trying
+    // when the active populations are within a few times the L2 size and no
+    // single instance is large
+    if (c.first == LBM_BATCH_PERSISTENT &&
+        (cells * 72 > size_t(512) << 20 || max_active_cells(b) > 65536))
+      return false;
+    return !(c.first == LBM_BATCH_COOPERATIVE && b->coop_grid == 0);
+  };
+  const auto choice = b->tuner.choose(cells, eligible);
+  mode = choice.first;
+  rows = choice.second;
 }
 
 }  // namespace
@@ -958,8 +862,8 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
       cudaMemsetAsync(b->buf[1], 0, off * sizeof(float), b->stream) != cudaSuccess ||
       cudaStreamSynchronize(b->stream) != cudaSuccess)
     return bail(LBM_E_CUDA, "memset");
-  for (int rows : {8, 16, 32, 64, 128}) b->candidates.push_back({LBM_BATCH_WORKLIST, rows});
-  b->candidates.push_back({LBM_BATCH_PERSISTENT, 0});
+  for (int rows : {8, 16, 32, 64, 128}) b->tuner.add(LBM_BATCH_WORKLIST, rows);
+  b->tuner.add(LBM_BATCH_PERSISTENT, 0);
   {
     // cooperative windows: every CTA resident, one launch per window
     int coop = 0, occ = 0;
@@ -971,9 +875,8 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
       b->coop_grid = occ * b->sm_count;
     cudaGetLastError();
     if (b->coop_grid > 0)
-      for (int rows : {16, 32, 64}) b->candidates.push_back({LBM_BATCH_COOPERATIVE, rows});
+      for (int rows : {16, 32, 64}) b->tuner.add(LBM_BATCH_COOPERATIVE, rows);
   }
-  b->cand_cost.assign(b->candidates.size(), -1.0);
   for (int i = 0; i < count; ++i) b->active.push_back(i);
   b->stats.n_active = count;
   *out = b;
@@ -1120,8 +1023,7 @@ lbm_status lbm_batch_run(lbm_batch* b, int max_windows, int* n_active) {
     if (st != LBM_OK && mode == LBM_BATCH_COOPERATIVE && b->p.mode == LBM_BATCH_AUTO) {
       // cooperative windows unavailable here: drop them and use the work list
       b->coop_grid = 0;
-      for (size_t k = 0; k < b->candidates.size(); ++k)
-        if (b->candidates[k].first == LBM_BATCH_COOPERATIVE) b->cand_cost[k] = 1e300;
+      b->tuner.disable(LBM_BATCH_COOPERATIVE);
       mode = LBM_BATCH_WORKLIST;
       st = window_graph(b, mode, &g);
     }
@@ -1157,9 +1059,8 @@ lbm_status lbm_batch_run(lbm_batch* b, int max_windows, int* n_active) {
     b->stats.windows += 1;
     b->stats.mode = mode;
     b->stats.rows_per_item = rows;
-    if (b->p.mode == LBM_BATCH_AUTO && !b->tuned) record_cost(b, mode, rows, ms, cells);
-    if (b->p.mode == LBM_BATCH_AUTO && b->tuned)
-      b->last_cost = ms * 1e6 / (double(cells) * b->p.window);
+    if (b->p.mode == LBM_BATCH_AUTO)
+      b->tuner.record(mode, rows, ms * 1e6 / (double(cells) * b->p.window));
     std::vector<int> still;
     const double floor32 = b->p.conv_rel;
     for (int i : b->active) {

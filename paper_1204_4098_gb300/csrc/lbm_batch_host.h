@@ -1,0 +1,151 @@
+// Host-side scheduling of the batch engine: the grid of a work-list class
+// kernel, the longest-processing-time assignment of whole instances to the
+// CTAs of a persistent window, and the window-level autotuner.  Plain C++
+// without CUDA, so that the CPU tests compile and exercise it on its own.
+#pragma once
+
+#include <algorithm>
+#include <cstddef>
+#include <functional>
+#include <queue>
+#include <utility>
+#include <vector>
+
+#include "lbm.h"
+
+namespace lbm {
+
+// CTAs of a work-list class kernel for `items` strip x band items: enough for
+// one item per warp, rounded up to a power of two (so that few distinct window
+// graphs arise), at most `max_grid` (one wave of resident CTAs); 0 when there
+// is no item.
+inline int worklist_grid(int items, int warps_per_cta, int max_grid) {
+  if (items <= 0) return 0;
+  const int need = (items + warps_per_cta - 1) / warps_per_cta;
+  if (need >= max_grid) return max_grid;
+  int g = 1;
+  while (g < need) g <<= 1;
+  return std::min(g, max_grid);
+}
+
+// Longest-processing-time assignment of `ids` onto at most `grid` CTAs: the
+// largest instance (cost(id), ties by id) first, each onto the least-loaded
+// CTA.  CTA c's instances are list[begin[c] .. begin[c + 1]), written from
+// position `pos` on (advanced); begin gets grid + 1 entries, and CTAs beyond
+// the number of instances get none.
+template <class Cost>
+void lpt_assign(std::vector<int> ids, const Cost& cost, int grid, int* begin, int* list,
+                int& pos) {
+  const int G = std::max(1, std::min(int(ids.size()), grid));
+  std::sort(ids.begin(), ids.end(), [&](int x, int y) {
+    const size_t cx = cost(x), cy = cost(y);
+    return cx != cy ? cx > cy : x < y;
+  });
+  using Load = std::pair<size_t, int>;
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+  for (int c = 0; c < G; ++c) heap.push({0, c});
+  std::vector<std::vector<int>> lists(G);
+  for (int i : ids) {
+    Load l = heap.top();
+    heap.pop();
+    lists[l.second].push_back(i);
+    heap.push({l.first + cost(i), l.second});
+  }
+  for (int c = 0; c <= grid; ++c) {
+    begin[c] = pos;
+    if (c < G && !ids.empty())
+      for (int i : lists[c]) list[pos++] = i;
+  }
+}
+
+// Window-level autotuner.  Each candidate (mode, rows) is timed on one live
+// window, the cheapest per cell update is kept, and tuning starts again once
+// the active work has halved or the chosen candidate has become 30 % dearer
+// per cell update (instances leaving change which band height balances the
+// remaining items best).  Every tuning window does live work, but a slow
+// candidate wastes part of it: one that was over 30 % dearer than the best at
+// the previous tuning is left out of the next one (and timed again at the one
+// after); the persistent candidate, which suits the small active sets of a
+// sweep's end, is always timed.
+struct WindowTuner {
+  static constexpr double kSkipped = 1e299;      // left out of this tuning
+  static constexpr double kUnavailable = 1e300;  // cannot run on this device
+
+  std::vector<std::pair<int, int>> candidates;  // (mode, rows per item)
+  std::vector<double> cost;  // per cell update; < 0: not timed in this tuning
+  bool tuned = false;
+  size_t tuned_cells = 0;   // active cells when the choice was made
+  double tuned_cost = 0.0;  // cost per cell update of the choice
+  double last_cost = 0.0;   // of the last window run with it
+  std::pair<int, int> cur{LBM_BATCH_WORKLIST, 32};
+
+  void add(int mode, int rows) {
+    candidates.push_back({mode, rows});
+    cost.push_back(-1.0);
+  }
+
+  // (mode, rows) for the next window over `cells` active cells;
+  // eligible(k) says whether candidate k may run now.
+  std::pair<int, int> choose(size_t cells, const std::function<bool(size_t)>& eligible) {
+    if (tuned && (cells * 2 < tuned_cells || last_cost > 1.3 * tuned_cost)) {
+      tuned = false;
+      double best = 1e300;
+      for (double c : cost)
+        if (c >= 0 && c < best) best = c;
+      for (size_t k = 0; k < cost.size(); ++k) {
+        const double c = cost[k];
+        const bool slow = c >= 0 && c < kSkipped && c > 1.3 * best &&
+                          candidates[k].first != LBM_BATCH_PERSISTENT;
+        cost[k] = slow ? kSkipped : -1.0;
+      }
+    }
+    if (!tuned) {
+      for (size_t k = 0; k < candidates.size(); ++k)
+        if (cost[k] < 0 && eligible(k)) return candidates[k];  // time it next
+      double best = 1e300;
+      size_t bk = 0;
+      for (size_t k = 0; k < candidates.size(); ++k)
+        if (cost[k] >= 0 && cost[k] < std::min(best, kSkipped)) {
+          best = cost[k];
+          bk = k;
+        }
+      if (best >= kSkipped) {
+        // every candidate timed last time was left out: time them again
+        bool again = false;
+        for (double& c : cost)
+          if (c == kSkipped) {
+            c = -1.0;
+            again = true;
+          }
+        if (again) return choose(cells, eligible);
+      }
+      cur = candidates[bk];
+      tuned = true;
+      tuned_cells = cells;
+      tuned_cost = best;
+      last_cost = best;
+    }
+    return cur;
+  }
+
+  // The window just run with (mode, rows) cost `c` per cell update; the
+  // persistent candidate has no band height.
+  void record(int mode, int rows, double c) {
+    if (tuned) {
+      last_cost = c;
+      return;
+    }
+    for (size_t k = 0; k < candidates.size(); ++k)
+      if (candidates[k].first == mode &&
+          (mode == LBM_BATCH_PERSISTENT || candidates[k].second == rows) && cost[k] < 0)
+        cost[k] = c;
+  }
+
+  // Candidates of `mode` cannot run here (e.g. a cooperative launch failed).
+  void disable(int mode) {
+    for (size_t k = 0; k < candidates.size(); ++k)
+      if (candidates[k].first == mode) cost[k] = kUnavailable;
+  }
+};
+
+}  // namespace lbm

@@ -1,0 +1,221 @@
+"""The batch engine's host scheduling without a GPU: the grid of a work-list
+class kernel, the longest-processing-time assignment of instances to the CTAs
+of a persistent window, and the window-level autotuner
+(paper_1204_4098_gb300/csrc/lbm_batch_host.h, compiled here with the host C++
+compiler through tests/batch_host_shim.cpp)."""
+import ctypes
+import heapq
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1204_4098_gb300", "csrc")
+WL, PERS, COOP = 1, 2, 3  # LBM_BATCH_WORKLIST, _PERSISTENT, _COOPERATIVE
+
+
+@pytest.fixture(scope="module")
+def S(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    out = str(tmp_path_factory.mktemp("shim") / "libbatchhost.so")
+    subprocess.run([cxx, "-std=c++17", "-O1", "-shared", "-fPIC",
+                    "-I", os.path.join(ROOT, "include"), "-I", CSRC,
+                    os.path.join(ROOT, "tests", "batch_host_shim.cpp"), "-o", out],
+                   check=True, capture_output=True, text=True)
+    lib = ctypes.CDLL(out)
+    lib.shim_tuner_new.restype = ctypes.c_void_p
+    lib.shim_tuner_free.argtypes = [ctypes.c_void_p]
+    lib.shim_tuner_add.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+    lib.shim_tuner_choose.argtypes = [ctypes.c_void_p, ctypes.c_ulonglong,
+                                      ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.shim_tuner_record.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double]
+    lib.shim_tuner_disable.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.shim_tuner_tuned.argtypes = [ctypes.c_void_p]
+    lib.shim_lpt.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int,
+                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    return lib
+
+
+# --- work-list grid -----------------------------------------------------------
+
+@pytest.mark.parametrize("items,want", [(0, 0), (1, 1), (4, 1), (5, 2), (9, 4), (17, 8),
+                                        (2000, 512), (2400, 608), (2432, 608), (10 ** 6, 608)])
+def test_worklist_grid(S, items, want):
+    # 4 warps per CTA, 608 resident CTAs: one item per warp, rounded up to a
+    # power of two, at most one wave
+    assert S.shim_worklist_grid(items, 4, 608) == want
+
+
+# --- longest-processing-time assignment ------------------------------------------
+
+def lpt_reference(cells, grid):
+    """The same greedy in Python: largest first (ties by id), each onto the
+    least-loaded CTA (ties by CTA index)."""
+    n = len(cells)
+    G = max(1, min(n, grid))
+    order = sorted(range(n), key=lambda i: (-cells[i], i))
+    heap = [(0, c) for c in range(G)]
+    lists = [[] for _ in range(G)]
+    for i in order:
+        load, c = heapq.heappop(heap)
+        lists[c].append(i)
+        heapq.heappush(heap, (load + cells[i], c))
+    return lists
+
+
+def run_lpt(S, cells, grid):
+    n = len(cells)
+    arr = (ctypes.c_longlong * max(n, 1))(*cells)
+    begin = (ctypes.c_int * (grid + 1))()
+    lst = (ctypes.c_int * max(n, 1))()
+    pos = S.shim_lpt(n, arr, grid, begin, lst)
+    return pos, list(begin), list(lst)[:n]
+
+
+@pytest.mark.parametrize("n,grid,seed", [(37, 8, 1), (512, 304, 2), (3, 8, 3), (1, 1, 4),
+                                         (0, 5, 5), (100, 1, 6)])
+def test_lpt_assignment(S, n, grid, seed):
+    cells = [int(c) for c in np.random.default_rng(seed).integers(32 * 128, 512 * 512, n)]
+    pos, begin, lst = run_lpt(S, cells, grid)
+    assert pos == n and begin[0] == 0 and begin[grid] == n
+    assert all(begin[c] <= begin[c + 1] for c in range(grid))
+    assert sorted(lst) == list(range(n))  # every instance exactly once
+    got = [lst[begin[c]:begin[c + 1]] for c in range(grid)]
+    want = lpt_reference(cells, grid)
+    assert got[:len(want)] == want and all(not g for g in got[len(want):])
+    if n:
+        # Graham's bound for the greedy: makespan <= 4/3 of the optimum, and
+        # the optimum is at least the largest instance and the mean load
+        loads = [sum(cells[i] for i in g) for g in got]
+        bound = max(max(cells), sum(cells) / min(grid, n))
+        assert max(loads) <= 4.0 / 3.0 * bound + 1e-9
+
+
+# --- window-level autotuner --------------------------------------------------------
+
+CANDS = [(WL, 8), (WL, 16), (WL, 32), (WL, 64), (WL, 128), (PERS, 0),
+         (COOP, 16), (COOP, 32), (COOP, 64)]
+
+
+class Tuner:
+    def __init__(self, S, cands=CANDS):
+        self.S, self.cands = S, cands
+        self.h = S.shim_tuner_new()
+        for m, r in cands:
+            S.shim_tuner_add(self.h, m, r)
+
+    def choose(self, cells, eligible=None):
+        elig = [1 if eligible is None or eligible(c) else 0 for c in self.cands]
+        e = (ctypes.c_int * len(elig))(*elig)
+        m, r = ctypes.c_int(), ctypes.c_int()
+        self.S.shim_tuner_choose(self.h, cells, e, ctypes.byref(m), ctypes.byref(r))
+        return m.value, r.value
+
+    def record(self, cand, cost):
+        self.S.shim_tuner_record(self.h, cand[0], cand[1], cost)
+
+    @property
+    def tuned(self):
+        return bool(self.S.shim_tuner_tuned(self.h))
+
+    def run(self, cells, costs, windows, eligible=None):
+        """`windows` windows: choose, then record the candidate's cost."""
+        seen = []
+        for _ in range(windows):
+            c = self.choose(cells, eligible)
+            seen.append(c)
+            self.record(c, costs[c])
+        return seen
+
+    def __del__(self):
+        self.S.shim_tuner_free(self.h)
+
+
+COSTS = {(WL, 8): 1.5, (WL, 16): 1.1, (WL, 32): 1.0, (WL, 64): 1.2, (WL, 128): 1.35,
+         (PERS, 0): 3.0, (COOP, 16): 1.25, (COOP, 32): 1.4, (COOP, 64): 1.6}
+
+
+def no_pers(c):
+    return c[0] != PERS
+
+
+def test_first_tuning_times_each_eligible_candidate_then_keeps_the_cheapest(S):
+    t = Tuner(S)
+    seen = t.run(1000, COSTS, 12, no_pers)
+    explored = [c for c in CANDS if c[0] != PERS]
+    assert seen[:len(explored)] == explored  # in order, the ineligible one left out
+    assert t.tuned and set(seen[len(explored):]) == {(WL, 32)}
+
+
+def test_retune_after_halving_skips_candidates_over_30_percent_dearer(S):
+    t = Tuner(S)
+    t.run(1000, COSTS, 9, no_pers)  # 8 timing windows, then the choice
+    assert t.tuned
+    # half the work left: tune again; WL 8 / 128 and COOP 32 / 64 were over
+    # 1.3x the best, so only WL 16, 32, 64 and COOP 16 are timed
+    seen = t.run(400, COSTS, 6, no_pers)
+    assert seen[:4] == [(WL, 16), (WL, 32), (WL, 64), (COOP, 16)]
+    assert seen[4:] == [(WL, 32), (WL, 32)]
+    # at the next tuning the left-out ones are timed again, and so are the
+    # four of this tuning, all within 30 % of the best
+    seen = t.run(150, COSTS, 10, no_pers)
+    assert seen[:8] == [c for c in CANDS if c[0] != PERS]
+    assert seen[8:] == [(WL, 32), (WL, 32)]
+
+
+def test_a_candidate_slow_in_one_tuning_sits_out_only_the_next(S):
+    costs = dict(COSTS)
+    t = Tuner(S)
+    t.run(1000, costs, 9, no_pers)
+    costs[(WL, 16)] = 1.4  # WL 16 turns slow during the second tuning
+    seen = t.run(400, costs, 5, no_pers)
+    assert seen == [(WL, 16), (WL, 32), (WL, 64), (COOP, 16), (WL, 32)]
+    seen = t.run(150, costs, 8, no_pers)
+    assert seen == [(WL, 8), (WL, 32), (WL, 64), (WL, 128), (COOP, 16), (COOP, 32),
+                    (COOP, 64), (WL, 32)]
+
+
+def test_persistent_candidate_is_always_timed_again(S):
+    t = Tuner(S)
+    t.run(1000, COSTS, 10)  # everything eligible (9 timing windows); PERS at 3x the best
+    assert t.tuned
+    seen = t.run(400, COSTS, 6)
+    assert (PERS, 0) in seen[:5]
+
+
+def test_retune_when_the_choice_becomes_30_percent_dearer(S):
+    t = Tuner(S)
+    t.run(1000, COSTS, 8, no_pers)
+    c = t.choose(1000, no_pers)
+    assert c == (WL, 32) and t.tuned
+    t.record(c, 1.29)  # within 30 %: keep it
+    assert t.choose(1000, no_pers) == (WL, 32) and t.tuned
+    t.record((WL, 32), 1.31)  # over 30 %: the next window starts a tuning
+    assert t.choose(1000, no_pers) == (WL, 16) and not t.tuned
+
+
+def test_all_candidates_left_out_are_timed_again(S):
+    cands = [(WL, 32), (WL, 64)]
+    costs = {(WL, 32): 1.0, (WL, 64): 2.0}
+    t = Tuner(S, cands)
+    t.run(1000, costs, 3)
+    assert t.tuned
+    # tuning again with WL 32 no longer eligible and WL 64 left out as slow:
+    # rather than choose nothing, WL 64 is timed
+    assert t.choose(100, lambda c: c != (WL, 32)) == (WL, 64)
+
+
+def test_disabled_mode_is_never_chosen(S):
+    t = Tuner(S)
+    t.S.shim_tuner_disable(t.h, COOP)
+    cheap = dict(COSTS)
+    cheap.update({(COOP, 16): 0.1, (COOP, 32): 0.1, (COOP, 64): 0.1})
+    seen = t.run(1000, cheap, 10, lambda c: c[0] == WL)
+    assert all(c[0] == WL for c in seen) and t.tuned
