@@ -11,6 +11,7 @@
 #include <string>
 
 #include "lbm.h"
+#include "lbm_geometry.h"
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -225,37 +226,15 @@ StripLaunch base_launch(lbm_ctx* c) {
   return L;
 }
 
-// Kernel variant for this lattice: the two-columns-per-lane kernel for direct
-// storage with even nx (AUTO), the bulk-copy staged kernel when asked for
-// (FP32 steps, nx % 4 == 0 so rows are 16-byte aligned, nx >= 64), else one
-// column per lane.
-// Shortest band of the automatic geometry: one wave of warps, but no band
-// under 4 rows (each band reloads the two rows around it).
-constexpr int kMinBandRows = 4;
-
+// Kernel variant of this context for a step (or an observe) launch
+// (resolve_variant).
 int pick_variant(const lbm_ctx* c, int mode) {
-  // AUTO keeps one column per lane on lattices too small to give the
-  // two-column kernel's 64-column strips (4-row bands) a quarter of the
-  // resident warps: there twice the strips beat the cheaper cells (measured:
-  // 256^2 1.33x faster with one column per lane, 512^2 equal, 768^2 and up
-  // faster with two).
-  const long long pair_items =
-      (long long)((c->p.nx + 63) / 64) * ((c->p.ny + kMinBandRows - 1) / kMinBandRows);
-  const bool small = pair_items * 4 < (long long)c->sm_count * 20;
-  const bool pair_ok = c->p.nx % 2 == 0;
-  const bool staged_ok = mode == kStepMode && c->p.precision == LBM_FP32 && c->p.nx >= 64 &&
-                         c->p.nx % 4 == 0;
-  if (c->variant == LBM_VARIANT_STAGED && staged_ok) return LBM_VARIANT_STAGED;
-  // AUTO takes PAIR except in FP64, where its doubled register state spills
-  if (((c->variant == LBM_VARIANT_AUTO && c->p.precision != LBM_FP64 && !small) ||
-       c->variant == LBM_VARIANT_PAIR) && pair_ok)
-    return LBM_VARIANT_PAIR;
-  return LBM_VARIANT_REGISTER;
+  return resolve_variant(c->variant, c->p.precision, c->p.nx, c->p.ny, c->sm_count,
+                         mode == kStepMode);
 }
 
-// Warp-strip geometry: strips of 32 columns (64 for PAIR), and as many row bands as fill
-// the resident warp slots once (one wave: every warp of a band runs at the
-// same time as its neighbours), at least kMinBandRows rows each.
+// Warp-strip geometry of one wave (strip_geometry) over the resident warp
+// slots of the variant's kernel.
 lbm_status geometry(lbm_ctx* c, int scheme, int mode, StripLaunch& L, int& grid) {
   int bps = 0;
   const int variant = pick_variant(c, mode);
@@ -268,24 +247,12 @@ lbm_status geometry(lbm_ctx* c, int scheme, int mode, StripLaunch& L, int& grid)
   if (bps < 1) bps = 1;
   const int warps_per_cta = kStripCtaThreads / 32;
   const long long resident = (long long)c->sm_count * bps * warps_per_cta;
-  const int strip_w = variant == LBM_VARIANT_PAIR ? 64 : 32;
-  const int n_strips = (c->p.nx + strip_w - 1) / strip_w;
-  const int ny = c->p.ny;
-  int band_rows;
-  if (c->band_rows_override > 0) {
-    band_rows = std::min(c->band_rows_override, ny);
-  } else {
-    long long n_bands = std::max<long long>(1, resident / n_strips);
-    const int min_rows = kMinBandRows;
-    n_bands = std::min<long long>(n_bands, std::max(1, ny / min_rows));
-    band_rows = int((ny + n_bands - 1) / n_bands);
-  }
-  const int n_bands = (ny + band_rows - 1) / band_rows;
-  L.n_strips = n_strips;
-  L.band_rows = band_rows;
-  L.n_bands = n_bands;
-  const long long warps = (long long)n_strips * n_bands;
-  grid = int((warps + warps_per_cta - 1) / warps_per_cta);
+  const StripGeometry g = strip_geometry(c->p.nx, c->p.ny, variant, resident, warps_per_cta,
+                                         c->band_rows_override);
+  L.n_strips = g.n_strips;
+  L.band_rows = g.band_rows;
+  L.n_bands = g.n_bands;
+  grid = g.grid;
   return LBM_OK;
 }
 

@@ -1,7 +1,9 @@
-// C entry points over the batch engine's host scheduling (lbm_batch_host.h),
-// compiled by tests/test_batch_host.py with the host C++ compiler (no CUDA) and
-// driven through ctypes.
+// C entry points over the host-side rules of the library, compiled by the
+// CPU tests with the host C++ compiler (no CUDA) and driven through ctypes:
+// the batch engine's scheduling (lbm_batch_host.h) and the single-lattice
+// launch rules (lbm_geometry.h).
 #include "lbm_batch_host.h"
+#include "lbm_geometry.h"
 
 extern "C" {
 
@@ -40,5 +42,22 @@ void shim_tuner_disable(void* t, int mode) {
   static_cast<lbm::WindowTuner*>(t)->disable(mode);
 }
 int shim_tuner_tuned(void* t) { return static_cast<lbm::WindowTuner*>(t)->tuned ? 1 : 0; }
+
+int shim_resolve_variant(int requested, int precision, int nx, int ny, int sm_count, int step) {
+  return lbm::resolve_variant(requested, precision, nx, ny, sm_count, step != 0);
+}
+
+// out = {n_strips, band_rows, n_bands, grid}
+void shim_strip_geometry(int nx, int ny, int variant, long long resident_warps,
+                         int warps_per_cta, int band_rows_override, int* out) {
+  const lbm::StripGeometry g =
+      lbm::strip_geometry(nx, ny, variant, resident_warps, warps_per_cta, band_rows_override);
+  out[0] = g.n_strips;
+  out[1] = g.band_rows;
+  out[2] = g.n_bands;
+  out[3] = g.grid;
+}
+
+int shim_min_band_rows() { return lbm::kMinBandRows; }
 
 }  // extern "C"

@@ -2,45 +2,19 @@
 class kernel, the longest-processing-time assignment of instances to the CTAs
 of a persistent window, and the window-level autotuner
 (paper_1204_4098_gb300/csrc/lbm_batch_host.h, compiled here with the host C++
-compiler through tests/batch_host_shim.cpp)."""
+compiler through tests/host_shim.cpp)."""
 import ctypes
 import heapq
-import os
-import shutil
-import subprocess
 
 import numpy as np
 import pytest
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-CSRC = os.path.join(ROOT, "paper_1204_4098_gb300", "csrc")
 WL, PERS, COOP = 1, 2, 3  # LBM_BATCH_WORKLIST, _PERSISTENT, _COOPERATIVE
 
 
 @pytest.fixture(scope="module")
-def S(tmp_path_factory):
-    cxx = shutil.which("g++") or shutil.which("c++")
-    if cxx is None:
-        pytest.skip("no host C++ compiler")
-    out = str(tmp_path_factory.mktemp("shim") / "libbatchhost.so")
-    subprocess.run([cxx, "-std=c++17", "-O1", "-shared", "-fPIC",
-                    "-I", os.path.join(ROOT, "include"), "-I", CSRC,
-                    os.path.join(ROOT, "tests", "batch_host_shim.cpp"), "-o", out],
-                   check=True, capture_output=True, text=True)
-    lib = ctypes.CDLL(out)
-    lib.shim_tuner_new.restype = ctypes.c_void_p
-    lib.shim_tuner_free.argtypes = [ctypes.c_void_p]
-    lib.shim_tuner_add.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
-    lib.shim_tuner_choose.argtypes = [ctypes.c_void_p, ctypes.c_ulonglong,
-                                      ctypes.POINTER(ctypes.c_int),
-                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
-    lib.shim_tuner_record.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
-                                      ctypes.c_double]
-    lib.shim_tuner_disable.argtypes = [ctypes.c_void_p, ctypes.c_int]
-    lib.shim_tuner_tuned.argtypes = [ctypes.c_void_p]
-    lib.shim_lpt.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int,
-                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
-    return lib
+def S(host_shim):
+    return host_shim
 
 
 # --- work-list grid -----------------------------------------------------------
