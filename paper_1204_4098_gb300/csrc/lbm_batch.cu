@@ -1062,35 +1062,23 @@ lbm_status lbm_batch_run(lbm_batch* b, int max_windows, int* n_active) {
     if (b->p.mode == LBM_BATCH_AUTO)
       b->tuner.record(mode, rows, ms * 1e6 / (double(cells) * b->p.window));
     std::vector<int> still;
-    const double floor32 = b->p.conv_rel;
+    const ConvRule rule{b->p.conv, b->p.tol, b->p.conv_rel, b->p.window, b->p.max_steps};
     for (int i : b->active) {
-      lbm_result& r = b->res[i];
       const BatchOut& o = b->h_out[i];
+      WindowObs obs;
+      obs.rho_g = o.rho_g;
+      obs.rho_l = o.rho_l;
+      obs.width = o.width;
+      obs.mass = o.mass;
+      obs.max_abs = o.max_abs;
+      obs.max_dev = o.max_dev;
+      obs.finite = o.finite != 0;
+      obs.diverged = (b->h_status[i] & kStatusDivergedFlag) != 0;
       const bool first = b->fresh[i] != 0;
       b->fresh[i] = 0;
-      const bool coex_calm =
-          !first && std::fabs(o.rho_g - r.rho_g) < std::max(b->p.tol, floor32 * std::fabs(o.rho_g)) &&
-          std::fabs(o.rho_l - r.rho_l) < std::max(b->p.tol, floor32 * std::fabs(o.rho_l));
-      b->calm[i] = coex_calm ? b->calm[i] + 1 : 0;
-      r.steps += b->p.window;
-      r.rho_g = o.rho_g;
-      r.rho_l = o.rho_l;
-      r.width = o.width;
-      r.mass = o.mass;
-      r.max_drho = o.max_abs;
-      const bool converged =
-          b->p.conv == LBM_CONV_CELL ? o.max_dev < 1.0f
-                                     : (b->p.conv == LBM_CONV_COEX && b->calm[i] >= 2);
-      if ((b->h_status[i] & kStatusDivergedFlag) || !o.finite) {
-        r.status = LBM_RUN_DIVERGED;
-      } else if (converged) {
-        r.status = LBM_RUN_CONVERGED;
-      } else if (r.steps >= b->p.max_steps) {
-        r.status = LBM_RUN_CAPPED;
-      } else {
-        r.status = LBM_RUN_ACTIVE;
-        still.push_back(i);
-      }
+      lbm_result& r = b->res[i];
+      r.status = window_verdict(rule, obs, first, b->calm[i], r);
+      if (r.status == LBM_RUN_ACTIVE) still.push_back(i);
     }
     b->active.swap(still);
     b->stats.n_active = int(b->active.size());

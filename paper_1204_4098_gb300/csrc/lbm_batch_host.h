@@ -1,10 +1,12 @@
-// Host-side scheduling of the batch engine: the grid of a work-list class
-// kernel, the longest-processing-time assignment of whole instances to the
-// CTAs of a persistent window, and the window-level autotuner.  Plain C++
-// without CUDA, so that the CPU tests compile and exercise it on its own.
+// Host-side logic of the batch engine: the grid of a work-list class kernel,
+// the longest-processing-time assignment of whole instances to the CTAs of a
+// persistent window, the window-level autotuner, and the convergence rule
+// applied after each window.  Plain C++ without CUDA, so that the CPU tests
+// compile and exercise it on its own.
 #pragma once
 
 #include <algorithm>
+#include <cmath>
 #include <cstddef>
 #include <functional>
 #include <queue>
@@ -147,5 +149,52 @@ struct WindowTuner {
       if (candidates[k].first == mode) cost[k] = kUnavailable;
   }
 };
+
+// One window's observables of an instance, as the window reduction reports
+// them (FP64 row means; the largest density change since the previous window,
+// absolute and relative to max(tol, 8 eps rho)).
+struct WindowObs {
+  double rho_g, rho_l, width, mass;
+  double max_abs;  // largest |rho(t) - rho(t - window)|
+  float max_dev;   // largest |drho| / max(tol, 8 * 2^-23 * rho)
+  bool finite;     // every density finite
+  bool diverged;   // the device status flagged divergence
+};
+
+struct ConvRule {
+  int conv;         // LBM_CONV_COEX, _CELL or _NONE
+  double tol;       // density-change tolerance per window
+  double conv_rel;  // COEX: relative floor
+  int window;       // steps per window
+  int max_steps;    // step cap
+};
+
+// Apply one window to an instance's result: steps and observables are
+// updated, `calm` counts consecutive windows whose coexistence densities each
+// changed by less than max(tol, conv_rel * value) (never the first window
+// after a (re)start), and the new status is returned: DIVERGED (device flag or
+// a non-finite density) before CONVERGED (CELL: every cell within its
+// tolerance; COEX: two calm windows in a row; NONE: never) before CAPPED
+// (step cap reached) before ACTIVE.
+inline int window_verdict(const ConvRule& rule, const WindowObs& o, bool first, int& calm,
+                          lbm_result& r) {
+  const bool coex_calm =
+      !first &&
+      std::fabs(o.rho_g - r.rho_g) < std::max(rule.tol, rule.conv_rel * std::fabs(o.rho_g)) &&
+      std::fabs(o.rho_l - r.rho_l) < std::max(rule.tol, rule.conv_rel * std::fabs(o.rho_l));
+  calm = coex_calm ? calm + 1 : 0;
+  r.steps += rule.window;
+  r.rho_g = o.rho_g;
+  r.rho_l = o.rho_l;
+  r.width = o.width;
+  r.mass = o.mass;
+  r.max_drho = o.max_abs;
+  const bool converged = rule.conv == LBM_CONV_CELL ? o.max_dev < 1.0f
+                                                    : (rule.conv == LBM_CONV_COEX && calm >= 2);
+  if (o.diverged || !o.finite) return LBM_RUN_DIVERGED;
+  if (converged) return LBM_RUN_CONVERGED;
+  if (r.steps >= rule.max_steps) return LBM_RUN_CAPPED;
+  return LBM_RUN_ACTIVE;
+}
 
 }  // namespace lbm

@@ -41,5 +41,8 @@ def host_shim(tmp_path_factory):
     lib.shim_tuner_tuned.argtypes = [P]
     lib.shim_lpt.argtypes = [I, ctypes.POINTER(ctypes.c_longlong), I, IP, IP]
     lib.shim_resolve_variant.argtypes = [I, I, I, I, I, I]
+    D = ctypes.c_double
+    lib.shim_window_verdict.argtypes = [I, D, D, I, I, ctypes.POINTER(D), I, I, I, IP,
+                                        ctypes.c_void_p]
     lib.shim_strip_geometry.argtypes = [I, I, I, ctypes.c_longlong, I, I, IP]
     return lib

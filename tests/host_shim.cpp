@@ -43,6 +43,24 @@ void shim_tuner_disable(void* t, int mode) {
 }
 int shim_tuner_tuned(void* t) { return static_cast<lbm::WindowTuner*>(t)->tuned ? 1 : 0; }
 
+// One window of the convergence rule: obs = {rho_g, rho_l, width, mass,
+// max_abs, max_dev}; r is updated in place; returns the status.
+int shim_window_verdict(int conv, double tol, double conv_rel, int window, int max_steps,
+                        const double* obs, int finite, int diverged, int first, int* calm,
+                        lbm_result* r) {
+  lbm::WindowObs o;
+  o.rho_g = obs[0];
+  o.rho_l = obs[1];
+  o.width = obs[2];
+  o.mass = obs[3];
+  o.max_abs = obs[4];
+  o.max_dev = float(obs[5]);
+  o.finite = finite != 0;
+  o.diverged = diverged != 0;
+  const lbm::ConvRule rule{conv, tol, conv_rel, window, max_steps};
+  return lbm::window_verdict(rule, o, first != 0, *calm, *r);
+}
+
 int shim_resolve_variant(int requested, int precision, int nx, int ny, int sm_count, int step) {
   return lbm::resolve_variant(requested, precision, nx, ny, sm_count, step != 0);
 }

@@ -1,13 +1,15 @@
-"""The batch engine's host scheduling without a GPU: the grid of a work-list
-class kernel, the longest-processing-time assignment of instances to the CTAs
-of a persistent window, and the window-level autotuner
-(paper_1204_4098_gb300/csrc/lbm_batch_host.h, compiled here with the host C++
-compiler through tests/host_shim.cpp)."""
+"""The batch engine's host logic without a GPU: the grid of a work-list class
+kernel, the longest-processing-time assignment of instances to the CTAs of a
+persistent window, the window-level autotuner and the convergence rule applied
+after each window (paper_1204_4098_gb300/csrc/lbm_batch_host.h, compiled here
+with the host C++ compiler through tests/host_shim.cpp)."""
 import ctypes
 import heapq
 
 import numpy as np
 import pytest
+
+from paper_1204_4098_gb300 import lbm
 
 WL, PERS, COOP = 1, 2, 3  # LBM_BATCH_WORKLIST, _PERSISTENT, _COOPERATIVE
 
@@ -193,3 +195,79 @@ def test_disabled_mode_is_never_chosen(S):
     cheap.update({(COOP, 16): 0.1, (COOP, 32): 0.1, (COOP, 64): 0.1})
     seen = t.run(1000, cheap, 10, lambda c: c[0] == WL)
     assert all(c[0] == WL for c in seen) and t.tuned
+
+
+# --- convergence rule after each window --------------------------------------------
+EPS8 = 8 * 2.0 ** -23  # the default relative floor
+
+
+class Instance:
+    """One instance's result and calm counter across windows."""
+
+    def __init__(self, S, conv=lbm.CONV_COEX, tol=1e-9, conv_rel=EPS8, window=1000,
+                 max_steps=200000):
+        self.S, self.rule = S, (conv, tol, conv_rel, window, max_steps)
+        self.r = lbm.lbm_result()
+        self.calm = ctypes.c_int(0)
+        self.first = True
+
+    def window(self, rho_g, rho_l, max_dev=5.0, finite=True, diverged=False):
+        obs = (ctypes.c_double * 6)(rho_g, rho_l, 7.5, 1234.5, 1e-6, max_dev)
+        st = self.S.shim_window_verdict(*self.rule, obs, int(finite), int(diverged),
+                                        int(self.first), ctypes.byref(self.calm),
+                                        ctypes.byref(self.r))
+        self.first = False
+        return st
+
+
+def test_coex_needs_two_calm_windows_after_the_first(S):
+    inst = Instance(S)
+    assert inst.window(0.05, 0.30) == lbm.RUN_ACTIVE  # first window: never calm
+    assert inst.window(0.05, 0.30) == lbm.RUN_ACTIVE and inst.calm.value == 1
+    assert inst.window(0.05, 0.30) == lbm.RUN_CONVERGED and inst.calm.value == 2
+    r = inst.r
+    assert r.steps == 3000 and (r.rho_g, r.rho_l, r.width, r.mass) == (0.05, 0.30, 7.5, 1234.5)
+    assert r.max_drho == pytest.approx(1e-6)
+
+
+def test_coex_relative_floor_and_reset(S):
+    inst = Instance(S)
+    inst.window(0.05, 0.30)
+    floor_l = EPS8 * 0.30  # 2.9e-7, above tol = 1e-9
+    assert inst.window(0.05, 0.30 + 0.9 * floor_l) == lbm.RUN_ACTIVE and inst.calm.value == 1
+    # a change above the floor in either density resets the count
+    assert inst.window(0.05, 0.30 + 3.0 * floor_l) == lbm.RUN_ACTIVE and inst.calm.value == 0
+    assert inst.window(0.05 + 1e-6, 0.30 + 3.0 * floor_l) == lbm.RUN_ACTIVE
+    assert inst.calm.value == 0
+    assert inst.window(0.05 + 1e-6, 0.30 + 3.0 * floor_l) == lbm.RUN_ACTIVE
+    assert inst.window(0.05 + 1e-6, 0.30 + 3.0 * floor_l) == lbm.RUN_CONVERGED
+    # with a larger floor the same change counts as calm
+    loose = Instance(S, conv_rel=1e-5)
+    loose.window(0.05, 0.30)
+    assert loose.window(0.05, 0.30 + 3.0 * floor_l) == lbm.RUN_ACTIVE and loose.calm.value == 1
+
+
+def test_cell_rule_and_no_rule(S):
+    cell = Instance(S, conv=lbm.CONV_CELL)
+    assert cell.window(0.05, 0.30, max_dev=1.5) == lbm.RUN_ACTIVE
+    assert cell.window(0.05, 0.31, max_dev=0.99) == lbm.RUN_CONVERGED  # every cell in tolerance
+    none = Instance(S, conv=lbm.CONV_NONE, max_steps=3000)
+    assert [none.window(0.05, 0.30, max_dev=0.0) for _ in range(3)] == [
+        lbm.RUN_ACTIVE, lbm.RUN_ACTIVE, lbm.RUN_CAPPED]  # runs to the cap
+
+
+def test_divergence_outranks_convergence_and_the_cap(S):
+    inst = Instance(S, conv=lbm.CONV_CELL, max_steps=1000)
+    assert inst.window(0.05, 0.30, max_dev=0.0, diverged=True) == lbm.RUN_DIVERGED
+    inst = Instance(S, conv=lbm.CONV_CELL)
+    assert inst.window(float("nan"), 0.30, max_dev=0.0, finite=False) == lbm.RUN_DIVERGED
+
+
+def test_convergence_outranks_the_cap(S):
+    inst = Instance(S, max_steps=3000)
+    inst.window(0.05, 0.30)
+    inst.window(0.05, 0.30)
+    assert inst.window(0.05, 0.30) == lbm.RUN_CONVERGED  # reached at the cap itself
+    capped = Instance(S, max_steps=2000)
+    capped.window(0.05, 0.30)
+    assert capped.window(0.05, 0.30) == lbm.RUN_CAPPED
