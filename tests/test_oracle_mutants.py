@@ -54,6 +54,22 @@ MUTANTS = {
     "MRT energy row 3|c|^2 -> 2|c|^2": ("M[1][a] = -4.0 + 3.0 * c2;", "M[1][a] = -4.0 + 2.0 * c2;"),
     "MRT f_eq moments at u": ("oracle_feq(rho, vx, vy, feq);\n  for (int a = 0; a < Q; ++a) fhat",
                               "oracle_feq(rho, ux, uy, feq);\n  for (int a = 0; a < Q; ++a) fhat"),
+    "EOS attraction sign": ("return rho * RT * num / den - a * rho * rho;",
+                            "return rho * RT * num / den + a * rho * rho;"),
+    "EOS denominator (1 - eta)^2": ("double den = (1.0 - eta) * (1.0 - eta) * (1.0 - eta);",
+                                    "double den = (1.0 - eta) * (1.0 - eta);"),
+    "eta = b rho / 2": ("double eta = b * rho / 4.0;", "double eta = b * rho / 2.0;"),
+    "psi without the factor 2": ("double arg = 2.0 * (", "double arg = 1.0 * ("),
+    "w(1) = 1/4": ("if (e2 == 1) return 1.0 / 3.0;", "if (e2 == 1) return 1.0 / 4.0;"),
+    "stream backwards in y": ("int yd = ((y + ey[a]) % ny + ny) % ny;",
+                              "int yd = ((y - ey[a]) % ny + ny) % ny;"),
+    "f_eq linear term without 1/c_s^2": ("(1.0 + eu / cs2() +", "(1.0 + eu +"),
+    "Guo second-order term halved": ("double Cee = 2.0 * Ce *", "double Cee = Ce *"),
+    "modified EDM f_eq at v": ("oracle_feq(rho, ux, uy, feq);\n      for (int a = 0; a < Q; ++a)\n        fout[a] = f[a] - (f[a] - feq[a]) / tau +\n                  guo_term(a, 1.0, 1.0 / tau",
+                               "oracle_feq(rho, vx, vy, feq);\n      for (int a = 0; a < Q; ++a)\n        fout[a] = f[a] - (f[a] - feq[a]) / tau +\n                  guo_term(a, 1.0, 1.0 / tau"),
+    "improved v = u + F/rho": ("*vx = ux + Fx / (2.0 * rho);", "*vx = ux + Fx / rho;"),
+    "SC shift against the force": ("oracle_feq(rho, ux + tau * Fx / rho, uy + tau * Fy / rho, feq);",
+                                   "oracle_feq(rho, ux - tau * Fx / rho, uy - tau * Fy / rho, feq);"),
     "SC relaxation 1/tau -> tau": ("for (int a = 0; a < Q; ++a) fout[a] = f[a] - (f[a] - feq[a]) / tau;\n      return 0;\n    }\n    case OR_EDM: {",
                                    "for (int a = 0; a < Q; ++a) fout[a] = f[a] - (f[a] - feq[a]) * tau;\n      return 0;\n    }\n    case OR_EDM: {"),
 }
