@@ -95,13 +95,35 @@ def _calm(new, old, tol, rel=COEX_REL):
     return abs(new - old) < max(tol, rel * abs(new))
 
 
+def window_status(conv, c, prev_c, calm, cell, finite, steps, tol, max_steps, rel=COEX_REL):
+    """The batch engine's rule after one window, for runs checked on the host:
+    c and prev_c are (rho_g, rho_l) now and one window earlier (prev_c None
+    for the first window after a start, which is never calm); calm counts
+    consecutive windows in which both changed by less than max(tol, rel value);
+    cell says every cell changed by less than its tolerance.  Returns
+    (status, calm): DIVERGED (a non-finite density) before CONVERGED (CELL:
+    cell; COEX: two calm windows in a row; NONE: never) before CAPPED (steps
+    reached max_steps) before ACTIVE."""
+    calm = calm + 1 if (prev_c is not None and _calm(c[0], prev_c[0], tol, rel)
+                        and _calm(c[1], prev_c[1], tol, rel)) else 0
+    converged = cell if conv == lbm.CONV_CELL else (conv == lbm.CONV_COEX and calm >= 2)
+    if not finite:
+        return lbm.RUN_DIVERGED, calm
+    if converged:
+        return lbm.RUN_CONVERGED, calm
+    if steps >= max_steps:
+        return lbm.RUN_CAPPED, calm
+    return lbm.RUN_ACTIVE, calm
+
+
 def run_sequential(instances, rho_g, rho_l, width, window=1000, tol=1e-9, max_steps=200000,
                    device=0, conv=lbm.CONV_COEX, conv_rel=None):
     """Plain runs, one instance after another, through lbm_step; convergence
-    is checked on the host with the batch engine's rules (CONV_COEX: rho_g
-    and rho_l each changed by less than max(tol, conv_rel value) over two
-    consecutive windows; CONV_CELL: every cell by less than
-    max(tol, 8 eps_32 rho) over a window).  Returns (results, wall seconds)."""
+    is checked on the host with the batch engine's rule (window_status:
+    CONV_COEX: rho_g and rho_l each changed by less than max(tol, conv_rel
+    value) over two consecutive windows; CONV_CELL: every cell by less than
+    max(tol, 8 eps_32 rho) over a window; CONV_NONE: run to max_steps).
+    Returns (results, wall seconds)."""
     rel = COEX_REL if conv_rel is None else conv_rel
     out = []
     t0 = time.perf_counter()
@@ -127,15 +149,10 @@ def run_sequential(instances, rho_g, rho_l, width, window=1000, tol=1e-9, max_st
                     break
                 rho = lat.observe()[0]
                 c = _coexistence(rho)
-                calm = calm + 1 if prev_c is not None and _calm(c[0], prev_c[0], tol, rel) and \
-                    _calm(c[1], prev_c[1], tol, rel) else 0
                 cell = np.all(np.abs(rho - prev) < np.maximum(tol, 8 * F32_EPS * np.abs(rho)))
-                if not np.all(np.isfinite(rho)):
-                    status = lbm.RUN_DIVERGED
-                elif (cell if conv == lbm.CONV_CELL else calm >= 2):
-                    status = lbm.RUN_CONVERGED
-                elif steps >= max_steps:
-                    status = lbm.RUN_CAPPED
+                status, calm = window_status(conv, c, prev_c, calm, cell,
+                                             bool(np.all(np.isfinite(rho))), steps, tol,
+                                             max_steps, rel)
                 prev, prev_c = rho, c
                 history.append((steps, c[0], c[1], len(history)))
             g, l = _coexistence(prev) if status != lbm.RUN_DIVERGED else (np.nan, np.nan)

@@ -271,3 +271,32 @@ def test_convergence_outranks_the_cap(S):
     capped = Instance(S, max_steps=2000)
     capped.window(0.05, 0.30)
     assert capped.window(0.05, 0.30) == lbm.RUN_CAPPED
+
+
+@pytest.mark.parametrize("conv", [lbm.CONV_COEX, lbm.CONV_CELL, lbm.CONV_NONE])
+@pytest.mark.parametrize("seed", range(12))
+def test_sequential_baseline_applies_the_batch_rule(S, conv, seed):
+    """sweep.window_status (the host check of the plain sequential runs the
+    batch is compared with) and the batch engine's window_verdict reach the
+    same status and calm count window after window."""
+    from paper_1204_4098_gb300 import sweep
+    rng = np.random.default_rng(seed)
+    tol, rel, window, max_steps = 1e-9, EPS8, 1000, 25000
+    inst = Instance(S, conv=conv, tol=tol, conv_rel=rel, window=window, max_steps=max_steps)
+    g, l = 0.05, 0.30
+    prev_c, calm, steps = None, 0, 0
+    for _ in range(40):
+        # no change, a change under the floor, a change over it
+        scale = rng.choice([0.0, 0.3, 5.0], p=[0.15, 0.2, 0.65]) * rel
+        g *= 1 + scale * rng.choice([-1, 1])
+        l *= 1 + scale * rng.choice([-1, 1])
+        max_dev = float(rng.choice([0.5, 2.0], p=[0.1, 0.9]))
+        finite = bool(rng.random() > 0.04)
+        steps += window
+        st_py, calm = sweep.window_status(conv, (g, l), prev_c, calm, max_dev < 1.0, finite,
+                                          steps, tol, max_steps, rel)
+        st_c = inst.window(g, l, max_dev=max_dev, finite=finite)
+        assert (st_py, calm) == (st_c, inst.calm.value)
+        prev_c = (g, l)
+        if st_py != lbm.RUN_ACTIVE:
+            break
