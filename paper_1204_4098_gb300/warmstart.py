@@ -108,6 +108,26 @@ def train(X, Y, stages=((1500, 2e-3), (1500, 5e-4), (1500, 1e-4)), batch=128, se
     return WarmStartModel(mlp, mean, std, loss, time.perf_counter() - t0)
 
 
+FALLBACK_RULES = ("first_window", "converged", "diverged")
+
+
+def needs_fallback(rule, status, windows_run, fell, rho_l, rho_g, pred_l, pred_g, tol):
+    """Whether a warm run restarts from the cold start after this window.  A
+    run falls back at most once (`fell`: it already has), always when it has
+    diverged, and otherwise when the prediction-error check of `rule` is due
+    and rho_l or rho_g differs from its prediction by more than `tol`
+    (relative): after the run's first window ("first_window"), when it has
+    converged ("converged"), or never ("diverged")."""
+    if fell:
+        return False
+    if status == lbm.RUN_DIVERGED:
+        return True
+    off = abs(rho_l / pred_l - 1) > tol or abs(rho_g / pred_g - 1) > tol
+    due = (rule == "converged" and status == lbm.RUN_CONVERGED) or \
+        (rule == "first_window" and windows_run == 1)
+    return due and off
+
+
 def run_warm(instances, model, window=1000, tol=1e-9, max_steps=200000, fallback_tol=1e-2,
              device=0, conv_rel=None, fallback="first_window"):
     """Warm-started batched runs with the cold-start fallback, checked after
@@ -121,7 +141,7 @@ def run_warm(instances, model, window=1000, tol=1e-9, max_steps=200000, fallback
       "diverged"     -- never (divergence only).
     Returns (results, info); results carry per-window histories of the run
     that produced the answer."""
-    if fallback not in ("converged", "first_window", "diverged"):
+    if fallback not in FALLBACK_RULES:
         raise ValueError(f"unknown fallback rule {fallback!r}")
     pl, pg, pw = model.predict(instances)
     cg, cl = sweep.cold_start_profiles(instances)
@@ -145,13 +165,8 @@ def run_warm(instances, model, window=1000, tol=1e-9, max_steps=200000, fallback
             for k in list(active):
                 r = b.result(k)
                 hist[k].append((r["steps"], r["rho_g"], r["rho_l"], len(times) - 1))
-                off = (abs(r["rho_l"] / pl[k] - 1) > fallback_tol or
-                       abs(r["rho_g"] / pg[k] - 1) > fallback_tol)
-                check = (fallback == "converged" and r["status"] == lbm.RUN_CONVERGED) or \
-                    (fallback == "first_window" and len(hist[k]) == 1 and
-                     r["status"] != lbm.RUN_DIVERGED)
-                bad = k not in fell and (r["status"] == lbm.RUN_DIVERGED or (check and off))
-                if bad:
+                if needs_fallback(fallback, r["status"], len(hist[k]), k in fell, r["rho_l"],
+                                  r["rho_g"], pl[k], pg[k], fallback_tol):
                     d = instances[k]
                     fell.add(k)
                     hist[k] = []

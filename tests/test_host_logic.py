@@ -1,6 +1,7 @@
 """Host-side logic of the sweep workloads on synthetic inputs (no GPU):
 droplet observables and fits, stability ladders, the sigma crossing, the
-coexistence read-out and convergence test of the sequential baseline."""
+coexistence read-out and convergence test of the sequential baseline, the
+warm start's fallback rules."""
 import numpy as np
 import pytest
 
@@ -82,6 +83,33 @@ def test_coexistence_readout_and_calm_rule():
 def test_warm_start_rejects_an_unknown_fallback_rule():
     with pytest.raises(ValueError):
         warmstart.run_warm([], None, fallback="sometimes")
+
+
+def test_warm_start_fallback_rules():
+    """The cold-start fallback of a warm run (prediction error above 1e-2,
+    taken after the first window, at convergence, or never; divergence
+    always restarts; at most one restart per run)."""
+    A, C, D, CAP = lbm.RUN_ACTIVE, lbm.RUN_CONVERGED, lbm.RUN_DIVERGED, lbm.RUN_CAPPED
+    pred = (0.300, 0.050)
+    good = (0.302, 0.0502)  # within 1 % of the prediction
+    bad_l = (0.306, 0.050)  # rho_l 2 % off
+    bad_g = (0.300, 0.0506)  # rho_g 1.2 % off
+
+    def f(rule, status, windows, fell, obs):
+        return warmstart.needs_fallback(rule, status, windows, fell, obs[0], obs[1], pred[0],
+                                        pred[1], 1e-2)
+
+    for rule in warmstart.FALLBACK_RULES:
+        assert f(rule, D, 5, False, good)  # divergence restarts whatever the rule
+        assert not f(rule, D, 5, True, bad_l)  # but only once
+    assert f("first_window", A, 1, False, bad_l) and f("first_window", A, 1, False, bad_g)
+    assert not f("first_window", A, 1, False, good)
+    assert not f("first_window", A, 2, False, bad_l)  # the check is due after window 1 only
+    assert f("first_window", C, 1, False, bad_l)
+    assert f("converged", C, 7, False, bad_l) and f("converged", C, 7, False, bad_g)
+    assert not f("converged", C, 7, False, good)
+    assert not f("converged", A, 1, False, bad_l) and not f("converged", CAP, 9, False, bad_l)
+    assert not any(f("diverged", st, w, False, bad_l) for st in (A, C, CAP) for w in (1, 7))
 
 
 def test_shard_balances_cells_and_covers_every_instance():
