@@ -118,3 +118,46 @@ def test_shard_balances_cells_and_covers_every_instance():
     assert sorted(i for p in parts for i in p) == list(range(40))
     loads = [sum(inst[i]["nx"] * inst[i]["ny"] for i in p) for p in parts]
     assert max(loads) - min(loads) <= max(d["nx"] * d["ny"] for d in inst)
+
+
+class _StandInLattice:
+    """Test double of lbm.Lattice for the host loop of sweep.run_sequential:
+    a slab whose bulk densities relax geometrically towards fixed values, and
+    that reports divergence when its temperature is marked unstable."""
+
+    def __init__(self, nx, ny, T_over_Tc, precision=None, device=0):
+        self.nx, self.ny, self.t = nx, ny, T_over_Tc
+        self.k = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
+
+    def init_density(self, rho):
+        self.rho0 = np.array(rho)
+
+    def step(self, n, scheme, tau, sigma=0.0, raise_on_error=True):
+        self.k += 1
+        return lbm.LBM_E_DIVERGED if self.t < 0.5 and self.k == 3 else lbm.LBM_OK
+
+    def observe(self):
+        d = 1e-3 * 0.5 ** (8 * self.k)  # settles below the FP32 floor after a few windows
+        return (self.rho0 * (1 + d), None, None)
+
+
+def test_sequential_runner_host_loop(monkeypatch):
+    monkeypatch.setattr(sweep.lbm, "Lattice", _StandInLattice)
+    inst = [dict(nx=4, ny=32, T_over_Tc=0.8, tau=1.0, sigma=0.0, scheme=lbm.SC),
+            dict(nx=4, ny=32, T_over_Tc=0.45, tau=1.0, sigma=0.0, scheme=lbm.SC)]
+    res, wall = sweep.run_sequential(inst, [0.05, 0.02], [0.3, 0.35], [0.0, 0.0], window=1000,
+                                     max_steps=20000)
+    assert res[0]["status"] == lbm.RUN_CONVERGED and res[0]["steps"] < 20000
+    assert res[0]["rho_g"] == pytest.approx(0.05, rel=1e-6)
+    assert res[0]["rho_l"] == pytest.approx(0.3, rel=1e-6)
+    assert [h[0] for h in res[0]["history"]] == list(range(1000, res[0]["steps"] + 1, 1000))
+    assert res[1]["status"] == lbm.RUN_DIVERGED and res[1]["steps"] == 3000
+    none, _ = sweep.run_sequential(inst[:1], [0.05], [0.3], [0.0], window=1000,
+                                   max_steps=5000, conv=lbm.CONV_NONE)
+    assert none[0]["status"] == lbm.RUN_CAPPED and none[0]["steps"] == 5000
