@@ -161,3 +161,82 @@ def test_sequential_runner_host_loop(monkeypatch):
     none, _ = sweep.run_sequential(inst[:1], [0.05], [0.3], [0.0], window=1000,
                                    max_steps=5000, conv=lbm.CONV_NONE)
     assert none[0]["status"] == lbm.RUN_CAPPED and none[0]["steps"] == 5000
+
+
+class _StandInBatch:
+    """Test double of lbm.Batch for the host loop of warmstart.run_warm: each
+    instance moves to its true densities in its first window after a
+    (re)start and converges in its third; instance 2 diverges in its second
+    window after the first start."""
+    TRUE = {0: (0.050, 0.300), 1: (0.040, 0.320), 2: (0.030, 0.340)}
+
+    def __init__(self, instances, **kw):
+        self.n = len(instances)
+        self.win = [0] * self.n
+        self.steps = [0] * self.n
+        self.starts = [0] * self.n
+        self.res = [None] * self.n
+        self.ms = 0.0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
+
+    def init_slabs(self, rho_g, rho_l, width):
+        self.starts = [1] * self.n
+
+    def init_density(self, k, rho):
+        self.win[k] = 0
+        self.starts[k] += 1
+
+    def run(self, windows):
+        self.ms += 1.0
+        for k in range(self.n):
+            if self.res[k] is not None and self.res[k]["status"] != lbm.RUN_ACTIVE \
+                    and self.win[k] > 0:
+                continue
+            self.win[k] += 1
+            self.steps[k] += 1000
+            g, l = self.TRUE[k]
+            if k == 2 and self.starts[k] == 1 and self.win[k] == 2:
+                st = lbm.RUN_DIVERGED
+            else:
+                st = lbm.RUN_CONVERGED if self.win[k] >= 3 else lbm.RUN_ACTIVE
+            self.res[k] = dict(status=st, steps=self.steps[k], rho_g=g, rho_l=l)
+        return sum(r["status"] == lbm.RUN_ACTIVE for r in self.res)
+
+    def stats(self):
+        return dict(gpu_ms=self.ms)
+
+    def result(self, k):
+        return dict(self.res[k])
+
+    def results(self):
+        return [dict(r) for r in self.res]
+
+
+class _StandInModel:
+    def predict(self, instances):
+        # instance 1 predicted 5 % off in rho_l; the others within 1 %
+        return (np.array([0.301, 0.336, 0.341]), np.array([0.0502, 0.040, 0.0301]),
+                np.array([5.0, 5.0, 5.0]))
+
+
+def test_warm_start_host_loop(monkeypatch):
+    monkeypatch.setattr(warmstart.lbm, "Batch", _StandInBatch)
+    monkeypatch.setattr(warmstart.sweep, "cold_start_profiles",
+                        lambda inst: (np.array([0.05, 0.04, 0.03]), np.array([0.3, 0.32, 0.34])))
+    inst = [dict(nx=4, ny=32, T_over_Tc=0.8, tau=1.0, sigma=0.0, scheme=lbm.SC)] * 3
+    res, info = warmstart.run_warm(inst, _StandInModel())
+    assert [r["fallback"] for r in res] == [False, True, True]
+    assert info["fallbacks"] == 2
+    assert all(r["status"] == lbm.RUN_CONVERGED for r in res)
+    # the restarted runs keep only the history of the run that gave the answer
+    assert [len(r["history"]) for r in res] == [3, 3, 3]
+    assert res[1]["steps"] == 4000 and res[2]["steps"] == 5000  # wasted steps are counted
+    res_c, info_c = warmstart.run_warm(inst, _StandInModel(), fallback="converged")
+    assert [r["fallback"] for r in res_c] == [False, True, True]
+    res_d, info_d = warmstart.run_warm(inst, _StandInModel(), fallback="diverged")
+    assert [r["fallback"] for r in res_d] == [False, False, True]
