@@ -123,3 +123,17 @@ def test_batch_create_rejects_bad_arguments_without_cuda(L):
         assert e.value.status == lbm.LBM_E_INVAL
     with pytest.raises(lbm.LbmError):
         lbm.Batch([])
+
+
+def test_every_entry_point_is_documented():
+    """Each declaration in include/lbm.h follows a comment (within three
+    lines, so that a pair such as get/set populations can share one) that
+    states what it does, its arguments and its errors."""
+    lines = open(HEADER).read().splitlines()
+    undocumented = []
+    for i, line in enumerate(lines):
+        m = re.match(r"\s*(?:lbm_status|const char \*|void|int)\s*\*?\s*(lbm_[a-z0-9_]+)\s*\(",
+                     line)
+        if m and not any("*/" in prev for prev in lines[max(0, i - 3):i]):
+            undocumented.append(m.group(1))
+    assert not undocumented, undocumented
