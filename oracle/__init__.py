@@ -28,6 +28,9 @@ from . import theory
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _LIB = os.path.join(_HERE, "liblbm_oracle.so")
+# the same source built with -fopenmp (cell loops split over threads,
+# bit-identical results); used to time the oracle on all host cores
+_LIB_OMP = os.path.join(_HERE, "liblbm_oracle_omp.so")
 
 SC, EDM, IMPROVED, NOFORCE, EDM_MOD, LADD, MRT = range(7)
 Q = 9
@@ -36,19 +39,30 @@ EY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
 W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
 
 
-def compile_oracle(src: str = _SRC, out: str = _LIB, defines=()) -> str:
+def compile_oracle(src: str = _SRC, out: str = _LIB, defines=(), openmp=False) -> str:
     """Compile the C oracle with gcc (FP contraction off, so x86 and Arm hosts
-    round identically)."""
+    round identically); ``openmp`` adds -fopenmp."""
     cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
+           *(["-fopenmp"] if openmp else []),
            *[f"-D{d}" for d in defines], "-o", out, src, "-lm"]
     subprocess.run(cmd, check=True)
     return out
+
+
+def compile_all() -> None:
+    """Both builds: plain (single-threaded) and OpenMP (if gcc supports it)."""
+    compile_oracle()
+    try:
+        compile_oracle(out=_LIB_OMP, openmp=True)
+    except (subprocess.CalledProcessError, OSError):
+        pass
 
 
 def _declare(lib):
     d, i, p = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
     sig = {
         "oracle_version": (i, []),
+        "oracle_threads": (i, [i]),
         "oracle_p_eos": (d, [d, d, d, d]),
         "oracle_psi": (i, [d, d, d, d, d, p]),
         "oracle_feq": (None, [d, d, d, p]),
@@ -77,11 +91,21 @@ _lib_cache = {}
 def load(path: str = _LIB):
     """The oracle library (compiled on first use if it is missing)."""
     if path not in _lib_cache:
-        if path == _LIB and (not os.path.exists(_LIB)
-                             or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)):
-            compile_oracle()
+        if path in (_LIB, _LIB_OMP) and (not os.path.exists(path)
+                                         or os.path.getmtime(path) < os.path.getmtime(_SRC)):
+            compile_oracle(out=path, openmp=path == _LIB_OMP)
         _lib_cache[path] = _declare(ctypes.CDLL(path))
     return _lib_cache[path]
+
+
+def load_omp(threads: int = 0):
+    """The OpenMP build (None if it cannot be built); ``threads`` > 0 sets
+    its thread count.  Returns (library, threads in use)."""
+    try:
+        lib = load(_LIB_OMP)
+    except (subprocess.CalledProcessError, OSError):
+        return None, 1
+    return lib, lib.oracle_threads(int(threads))
 
 
 def _ptr(a: np.ndarray):

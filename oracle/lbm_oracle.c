@@ -23,10 +23,19 @@
  * e0 = (0,0); e1..e4 = (1,0), (0,1), (-1,0), (0,-1); e5..e8 = (1,1), (-1,1),
  * (-1,-1), (1,-1).  Weights 4/9, 1/9, 1/36 (text after Eq. 2).
  * Populations are stored as f[a][y][x] (x fastest), periodic in x and y.
+ *
+ * Built with -fopenmp (a separate library; the default build has no
+ * OpenMP), the loops over cells whose iterations are independent -- moments,
+ * potential, force, collision, streaming -- are split over threads.  Each
+ * cell's arithmetic is the same, and nothing is summed across cells in
+ * those loops, so the result is bit-identical to the single-threaded build.
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define Q 9
 
@@ -51,6 +60,17 @@ enum {
 static double cs2(void) { return 1.0 / 3.0; }
 
 int oracle_version(void) { return 1; }
+
+/* Threads used by the cell loops (n > 0 sets it); 1 without OpenMP. */
+int oracle_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 /* ---- equation of state ------------------------------------------------ */
 
@@ -91,6 +111,7 @@ void oracle_feq(double rho, double ux, double uy, double *feq) {
 void oracle_moments(int nx, int ny, const double *f, double *rho, double *ux,
                     double *uy) {
   int n = nx * ny;
+#pragma omp parallel for schedule(static)
   for (int c = 0; c < n; ++c) {
     double r = 0.0, jx = 0.0, jy = 0.0;
     for (int a = 0; a < Q; ++a) {
@@ -109,9 +130,11 @@ void oracle_moments(int nx, int ny, const double *f, double *rho, double *ux,
 
 int oracle_psi_field(int nx, int ny, const double *rho, double RT, double a,
                      double b, double G, double *psi) {
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
   for (int c = 0; c < nx * ny; ++c)
-    if (oracle_psi(rho[c], RT, a, b, G, &psi[c])) return 1;
-  return 0;
+    bad |= oracle_psi(rho[c], RT, a, b, G, &psi[c]) != 0;
+  return bad;
 }
 
 /* ---- step 3: interaction force, Eq. 3 ----------------------------------- */
@@ -126,6 +149,7 @@ static double w_int(int a) {
 
 void oracle_force(int nx, int ny, double G, const double *psi, double *Fx,
                   double *Fy) {
+#pragma omp parallel for schedule(static)
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
       double sx = 0.0, sy = 0.0;
@@ -323,6 +347,7 @@ int oracle_collide_cell(int scheme, double tau, double sigma, const double *f,
 
 void oracle_stream(int nx, int ny, const double *fpost, double *fnew) {
   size_t n = (size_t)nx * ny;
+#pragma omp parallel for collapse(2) schedule(static)
   for (int a = 0; a < Q; ++a)
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x) {
@@ -357,15 +382,18 @@ int oracle_step(int nx, int ny, double *f, int scheme, double tau, double sigma,
     if (oracle_psi_field(nx, ny, rho, RT, a, b, G, psi)) { rc = 1; goto done; }
     oracle_force(nx, ny, G, psi, Fx, Fy);
   }
-  for (size_t c = 0; c < n; ++c) {
+  int bad_scheme = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad_scheme)
+  for (long long c = 0; c < (long long)n; ++c) {
     double fc[Q], fo[Q];
     for (int q = 0; q < Q; ++q) fc[q] = f[q * n + c];
     if (oracle_collide_cell(scheme, tau, sigma, fc, Fx[c], Fy[c], psi[c], fo)) {
-      rc = 2;
-      goto done;
+      bad_scheme = 1;
+      continue;
     }
     for (int q = 0; q < Q; ++q) fpost[q * n + c] = fo[q];
   }
+  if (bad_scheme) { rc = 2; goto done; }
   oracle_stream(nx, ny, fpost, f);
 done:
   free(rho); free(ux); free(uy); free(psi); free(Fx); free(Fy); free(fpost);
