@@ -164,25 +164,80 @@ def workload_density(n, rank, T_over_Tc=0.85):
     return inputs.spinodal(n, n, 0.5 * (rg + rl), amp=0.01, seed=3 + rank), (rg, rl)
 
 
-def cpu_baseline(n_side=1024, steps=60):
-    """FP64 oracle (test infrastructure) on a 1024 x 1024 sample of the
-    workload for `steps` steps, single-threaded."""
+def host_description():
+    """Host CPU of this machine: model name and the cores this process may use."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() == "Model name" and v.strip() and v.strip() != "-":
+                model = v.strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine()
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except AttributeError:
+        usable = os.cpu_count()
+    return {"cpu_model": model, "nproc": usable, "machine": os.uname().machine}
+
+
+def _time_oracle(lib, nx, ny, steps, init, scheme, tau, sigma, t):
+    import oracle
+    lat = oracle.Lattice(nx, ny, t, lib=lib)
+    lat.init_density(init)
+    t0 = time.perf_counter()
+    rc, done = lat.step(steps, scheme, tau, sigma)
+    dt = time.perf_counter() - t0
+    assert rc == 0
+    return nx * ny * done / dt / 1e6, dt, done
+
+
+def cpu_baseline(n_side=1024, steps_1=40, steps_all=200, config1_steps=10000):
+    """FP64 oracle (test infrastructure) on the host cores: the 1024 x 1024
+    sample of the workload recipe (improved sigma = 0.1, T = 0.85 Tc,
+    tau = 0.8, spinodal init seed 3) on one core and on all cores (the
+    oracle's OpenMP build, bit-identical), and the 64 x 64 flat-interface
+    slab (Shan-Chen, tau = 1, T = 0.8 Tc, 1e4 steps) likewise.  The headline
+    value is the all-core sample."""
     import oracle
     from oracle import theory as th
     from paper_1204_4098_gb300 import inputs
+    host = host_description()
     t = 0.85
     rg, rl, _ = th.maxwell(th.CarnahanStarling(th.temperature(t)))
     rho0 = inputs.spinodal(n_side, n_side, 0.5 * (rg + rl), amp=0.01, seed=3)
-    lat = oracle.Lattice(n_side, n_side, t)
-    lat.init_density(rho0)
-    t0 = time.perf_counter()
-    rc, done = lat.step(steps, oracle.IMPROVED, 0.8, 0.1)
-    dt = time.perf_counter() - t0
-    assert rc == 0
-    return {"value": n_side * n_side * done / dt / 1e6, "unit": "MLUPS", "cores": 1,
-            "kind": "oracle",
-            "sample": f"{n_side}x{n_side} crop of the workload recipe, {done} steps, FP64, "
-                      f"1 thread ({dt:.1f} s)"}
+    one = oracle.load()
+    omp, threads = oracle.load_omp(host["nproc"])
+    v1, dt1, d1 = _time_oracle(one, n_side, n_side, steps_1, rho0, oracle.IMPROVED, 0.8, 0.1, t)
+    out = {"unit": "MLUPS", "kind": "oracle", "host": host,
+           "single_core": {"value": v1, "cores": 1,
+                           "sample": f"{n_side}x{n_side} crop, {d1} steps, 1 thread "
+                                     f"({dt1:.1f} s)"}}
+    if omp is not None:
+        va, dta, da = _time_oracle(omp, n_side, n_side, steps_all, rho0, oracle.IMPROVED, 0.8,
+                                   0.1, t)
+        out.update({"value": va, "cores": threads,
+                    "sample": f"{n_side}x{n_side} crop of the workload recipe, {da} steps, FP64, "
+                              f"{threads} threads (OpenMP build, bit-identical; {dta:.1f} s)"})
+    else:
+        out.update({"value": v1, "cores": 1, "sample": out["single_core"]["sample"]})
+    # config 1 in full: 64 x 64 slab at the Maxwell densities, 1e4 steps
+    t1 = 0.8
+    g1, l1, _ = th.maxwell(th.CarnahanStarling(th.temperature(t1)))
+    slab = inputs.slab_step(64, 64, g1, l1, 16, 48, amp=1e-3, seed=1)
+    c1 = {}
+    for name, lib, cores in (("single_core", one, 1), ("all_cores", omp, threads)):
+        if lib is None:
+            continue
+        v, dt, d = _time_oracle(lib, 64, 64, config1_steps, slab, oracle.SC, 1.0, 0.0, t1)
+        c1[name] = {"value": v, "cores": cores, "seconds": dt, "steps": d}
+    out["config1_64x64_1e4_steps"] = c1
+    return out
 
 
 def run_reference(args, world, rank):
@@ -194,22 +249,27 @@ def run_reference(args, world, rank):
     from paper_1204_4098_gb300 import inputs
     side = args.ref_side
     t = 0.85
+    host = host_description()
+    lib, threads = oracle.load_omp(host["nproc"])
+    if lib is None:
+        lib, threads = oracle.load(), 1
     rg, rl, _ = th.maxwell(th.CarnahanStarling(th.temperature(t)))
-    lat = oracle.Lattice(side, side, t)
+    lat = oracle.Lattice(side, side, t, lib=lib)
     lat.init_density(inputs.spinodal(side, side, 0.5 * (rg + rl), amp=0.01, seed=3))
     lat.step(args.warmup, oracle.IMPROVED, 0.8, 0.1)
     t0 = time.perf_counter()
     rc, done = lat.step(args.steps, oracle.IMPROVED, 0.8, 0.1)
     dt = time.perf_counter() - t0
     value = side * side * done / dt / 1e6
-    sample = f"{side}x{side} crop of the 8192x8192 recipe per step, FP64 oracle, 1 thread"
+    sample = (f"{side}x{side} crop of the 8192x8192 recipe per step, FP64 oracle, "
+              f"{threads} threads (OpenMP build)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / max(done, 1) * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args),
-            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                             "sample": sample, "host": host},
             "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -335,7 +395,7 @@ def run_ours(args, world, rank, local):
 
     sweep_line = None
     if rank == 0 and not args.no_sweep:
-        sweep_line = sweep_measure(128, 16, seed=4, device=local)
+        sweep_line = sweep_measure(128, 128, seed=4, device=local)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -390,8 +450,9 @@ def sweep_measure(n_inst, n_seq, seed=4, device=0):
     seq, seq_wall = sweep.run_sequential(inst[:n_seq], g[:n_seq], l[:n_seq], w[:n_seq],
                                          device=device)
     agree, n_both = _coex_agreement(res[:n_seq], seq)
-    # sequential time per instance, over the same instances the batch also ran
+    # measured over every instance when n_seq == n_inst; otherwise scaled
     seq_total = seq_wall * n_inst / max(n_seq, 1)
+    per = np.array([r["wall"] for r in seq])
     cells_steps = sum(d["nx"] * d["ny"] * r["steps"] for d, r in zip(inst, res))
     return {"instances": n_inst, "batched_wall_s": wall, "batched_gpu_s": stats["gpu_ms"] / 1e3,
             "instances_per_s": n_inst / wall,
@@ -399,6 +460,9 @@ def sweep_measure(n_inst, n_seq, seed=4, device=0):
             "windows": stats["windows"], "status": _status_counts(res),
             "sequential_instances_timed": n_seq, "sequential_wall_s": seq_wall,
             "sequential_wall_s_all": seq_total,
+            "sequential_measured_in_full": n_seq == n_inst,
+            "sequential_per_instance_s": {"min": float(per.min()), "median": float(np.median(per)),
+                                          "max": float(per.max())} if len(per) else None,
             "speedup_vs_sequential": seq_total / wall,
             "coexistence_max_rel_diff_vs_sequential": agree, "converged_in_both": n_both,
             "convergence_rule": "COEX: rho_g, rho_l (FP64 row means) change < max(1e-9, 8 ulp) "
@@ -631,7 +695,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variants", action="store_true", default=True)
     ap.add_argument("--no-variants", dest="variants", action="store_false")
-    ap.add_argument("--ref-side", type=int, default=384)
+    ap.add_argument("--ref-side", type=int, default=1024)
     ap.add_argument("--workload", choices=("roofline", "sweep", "warmstart", "droplets",
                                            "stability", "calibrate"), default="roofline")
     ap.add_argument("--droplet-steps", type=int, default=20000)

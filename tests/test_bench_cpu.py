@@ -98,3 +98,15 @@ def test_max_over_ranks_with_two_gloo_ranks():
         p.join(timeout=60)
         assert p.exitcode == 0
     assert got == [(0, 2, 11.0), (1, 2, 11.0)]
+
+
+def test_cpu_baseline_reports_one_and_all_cores_and_the_host():
+    d = bench.cpu_baseline(n_side=32, steps_1=2, steps_all=2, config1_steps=5)
+    assert d["kind"] == "oracle" and d["unit"] == "MLUPS" and d["value"] > 0
+    assert d["single_core"]["cores"] == 1 and d["single_core"]["value"] > 0
+    assert d["host"]["nproc"] >= 1 and d["host"]["cpu_model"]
+    assert d["cores"] >= 1
+    c1 = d["config1_64x64_1e4_steps"]
+    assert c1["single_core"]["steps"] == 5
+    if "all_cores" in c1:
+        assert c1["all_cores"]["cores"] == d["cores"]
