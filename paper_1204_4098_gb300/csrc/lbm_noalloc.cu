@@ -18,10 +18,9 @@
 
 namespace {
 
-// Values summed by one block; the partial-sum array bounds the number of
-// blocks, and so the largest input.
-constexpr size_t kChunk = size_t(1) << 20;
-constexpr int kMaxBlocks = 1024;  // 8 KB of partial sums
+constexpr int kMaxBlocks = 1024;                    // 8 KB of partial sums
+constexpr size_t kMinPerBlock = 4096;               // values per block at least
+constexpr size_t kMaxValues = size_t(1) << 30;      // largest accepted n
 constexpr int kThreads = 256;
 constexpr int kMaxDevices = 64;
 
@@ -33,6 +32,16 @@ static __device__ __align__(256) double g_partial[kMaxBlocks];
 std::mutex g_setup_mutex;
 double* g_partial_addr[kMaxDevices] = {nullptr};
 
+// Blocks of a call: enough to spread n over the GPU (one per kMinPerBlock
+// values, at most kMaxBlocks).  Depends only on n.
+int blocks_for(size_t n) {
+  const size_t b = (n + kMinPerBlock - 1) / kMinPerBlock;
+  return int(b < size_t(kMaxBlocks) ? b : size_t(kMaxBlocks));
+}
+
+// Block-wide sum.  The result is valid in thread 0 only (the other threads
+// get 0); every launch of the kernels below uses exactly kThreads threads,
+// which the shared array is sized for.
 __device__ double block_reduce(double v, double* smem) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   if ((threadIdx.x & 31) == 0) smem[threadIdx.x >> 5] = v;
@@ -43,13 +52,16 @@ __device__ double block_reduce(double v, double* smem) {
   return s;
 }
 
-// Block b sums values [b * kChunk, min((b + 1) * kChunk, n)) in a fixed
-// order into partial[b]; the result does not depend on scheduling.
+// Block b of gridDim.x sums the contiguous range [b * per, min((b + 1) * per,
+// n)), per = ceil(n / gridDim.x), in a fixed order into partial[b]: the
+// ranges and the order depend only on n, so the result does not depend on
+// scheduling.
 __global__ void __launch_bounds__(kThreads)
-chunk_sum_kernel(const float* __restrict__ x, size_t n, double* partial) {
+range_sum_kernel(const float* __restrict__ x, size_t n, double* partial) {
   __shared__ double smem[kThreads / 32];
-  const size_t begin = size_t(blockIdx.x) * kChunk;
-  const size_t end = begin + kChunk < n ? begin + kChunk : n;
+  const size_t per = (n + gridDim.x - 1) / gridDim.x;
+  const size_t begin = size_t(blockIdx.x) * per;
+  const size_t end = begin + per < n ? begin + per : n;
   double acc = 0.0;
   for (size_t i = begin + threadIdx.x; i < end; i += kThreads) acc += double(x[i]);
   const double s = block_reduce(acc, smem);
@@ -66,8 +78,11 @@ final_sum_kernel(const double* partial, int nblocks, double* out) {
 }
 
 // Device address of g_partial on the current device, looked up once per
-// device.  In host code the name g_partial is only a host-side stand-in, so
-// the address has to come from cudaGetSymbolAddress.
+// device and cached for the life of the process.  In host code the name
+// g_partial is only a host-side stand-in, so the address has to come from
+// cudaGetSymbolAddress.  A device reset (cudaDeviceReset) reloads the
+// module and makes the cached address stale; the entry point's contract
+// excludes resetting a device it has been used on.
 cudaError_t partial_address(double** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -89,12 +104,12 @@ cudaError_t partial_address(double** out) {
 extern "C" lbm_status lbm_mass_f32_noalloc(const float* d_values, size_t n, double* d_out,
                                            void* cuda_stream) {
   if (!d_out || (n > 0 && !d_values)) return LBM_E_INVAL;
-  if (n > size_t(kMaxBlocks) * kChunk) return LBM_E_INVAL;  // beyond the fixed scratch
+  if (n > kMaxValues) return LBM_E_INVAL;  // the documented maximum
   double* partial = nullptr;
   if (partial_address(&partial) != cudaSuccess) return LBM_E_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  const int nblocks = int((n + kChunk - 1) / kChunk);
-  if (nblocks > 0) chunk_sum_kernel<<<nblocks, kThreads, 0, s>>>(d_values, n, partial);
+  const int nblocks = blocks_for(n);
+  if (nblocks > 0) range_sum_kernel<<<nblocks, kThreads, 0, s>>>(d_values, n, partial);
   final_sum_kernel<<<1, kThreads, 0, s>>>(partial, nblocks, d_out);
   return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_E_CUDA;
 }
