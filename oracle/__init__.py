@@ -75,6 +75,7 @@ def _declare(lib):
         "oracle_step": (i, [i, i, p, i, d, d, d, d, d, d]),
         "oracle_run": (i, [i, i, p, i, i, d, d, d, d, d, d, p]),
         "oracle_init_equilibrium": (None, [i, i, p, p, p, p]),
+        "oracle_init_at_rest": (i, [i, i, p, d, d, d, d, p]),
         "oracle_observe": (i, [i, i, p, d, d, d, d, i, p, p, p]),
         "oracle_mass": (d, [i, i, p]),
     }
@@ -218,6 +219,18 @@ class Lattice:
 
     def init_density(self, rho, ux=None, uy=None):
         self.f = init_equilibrium(rho, ux, uy, lib=self.lib)
+        self.steps = 0
+
+    def init_density_at_rest(self, rho):
+        """f = f_eq(rho, u) with u = -F / (2 rho) (zero actual velocity)."""
+        rho = _vec(rho)
+        assert rho.shape == (self.ny, self.nx)
+        f = np.zeros((Q, self.ny, self.nx))
+        rc = self.lib.oracle_init_at_rest(self.nx, self.ny, _ptr(rho), self.RT, self.a,
+                                          self.b, self.G, _ptr(f))
+        if rc:
+            raise FloatingPointError("density outside the domain of psi")
+        self.f = f
         self.steps = 0
 
     def step(self, n, scheme, tau, sigma=0.0):

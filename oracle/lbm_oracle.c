@@ -425,6 +425,30 @@ void oracle_init_equilibrium(int nx, int ny, const double *rho, const double *ux
   }
 }
 
+/* A density field at rest: f_a = f_eq(rho, u) with u = -F / (2 rho), where F
+ * is the Eq. 3 force of rho itself, so that the actual fluid velocity
+ * v = u + F / (2 rho) of Table I vanishes at every cell.  Returns 0, or 1 if
+ * psi is undefined somewhere (f is then left unchanged). */
+int oracle_init_at_rest(int nx, int ny, const double *rho, double RT, double a,
+                        double b, double G, double *f) {
+  size_t n = (size_t)nx * ny;
+  double *psi = malloc(n * sizeof(double));
+  double *Fx = malloc(n * sizeof(double)), *Fy = malloc(n * sizeof(double));
+  double *ux = malloc(n * sizeof(double)), *uy = malloc(n * sizeof(double));
+  int rc = 0;
+  if (!psi || !Fx || !Fy || !ux || !uy) { rc = 2; goto done; }
+  if (oracle_psi_field(nx, ny, rho, RT, a, b, G, psi)) { rc = 1; goto done; }
+  oracle_force(nx, ny, G, psi, Fx, Fy);
+  for (size_t c = 0; c < n; ++c) {
+    ux[c] = -Fx[c] / (2.0 * rho[c]);
+    uy[c] = -Fy[c] / (2.0 * rho[c]);
+  }
+  oracle_init_equilibrium(nx, ny, rho, ux, uy, f);
+done:
+  free(psi); free(Fx); free(Fy); free(ux); free(uy);
+  return rc;
+}
+
 /* Density and the actual fluid velocity v = u + F / (2 rho) (Table I, every
  * scheme) of the current state; F = 0 when noforce is set.  Returns 0 or 1
  * (psi undefined). */

@@ -428,6 +428,35 @@ def pin_static_interface_actual_velocity(lib):
     return fails
 
 
+def pin_init_at_rest(lib):
+    """A density field at rest (zero actual velocity v = u + F/(2 rho),
+    Table I): for a uniform density it is the plain equilibrium at u = 0
+    (F = 0 there); for the density of a slab the dynamics have relaxed to a
+    static state, its velocity must be the relaxed state's own u (which the
+    step computed, not the initialisation), and it is not zero."""
+    fails = []
+    t = 0.9
+    uni = np.full((5, 4), 0.2)
+    a = oracle.Lattice(4, 5, t, lib=lib)
+    a.init_density_at_rest(uni)
+    fails += _close("uniform at rest", a.f, oracle.init_equilibrium(uni, lib=lib))
+    rg, rl, _ = th.maxwell(th.CarnahanStarling(th.temperature(t)))
+    lat = oracle.Lattice(2, 40, t, lib=lib)
+    lat.init_density(inputs.slab_tanh(2, 40, rg, rl, W=5.0))
+    if lat.step(8000, oracle.SC, 0.8, 0.0)[0]:
+        return fails + ["relaxing slab diverged"]
+    rho_r, ux_r, uy_r = oracle.moments(lat.f, lib=lib)
+    b = oracle.Lattice(2, 40, t, lib=lib)
+    b.init_density_at_rest(rho_r)
+    rho_b, ux_b, uy_b = oracle.moments(b.f, lib=lib)
+    fails += _close("at-rest density", rho_b, rho_r, rtol=1e-14)
+    fails += _close("at-rest u_y vs relaxed", uy_b, uy_r, atol=1e-11)
+    fails += _close("at-rest u_x vs relaxed", ux_b, ux_r, atol=1e-11)
+    if not np.abs(uy_r).max() > 1e-2:
+        fails.append(f"relaxed slab has no u: {np.abs(uy_r).max():.2e}")
+    return fails
+
+
 # ---------------------------------------------------------------------------
 # multiple-relaxation-time form of the improved scheme (end of Sec. IV)
 # ---------------------------------------------------------------------------
@@ -501,5 +530,5 @@ ALL_FAST_PINS = [
     pin_collision_momentum, pin_eos_and_psi, pin_step_conservation,
     pin_uniform_fixed_point, pin_shear_wave_decay, pin_taylor_green_decay,
     pin_guo_flat_interface_is_eps0, pin_static_interface_actual_velocity,
-    pin_mrt_reduces_to_improved, pin_mrt_moment_relaxation,
+    pin_init_at_rest, pin_mrt_reduces_to_improved, pin_mrt_moment_relaxation,
 ]

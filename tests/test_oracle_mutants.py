@@ -54,6 +54,10 @@ MUTANTS = {
     "MRT energy row 3|c|^2 -> 2|c|^2": ("M[1][a] = -4.0 + 3.0 * c2;", "M[1][a] = -4.0 + 2.0 * c2;"),
     "MRT f_eq moments at u": ("oracle_feq(rho, vx, vy, feq);\n  for (int a = 0; a < Q; ++a) fhat",
                               "oracle_feq(rho, ux, uy, feq);\n  for (int a = 0; a < Q; ++a) fhat"),
+    "at-rest velocity +F/(2 rho)": ("ux[c] = -Fx[c] / (2.0 * rho[c]);\n    uy[c] = -Fy[c] / (2.0 * rho[c]);",
+                                    "ux[c] = Fx[c] / (2.0 * rho[c]);\n    uy[c] = Fy[c] / (2.0 * rho[c]);"),
+    "at-rest velocity -F/rho": ("ux[c] = -Fx[c] / (2.0 * rho[c]);\n    uy[c] = -Fy[c] / (2.0 * rho[c]);",
+                                "ux[c] = -Fx[c] / rho[c];\n    uy[c] = -Fy[c] / rho[c];"),
     "EOS attraction sign": ("return rho * RT * num / den - a * rho * rho;",
                             "return rho * RT * num / den + a * rho * rho;"),
     "EOS denominator (1 - eta)^2": ("double den = (1.0 - eta) * (1.0 - eta) * (1.0 - eta);",
