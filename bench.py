@@ -397,6 +397,13 @@ def run_ours(args, world, rank, local):
     if rank == 0 and not args.no_sweep:
         sweep_line = sweep_measure(128, 128, seed=4, device=local)
 
+    warm_line = None
+    if rank == 0 and not args.no_warmstart:
+        warm_line = {"label": "reduced config 5: 2,000 training draws (nx = 32 slabs, cap 6e4 "
+                              "steps), 3 x 500 epochs, 64 held-out 256x256 points; cold "
+                              "sequential measured over all 64",
+                     **warmstart_measure(2000, 500, 64, device=local, train_max_steps=60000)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
@@ -414,6 +421,8 @@ def run_ours(args, world, rank, local):
             line["storage_variants"] = variants
         if sweep_line:
             line["batched_sweep"] = sweep_line
+        if warm_line:
+            line["warm_start"] = warm_line
         print(json.dumps(line), flush=True)
 
 
@@ -504,79 +513,115 @@ def run_sweep_workload(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
-def run_warmstart_workload(args, world, rank, local):
-    """Config 5: train the network on converged cold runs, then start held-out
-    points on 256 x 256 grids from its predictions; compare with cold runs."""
+def warmstart_measure(train_draws, epochs, held_out, device=0, seq_all=True, seed_train=40,
+                      seed_held=41, train_max_steps=100000):
+    """Config 5: train the network on converged cold runs of narrow slabs,
+    then start held-out points on 256 x 256 grids from its predictions and
+    compare the whole sweep with cold batched runs and with cold sequential
+    plain runs, all stopped by the same TREND rule."""
     import numpy as np
-    import torch
 
     from paper_1204_4098_gb300 import inputs, lbm, sweep, warmstart
-    torch.cuda.set_device(local)
     t0 = time.perf_counter()
-    X, Y, info = warmstart.training_data(args.train_draws, seed=40, max_steps=100000)
+    X, Y, info = warmstart.training_data(train_draws, seed=seed_train, max_steps=train_max_steps)
     data_s = time.perf_counter() - t0
-    model = warmstart.train(X, Y, stages=((args.epochs, 2e-3), (args.epochs, 5e-4),
-                                          (args.epochs, 1e-4)), batch=128, seed=1)
-    held = inputs.sweep_instances(args.held_out, seed=41, nx_range=(256, 256),
+    model = warmstart.train(X, Y, stages=((epochs, 2e-3), (epochs, 5e-4), (epochs, 1e-4)),
+                            batch=128, seed=1, device=device)
+    held = inputs.sweep_instances(held_out, seed=seed_held, nx_range=(256, 256),
                                   ny_range=(256, 256))
-    warm, winfo = warmstart.run_warm(held, model)  # default rule: check after window 1
-    cold, cinfo = warmstart.run_cold_batched(held)
-    other_rules = {}
-    for rule in ("converged", "diverged"):
-        w2, i2 = warmstart.run_warm(held, model, fallback=rule)
-        b2 = [k for k in range(len(held)) if w2[k]["status"] == 1 and cold[k]["status"] == 1]
-        t2, s2 = warmstart.time_to_answer(w2, i2, cold, among=b2)
-        e2, _ = _coex_agreement(w2, cold)
-        other_rules[rule] = {"fallbacks": i2["fallbacks"], "gpu_s": i2["gpu_ms"] / 1e3,
-                             "status": _status_counts(w2), "converged_in_both": len(b2),
-                             "time_to_answer_gpu_s": t2, "mean_steps_to_answer": s2,
-                             "coexistence_max_rel_err_vs_cold": e2}
+    warm, winfo = warmstart.run_warm(held, model, device=device)
+    cold, cinfo = warmstart.run_cold_batched(held, device=device)
     g, l = sweep.cold_start_profiles(held)
-    ns = args.seq_sample
-    seq, seq_wall = sweep.run_sequential(held[:ns], g[:ns], l[:ns], np.zeros(ns))
-    seq_all = seq_wall * len(held) / max(ns, 1)
+    ns = len(held) if seq_all else min(32, len(held))
+    seq, seq_wall = sweep.run_sequential(held[:ns], g[:ns], l[:ns], np.zeros(ns), device=device,
+                                         conv=lbm.CONV_TREND)
+    seq_all_s = seq_wall * len(held) / ns
     err, n_both = _coex_agreement(warm, cold)
+    err_seq, n_both_seq = _coex_agreement(warm[:ns], seq)
     both = [k for k in range(len(held)) if warm[k]["status"] == 1 and cold[k]["status"] == 1]
-    ws = float(np.mean([warm[k]["steps"] for k in both])) if both else None
-    cs = float(np.mean([cold[k]["steps"] for k in both])) if both else None
-    # time to the answer: rho_g, rho_l settled within 1e-3 of the cold converged values
+    mean = lambda rs: float(np.mean([rs[k]["steps"] for k in both])) if both else None
     t_warm, s_warm = warmstart.time_to_answer(warm, winfo, cold, among=both)
-    t_coldb, s_coldb = warmstart.time_to_answer(cold, cinfo, cold, among=both)
-    seq_t = []
-    for k, r in enumerate(seq):
-        if k not in both:
-            seq_t.append(r["wall"])  # outside the compared set: its whole time
-            continue
-        a = sweep.answer_step(r["history"], cold[k]["rho_g"], cold[k]["rho_l"])
-        seq_t.append(r["wall"] * (a[0] / r["steps"] if a else 1.0))
-    seq_answer_all = float(np.sum(seq_t)) * len(held) / max(ns, 1)
-    line = {"metric": METRIC, "workload": "learned warm start (config 5)",
-            "value": seq_answer_all / t_warm if t_warm else None,
-            "unit": "x less time to the coexistence densities within 1e-3 (warm batched vs "
-                    "cold sequential plain runs)",
-            "higher_is_better": True, "n_gpus": world, "data": "synthetic", "dtype": "f32",
-            "time_to_answer_s": {"warm_batched_gpu": t_warm, "cold_batched_gpu": t_coldb,
-                                 "cold_sequential_wall": seq_answer_all,
-                                 "mean_steps_warm": s_warm, "mean_steps_cold": s_coldb},
+    warm_gpu, cold_gpu = winfo["gpu_ms"] / 1e3, cinfo["gpu_ms"] / 1e3
+    return {"held_out": len(held), "grid": "256x256",
+            "rule": "TREND: rho_g, rho_l within 1e-4 of their limits extrapolated from the last "
+                    "two window changes (warm, cold batched and cold sequential alike); "
+                    "fallback: extrapolated limits > 1e-2 from the prediction at window 3, "
+                    "or divergence",
             "training": {**info, "data_wall_s": data_s, "train_loss": model.train_loss,
-                         "train_s": model.train_seconds,
-                         "epochs": [args.epochs, args.epochs, args.epochs],
+                         "train_s": model.train_seconds, "epochs": [epochs] * 3,
                          "learning_rates": [2e-3, 5e-4, 1e-4]},
-            "held_out": len(held), "grid": "256x256",
-            "warm": {"wall_s": winfo["wall"], "gpu_s": winfo["gpu_ms"] / 1e3,
-                     "fallbacks": winfo["fallbacks"], "status": _status_counts(warm),
-                     "mean_steps_converged_both": ws},
-            "cold_batched": {"wall_s": cinfo["wall"], "gpu_s": cinfo["gpu_ms"] / 1e3,
-                             "status": _status_counts(cold), "mean_steps_converged_both": cs},
-            "cold_sequential": {"instances_timed": args.seq_sample, "wall_s": seq_wall,
-                                "wall_s_all": seq_all},
-            "coexistence_max_rel_err_warm_vs_cold": err, "converged_in_both": n_both,
-            "speedup_warm_batched_vs_cold_batched": cinfo["wall"] / winfo["wall"],
-            "sweep_gpu_time_ratio_cold_sequential_over_warm_batched":
-                seq_all / (winfo["gpu_ms"] / 1e3),
-            "fallback_rule": "prediction error > 1e-2 after the first window, or divergence",
-            "other_fallback_rules": other_rules}
+            "warm_batched": {"gpu_s": warm_gpu, "wall_s": winfo["wall"],
+                             "fallbacks": winfo["fallbacks"], "status": _status_counts(warm),
+                             "mean_steps_converged_both": mean(warm)},
+            "cold_batched": {"gpu_s": cold_gpu, "wall_s": cinfo["wall"],
+                             "status": _status_counts(cold), "mean_steps_converged_both": mean(cold)},
+            "cold_sequential": {"instances_timed": ns, "wall_s": seq_wall,
+                                "wall_s_all": seq_all_s, "measured_in_full": ns == len(held),
+                                "status": _status_counts(seq)},
+            "whole_sweep_cold_batched_over_warm_batched": cold_gpu / warm_gpu,
+            "whole_sweep_cold_sequential_over_warm_batched": seq_all_s / warm_gpu,
+            "coexistence_max_rel_err_warm_vs_cold_batched": err,
+            "converged_in_both": n_both,
+            "coexistence_max_rel_err_warm_vs_cold_sequential": err_seq,
+            "converged_in_both_sequential": n_both_seq,
+            "retrospective_time_to_answer_warm_gpu_s": t_warm,
+            "retrospective_mean_steps_to_answer_warm": s_warm}
+
+
+def run_warmstart_workload(args, world, rank, local):
+    """Config 5 in full (about 11,000 training draws, 256 held-out points)."""
+    import torch
+    torch.cuda.set_device(local)
+    res = warmstart_measure(args.train_draws, args.epochs, args.held_out, device=local)
+    line = {"metric": METRIC, "workload": "learned warm start (config 5)",
+            "value": res["whole_sweep_cold_sequential_over_warm_batched"],
+            "unit": "x less whole-sweep time: warm batched GPU vs cold sequential plain runs",
+            "higher_is_better": True, "n_gpus": world, "data": "synthetic", "dtype": "f32",
+            **res}
     print(json.dumps(line), flush=True)
+
+
+def run_band_workload(args, world, rank, local):
+    """Strong scaling of one lattice: the n x n workload split into `world`
+    y-slabs (halo.band_partition), one per rank, each step followed by the
+    halo exchange (two rows x 9 populations to each neighbour, NCCL point to
+    point on device buffers).  At N = 1 the band exchanges with itself (the
+    periodic wrap).  value = all cells x steps / the slowest rank's time."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1204_4098_gb300 import halo, lbm
+    torch.cuda.set_device(local)
+    group = None
+    if world > 1:
+        group = dist.new_group(backend="nccl")
+    n = args.n
+    rho0, _ = workload_density(n, 0)
+    band = halo.BandLattice(n, n, 0.85, rho0, rank=rank, world=world, device=local,
+                            group=group)
+    band.step(args.warmup, lbm.IMPROVED, 0.8, 0.1)
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = lbm.launch_count()
+    start.record(band.stream)
+    st = band.step(args.steps, lbm.IMPROVED, 0.8, 0.1)
+    end.record(band.stream)
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    assert st == lbm.LBM_OK
+    ms = dist_max(start.elapsed_time(end), world)
+    if rank == 0:
+        line = {"metric": METRIC, "workload": f"{n}x{n} single lattice in {world} y-slabs "
+                                              "with halo exchange (strong scaling)",
+                "value": n * n * args.steps / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong",
+                "data": "synthetic", "dtype": "f32", "rows_per_rank": band.rows,
+                "halo_bytes_per_message": band.lat.halo_bytes(),
+                "gpu_launches": lbm.launch_count() - launches0}
+        print(json.dumps(line), flush=True)
+    band.close()
 
 
 def run_droplets_workload(args, world, rank, local):
@@ -623,9 +668,9 @@ def run_droplets_workload(args, world, rank, local):
 
 def run_stability_workload(args, world, rank, local):
     """Figs. 1, 2, 7: lowest stable T/Tc of a 200 x 200 droplet (r0 = 30, initial
-    interface width W = 3 by default, Maxwell densities, Tc = 0.094 as
-    printed) per scheme and tau, on a T/Tc ladder 0.95 .. 0.45 in steps of
-    0.01, in one batch."""
+    interface width W = 4 by default, Maxwell densities, Tc = 0.094 as
+    printed, started at rest: zero actual velocity) per scheme and tau, on a
+    T/Tc ladder 0.95 .. 0.45 in steps of 0.01, in one batch."""
     import json as _json
 
     import numpy as np
@@ -638,7 +683,8 @@ def run_stability_workload(args, world, rank, local):
     taus = (0.6, 0.7, 0.8, 0.9)
     temps = np.round(np.arange(0.95, 0.4499, -0.01), 2)
     inst = droplets.stability_instances(schemes, taus, temps)
-    res, info = droplets.run(inst, args.stability_steps, W=args.stability_width, tc_mode=1)
+    res, info = droplets.run(inst, args.stability_steps, W=args.stability_width, tc_mode=1,
+                             at_rest=True)
     th = droplets.thresholds(inst, res)
     names = {lbm.SC: "SC", lbm.EDM: "EDM", lbm.EDM_MOD: "EDM_Ce=1/tau",
              lbm.IMPROVED: "improved"}
@@ -652,6 +698,7 @@ def run_stability_workload(args, world, rank, local):
             "wall_s": info["wall"], "status": _status_counts(res),
             "criterion": f"diverged, or max |v| > {droplets.UNSTABLE_SPEED} after the budget",
             "initial_width": args.stability_width,
+            "initial_velocity": "at rest: u = -F/(2 rho), zero actual velocity (Table I)",
             "lowest_stable_T_over_Tc": [
                 {"scheme": names[s], "sigma": sg, "tau": tau, "T_min": t}
                 for (s, sg, tau), t in sorted(th.items())],
@@ -697,16 +744,18 @@ def main():
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--ref-side", type=int, default=1024)
     ap.add_argument("--workload", choices=("roofline", "sweep", "warmstart", "droplets",
-                                           "stability", "calibrate"), default="roofline")
+                                           "stability", "calibrate", "band"),
+                    default="roofline")
     ap.add_argument("--droplet-steps", type=int, default=20000)
     ap.add_argument("--stability-steps", type=int, default=20000)
-    ap.add_argument("--stability-width", type=float, default=3.0)
+    ap.add_argument("--stability-width", type=float, default=4.0)
     ap.add_argument("--sweep-instances", type=int, default=512)
     ap.add_argument("--seq-sample", type=int, default=32)
     ap.add_argument("--train-draws", type=int, default=11000)
     ap.add_argument("--epochs", type=int, default=1500)
     ap.add_argument("--held-out", type=int, default=256)
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-warmstart", action="store_true")
     ap.add_argument("--kernel-variant", choices=("auto", "register", "pair", "staged"),
                     default="auto", help="step kernel of the roofline run")
     args = ap.parse_args()
@@ -725,6 +774,8 @@ def main():
         run_stability_workload(args, world, rank, local)
     elif args.workload == "calibrate":
         run_calibrate_workload(args, world, rank, local)
+    elif args.workload == "band":
+        run_band_workload(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -104,12 +104,61 @@ void lbm_default_params(lbm_params *p);
  * On success *out owns the context (free it with lbm_destroy). */
 lbm_status lbm_create(const lbm_params *p, lbm_ctx **out);
 
+/* ---- domain decomposition in y (one band of rows per rank) ----------------
+ * A band context holds p->ny >= 2 rows of a larger lattice that is periodic
+ * in y, as one rank's share of a decomposition in y-slabs.  One time step of
+ * a row reads the post-collision populations of the rows one above and one
+ * below it (the pull of Eq. 1), and its force (Eq. 3) the density of those
+ * rows, which needs their pulls from the rows beyond: a band therefore keeps
+ * two ghost rows below and two above its own rows, refreshed between steps
+ * from the neighbouring bands' two boundary rows (all 9 populations, and for
+ * deviation storage the density plane).  Periodicity in y is that exchange
+ * (the band below rank 0 is the last rank's); x stays periodic in the band.
+ *   - lbm_init_density / lbm_init_density_at_rest take (p->ny + 4) x nx
+ *     densities: the band's rows with the two global rows below and above
+ *     them (wrapped), so that the first step needs no exchange;
+ *   - lbm_step / lbm_step_async advance one step per call (n <= 1; larger n
+ *     is LBM_E_INVAL); between calls the caller exchanges halos:
+ *     lbm_band_halo_pack, send / receive, lbm_band_halo_unpack;
+ *   - lbm_get_moments, lbm_get_mass and lbm_get_populations report the
+ *     owned rows only ([ny][nx], [9][ny][nx]); lbm_set_populations is
+ *     LBM_E_INVAL on a band.
+ * Each owned row evaluates exactly what the same row of the whole lattice
+ * does, so a decomposed run is bit-identical to an undecomposed one. */
+lbm_status lbm_create_band(const lbm_params *p, lbm_ctx **out);
+
+/* Bytes of one halo message of a band: 2 rows x nx x (9 populations of the
+ * storage type + 4 bytes of density plane for deviation storage).
+ * LBM_E_STATE for a context that is not a band. */
+lbm_status lbm_band_halo_bytes(const lbm_ctx *ctx, size_t *bytes);
+
+/* Queue on the context stream the copies of the band's two lowest owned rows
+ * into d_lo and its two highest into d_hi (caller-owned device buffers of
+ * lbm_band_halo_bytes each; layout [9][2][nx] populations then [2][nx]
+ * density plane): the messages for the band below and the band above.
+ * Returns without waiting. */
+lbm_status lbm_band_halo_pack(lbm_ctx *ctx, void *d_lo, void *d_hi);
+
+/* Queue the copies of the received messages into the ghost rows: d_below is
+ * the band below's d_hi, d_above the band above's d_lo.  Returns without
+ * waiting; the next step on the context stream reads them. */
+lbm_status lbm_band_halo_unpack(lbm_ctx *ctx, const void *d_below, const void *d_above);
+
 /* Set the state to f_a = f_eq(rho, u) (Eq. 2) at every cell.  rho is a host
  * array of ny*nx doubles; ux and uy may be NULL (zero velocity).  Copied to
  * the device during the call.  LBM_E_INVAL if any rho is outside the domain
  * of psi (rho <= 0, b rho / 4 >= 1 or a negative radicand in Eq. 8). */
 lbm_status lbm_init_density(lbm_ctx *ctx, const double *rho, const double *ux,
                             const double *uy);
+
+/* The same density at rest: f_a = f_eq(rho, u) (Eq. 2) with u = -F / (2 rho),
+ * F the interaction force of Eq. 3 evaluated (in FP64, on the device) on rho
+ * itself, so that the actual fluid velocity v = u + F / (2 rho) of Table I is
+ * zero at every cell.  Starting a smooth profile (Eq. 24 droplet, Eq. 36
+ * slab) from u = 0 instead gives its interfaces the velocity F / (2 rho) and
+ * an initial transient.  rho as for lbm_init_density (host, ny*nx doubles,
+ * copied); the same errors. */
+lbm_status lbm_init_density_at_rest(lbm_ctx *ctx, const double *rho);
 
 /* Advance n >= 0 time steps with the given scheme and relaxation time
  * tau > 1/2 (sigma is read by LBM_SCHEME_IMPROVED only).  Kernels are queued
@@ -240,8 +289,19 @@ enum { LBM_BATCH_AUTO = 0, LBM_BATCH_WORKLIST = 1, LBM_BATCH_PERSISTENT = 2,
  * max(tol, conv_rel * value) over two consecutive windows.  In FP32 the
  * interface position of a relaxed slab jitters by ~1e-4 cells per window
  * (rounding noise driving a nearly neutral mode), so CELL is met only by
- * some runs; COEX tests what a sweep reports. */
-enum { LBM_CONV_COEX = 0, LBM_CONV_CELL = 1, LBM_CONV_NONE = 2 /* run to max_steps */ };
+ * some runs; COEX tests what a sweep reports.  TREND: from the third
+ * window after a (re)start, each coexistence density is within
+ * max(tol, trend_tol * value) of its limit as estimated from its last two
+ * window-to-window changes: two changes of one sign, the later smaller, are
+ * a geometric decay with ratio r = d / d_prev and remaining distance
+ * |d| r / (1 - r); any other pair is noise (or oscillation) of amplitude
+ * |d| + |d_prev|.  COEX's floor sits at FP32 rounding noise, which keeps a
+ * settled slab running for tens of thousands of steps; TREND stops it once
+ * the answer is known to trend_tol, while a slow monotone drift (r near 1)
+ * keeps running.  The paper has no convergence test; this one serves the
+ * sweeps (steps to convergence, warm against cold starts). */
+enum { LBM_CONV_COEX = 0, LBM_CONV_CELL = 1, LBM_CONV_NONE = 2 /* run to max_steps */,
+       LBM_CONV_TREND = 3 };
 enum { LBM_RUN_ACTIVE = 0, LBM_RUN_CONVERGED = 1, LBM_RUN_DIVERGED = 2, LBM_RUN_CAPPED = 3 };
 
 typedef struct {
@@ -255,13 +315,15 @@ typedef struct {
   int mode;             /* LBM_BATCH_AUTO (window-level autotuning), _WORKLIST,
                            _PERSISTENT, _COOPERATIVE                           */
   int rows_per_item;    /* band height of a work-list item; 0 = autotuned      */
-  int conv;             /* LBM_CONV_COEX (default), _CELL or _NONE              */
+  int conv;             /* LBM_CONV_COEX (default), _CELL, _NONE or _TREND      */
   int variant;          /* LBM_VARIANT_AUTO (default) or _PAIR: two columns per
                            lane for even nx; _REGISTER: one column per lane for
                            every instance.  Results are identical.             */
   double conv_rel;      /* COEX: relative floor, changes below
                            max(tol, conv_rel * value) count as calm (8 * 2^-23
                            by default; must be >= 0)                           */
+  double trend_tol;     /* TREND: relative bound on the estimated distance of
+                           rho_g, rho_l to their limits (1e-4; >= 0)           */
 } lbm_batch_params;
 
 typedef struct {
@@ -286,7 +348,8 @@ typedef struct lbm_batch lbm_batch;
 
 /* Fill *p with the defaults named above (a = 1, b = 4, R = 1, G = -1, exact
  * Tc, window 1000, tol 1e-9, max_steps 200000, AUTO mode, COEX rule,
- * conv_rel 8 * 2^-23, AUTO variant, device 0, own stream).  NULL is ignored. */
+ * conv_rel 8 * 2^-23, trend_tol 1e-4, AUTO variant, device 0, own stream).
+ * NULL is ignored. */
 void lbm_batch_default_params(lbm_batch_params *p);
 
 /* Allocate a batch of `count` instances.  LBM_E_INVAL for count < 1 or any
@@ -299,6 +362,11 @@ lbm_status lbm_batch_create(const lbm_batch_params *p, const lbm_instance *inst,
  * that has run, it restarts it from rho (active again, convergence history
  * cleared) while its step count keeps the steps already spent. */
 lbm_status lbm_batch_init_density(lbm_batch *b, int i, const double *rho);
+
+/* The same with instance i at zero actual velocity: f = f_eq(rho, u), u =
+ * -F / (2 rho) from the Eq. 3 force on rho (Table I; see
+ * lbm_init_density_at_rest).  Same arguments, errors and restart rule. */
+lbm_status lbm_batch_init_density_at_rest(lbm_batch *b, int i, const double *rho);
 
 /* Every instance starts (all results reset) at rest from the flat-interface
  * profile of Eq. 36 built on the device: rho_g + (rho_l - rho_g)/2
@@ -391,8 +459,6 @@ lbm_status lbm_mlp_train(lbm_mlp *m, const float *X, const float *Y, int n,
 /* Y = network(X) for n samples. */
 lbm_status lbm_mlp_predict(lbm_mlp *m, const float *X, int n, float *Y);
 
-/* ---- allocation-free variant ------------------------------------------- */
-
 /* ---- self-test of the bounded device waits -------------------------------- */
 /* One warp on `device` waits, `polls` times (1 .. 2^20), on a shared-memory
  * mbarrier that nothing arrives on, gives up, records the timeout in a
@@ -413,21 +479,27 @@ lbm_status lbm_selftest_wait_timeout(int device, long long polls, int *result);
  * counterpart. */
 lbm_status lbm_selftest_grid_barrier_timeout(int device, int *result);
 
+/* ---- allocation-free variant ------------------------------------------- */
+
 /* FP64 sum of n FP32 values in device memory (for an FP32 population buffer
  * [9][ny][nx]: its total mass), written to the caller's device slot *d_out.
  * The paper has no counterpart: this is a deployment helper for callers that
  * cannot call cudaMalloc -- code whose device memory belongs to another
  * allocator (a framework's caching pool, a fixed budget) or that must not
  * block on an allocation.  It allocates nothing: its partial sums live in a
- * fixed 8 KB file-scope device array (1024 doubles), held by every GPU that
- * loads the library until exit.  Each block sums 2^20 values, so n may be at
- * most 1024 * 2^20 (= 2^30); larger n returns LBM_E_INVAL, as do NULL
- * pointers.  The first call on a device (the one current when called) looks
- * up the array's device address; make that first call before any stream
- * capture.  Kernels are queued on cuda_stream (NULL: the legacy default
- * stream) and the call returns without waiting.  Every call on a device
- * shares the array and overwrites what it uses (nothing needs clearing), so
- * calls whose kernels overlap on the GPU race: order them on one stream. */
+ * fixed 8 KB file-scope device array (1024 doubles, one per block), held by
+ * every GPU that loads the library until exit.  n may be at most 2^30; larger
+ * n returns LBM_E_INVAL, as do NULL pointers (n = 0 writes 0).  The blocks
+ * and their value ranges depend only on n, so the result is reproducible.
+ * The first call on a device (the one current when called) looks up the
+ * array's device address and keeps it for the life of the process; make
+ * that first call before any stream capture, and do not reset
+ * (cudaDeviceReset) a device this entry point has been used on -- the kept
+ * address would be stale.  Kernels are queued on cuda_stream (NULL: the
+ * legacy default stream) and the call returns without waiting.  Every call
+ * on a device shares the array and overwrites what it uses (nothing needs
+ * clearing), so calls whose kernels overlap on the GPU race: order them on
+ * one stream. */
 lbm_status lbm_mass_f32_noalloc(const float *d_values, size_t n, double *d_out,
                                 void *cuda_stream);
 

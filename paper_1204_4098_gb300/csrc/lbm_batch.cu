@@ -82,6 +82,9 @@ __device__ __forceinline__ StripArgs<StoreF32> inst_args(const BatchInst& I, con
   A.status = status;
   A.nx = I.nx;
   A.ny = I.ny;
+  A.y_begin = 0;
+  A.y_end = I.ny;
+  A.out_row0 = 0;
   A.n_strips = I.n_strips;
   A.band_rows = persistent ? I.pband_rows : I.band_rows;
   A.n_bands = persistent ? I.pn_bands : I.n_bands;
@@ -445,6 +448,7 @@ struct lbm_batch {
   int count = 0;
   std::vector<lbm_instance> inst;
   std::vector<BatchInst> desc;
+  std::vector<double> T;  // absolute temperature of each instance
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   float* buf[2] = {nullptr, nullptr};
@@ -469,7 +473,7 @@ struct lbm_batch {
   BatchOut* h_out = nullptr;
   unsigned* h_status = nullptr;
   std::vector<lbm_result> res;
-  std::vector<int> calm;     // consecutive windows meeting the COEX rule
+  std::vector<ConvState> conv;  // per-instance state of the convergence rule
   std::vector<char> fresh;   // (re)initialised since the last window
   std::vector<int> active;
   int sm_count = 0;
@@ -729,6 +733,7 @@ void lbm_batch_default_params(lbm_batch_params* p) {
   p->max_steps = 200000;
   p->mode = LBM_BATCH_AUTO;
   p->conv_rel = 8.0 * 1.1920928955078125e-7;  // 8 ulp of FP32
+  p->trend_tol = 1e-4;
 }
 
 lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, int count,
@@ -737,7 +742,8 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
   *out = nullptr;
   if (p->window < 2 || p->window % 2 || p->max_steps < 1 || !(p->tol >= 0) ||
       p->mode < LBM_BATCH_AUTO || p->mode > LBM_BATCH_COOPERATIVE || p->rows_per_item < 0 ||
-      p->conv < LBM_CONV_COEX || p->conv > LBM_CONV_NONE || !(p->conv_rel >= 0.0) ||
+      p->conv < LBM_CONV_COEX || p->conv > LBM_CONV_TREND || !(p->conv_rel >= 0.0) ||
+      !(p->trend_tol >= 0.0) ||
       !(p->variant == LBM_VARIANT_AUTO || p->variant == LBM_VARIANT_PAIR ||
         p->variant == LBM_VARIANT_REGISTER) ||
       !(p->G < 0) || !(p->a > 0) || !(p->b > 0) || !(p->R > 0) || p->tc_mode < 0 ||
@@ -776,6 +782,7 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
     d.scheme = s.scheme;
     d.row_off = roff;
     const double T = s.T_over_Tc * Tc;
+    b->T.push_back(T);
     d.P.RT = float(p->R * T);
     d.P.a = float(p->a);
     d.P.b4 = float(p->b / 4.0);
@@ -796,7 +803,7 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
   }
   b->tmp_cells = max_cells;
   b->res.assign(count, lbm_result{});
-  b->calm.assign(count, 0);
+  b->conv.assign(count, ConvState{});
   b->fresh.assign(count, 1);
   auto bail = [&](lbm_status st, const char* m) {
     lbm_batch_destroy(b);
@@ -922,7 +929,13 @@ lbm_status lbm_batch_destroy(lbm_batch* b) {
 
 const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str() : ""; }
 
-lbm_status lbm_batch_init_density(lbm_batch* b, int i, const double* rho) {
+}  // extern "C"
+
+namespace {
+
+// Instance i from f_eq(rho, u): u = 0, or at_rest the velocity of zero
+// actual velocity computed on the device (rest_velocity_launch).
+lbm_status batch_init_state(lbm_batch* b, int i, const double* rho, bool at_rest) {
   if (!b || !rho || i < 0 || i >= b->count) return bfail(b, LBM_E_INVAL, "bad argument");
   BDeviceGuard guard(b->p.device);
   const BatchInst& d = b->desc[i];
@@ -936,8 +949,17 @@ lbm_status lbm_batch_init_density(lbm_batch* b, int i, const double* rho) {
   chk.b4 = double(d.P.b4);
   chk.two_over_G = double(d.P.two_over_G);
   chk.status = b->d_status + i;
+  double *ux = nullptr, *uy = nullptr;
+  if (at_rest) {
+    ux = b->d_tmp + cells;
+    uy = b->d_tmp + 2 * cells;
+    LBM_BCUDA(b, rest_velocity_launch(b->d_tmp, d.nx, d.ny, b->p.R * b->T[i], b->p.a, b->p.b,
+                                      b->p.G, ux, uy, b->d_status + i, b->stream));
+    count_launches(1);
+    b->stats.launches += 1;
+  }
   LBM_BCUDA(b, set_state_launch(kFP32, b->buf[0] + d.off, nullptr, d.nx, d.ny, cells, b->d_tmp,
-                                nullptr, nullptr, nullptr, chk, b->stream));
+                                ux, uy, nullptr, chk, b->stream));
   to_float_kernel<<<256, 256, 0, b->stream>>>(b->d_tmp, b->snap + d.coff, cells);
   LBM_BCUDA(b, cudaGetLastError());
   count_launches(2);
@@ -954,7 +976,7 @@ lbm_status lbm_batch_init_density(lbm_batch* b, int i, const double* rho) {
   // a restart: the instance runs again from this state; its step count keeps
   // the steps already spent
   b->fresh[i] = 1;
-  b->calm[i] = 0;
+  b->conv[i] = ConvState{};
   b->res[i].status = LBM_RUN_ACTIVE;
   if (std::find(b->active.begin(), b->active.end(), i) == b->active.end()) {
     b->active.push_back(i);
@@ -963,6 +985,18 @@ lbm_status lbm_batch_init_density(lbm_batch* b, int i, const double* rho) {
   }
   b->initialized = true;
   return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_init_density(lbm_batch* b, int i, const double* rho) {
+  return batch_init_state(b, i, rho, false);
+}
+
+lbm_status lbm_batch_init_density_at_rest(lbm_batch* b, int i, const double* rho) {
+  return batch_init_state(b, i, rho, true);
 }
 
 lbm_status lbm_batch_init_slabs(lbm_batch* b, const double* rho_g, const double* rho_l,
@@ -998,7 +1032,7 @@ lbm_status lbm_batch_init_slabs(lbm_batch* b, const double* rho_g, const double*
     }
   for (int i = 0; i < b->count; ++i) {
     b->fresh[i] = 1;
-    b->calm[i] = 0;
+    b->conv[i] = ConvState{};
     b->res[i] = lbm_result{};
   }
   b->active.resize(b->count);
@@ -1062,7 +1096,8 @@ lbm_status lbm_batch_run(lbm_batch* b, int max_windows, int* n_active) {
     if (b->p.mode == LBM_BATCH_AUTO)
       b->tuner.record(mode, rows, ms * 1e6 / (double(cells) * b->p.window));
     std::vector<int> still;
-    const ConvRule rule{b->p.conv, b->p.tol, b->p.conv_rel, b->p.window, b->p.max_steps};
+    const ConvRule rule{b->p.conv,   b->p.tol,       b->p.conv_rel,
+                        b->p.window, b->p.max_steps, b->p.trend_tol};
     for (int i : b->active) {
       const BatchOut& o = b->h_out[i];
       WindowObs obs;
@@ -1077,7 +1112,7 @@ lbm_status lbm_batch_run(lbm_batch* b, int max_windows, int* n_active) {
       const bool first = b->fresh[i] != 0;
       b->fresh[i] = 0;
       lbm_result& r = b->res[i];
-      r.status = window_verdict(rule, obs, first, b->calm[i], r);
+      r.status = window_verdict(rule, obs, first, b->conv[i], r);
       if (r.status == LBM_RUN_ACTIVE) still.push_back(i);
     }
     b->active.swap(still);

@@ -162,35 +162,73 @@ struct WindowObs {
 };
 
 struct ConvRule {
-  int conv;         // LBM_CONV_COEX, _CELL or _NONE
+  int conv;         // LBM_CONV_COEX, _CELL, _NONE or _TREND
   double tol;       // density-change tolerance per window
   double conv_rel;  // COEX: relative floor
   int window;       // steps per window
   int max_steps;    // step cap
+  double trend_tol = 1e-4;  // TREND: relative bound on the distance to the limit
 };
 
+// Per-instance state of the convergence rules, reset by a (re)start.
+struct ConvState {
+  int calm = 0;       // COEX: consecutive calm windows
+  int windows = 0;    // windows since the last (re)start
+  double dg = 0.0;    // TREND: change of rho_g over the last window
+  double dl = 0.0;    //        and of rho_l
+};
+
+// TREND: estimated distance to the limit of a quantity that changed by d
+// over the last window and by d_prev over the one before.  Two changes of the
+// same sign, the later smaller, are taken as a geometric decay with ratio
+// r = d / d_prev, whose remaining distance is |d| r / (1 - r); anything else
+// (a sign change, a growing change) as noise or oscillation of amplitude
+// |d| + |d_prev|.
+inline double trend_remaining(double d, double d_prev) {
+  if (d * d_prev > 0.0 && std::fabs(d) < std::fabs(d_prev)) {
+    const double r = d / d_prev;
+    return std::fabs(d) * r / (1.0 - r);
+  }
+  return std::fabs(d) + std::fabs(d_prev);
+}
+
 // Apply one window to an instance's result: steps and observables are
-// updated, `calm` counts consecutive windows whose coexistence densities each
-// changed by less than max(tol, conv_rel * value) (never the first window
-// after a (re)start), and the new status is returned: DIVERGED (device flag or
-// a non-finite density) before CONVERGED (CELL: every cell within its
-// tolerance; COEX: two calm windows in a row; NONE: never) before CAPPED
-// (step cap reached) before ACTIVE.
-inline int window_verdict(const ConvRule& rule, const WindowObs& o, bool first, int& calm,
+// updated, the rule state advanced, and the new status returned: DIVERGED
+// (device flag or a non-finite density) before CONVERGED before CAPPED (step
+// cap reached) before ACTIVE.  CONVERGED means, by rule: CELL every cell
+// within its tolerance; COEX two calm windows in a row, a calm window being
+// one in which rho_g and rho_l each changed by less than max(tol, conv_rel
+// value) (never the first window after a (re)start); TREND, from the third
+// window after a (re)start on, both coexistence densities within
+// max(tol, trend_tol value) of their limits as trend_remaining estimates
+// them; NONE never.
+inline int window_verdict(const ConvRule& rule, const WindowObs& o, bool first, ConvState& st,
                           lbm_result& r) {
+  if (first) st = ConvState{};
+  st.windows += 1;
+  const double dg = first ? 0.0 : o.rho_g - r.rho_g;
+  const double dl = first ? 0.0 : o.rho_l - r.rho_l;
   const bool coex_calm =
       !first &&
-      std::fabs(o.rho_g - r.rho_g) < std::max(rule.tol, rule.conv_rel * std::fabs(o.rho_g)) &&
-      std::fabs(o.rho_l - r.rho_l) < std::max(rule.tol, rule.conv_rel * std::fabs(o.rho_l));
-  calm = coex_calm ? calm + 1 : 0;
+      std::fabs(dg) < std::max(rule.tol, rule.conv_rel * std::fabs(o.rho_g)) &&
+      std::fabs(dl) < std::max(rule.tol, rule.conv_rel * std::fabs(o.rho_l));
+  st.calm = coex_calm ? st.calm + 1 : 0;
+  const bool trend_settled =
+      st.windows >= 3 &&
+      trend_remaining(dg, st.dg) <= std::max(rule.tol, rule.trend_tol * std::fabs(o.rho_g)) &&
+      trend_remaining(dl, st.dl) <= std::max(rule.tol, rule.trend_tol * std::fabs(o.rho_l));
+  st.dg = dg;
+  st.dl = dl;
   r.steps += rule.window;
   r.rho_g = o.rho_g;
   r.rho_l = o.rho_l;
   r.width = o.width;
   r.mass = o.mass;
   r.max_drho = o.max_abs;
-  const bool converged = rule.conv == LBM_CONV_CELL ? o.max_dev < 1.0f
-                                                    : (rule.conv == LBM_CONV_COEX && calm >= 2);
+  bool converged = false;
+  if (rule.conv == LBM_CONV_CELL) converged = o.max_dev < 1.0f;
+  else if (rule.conv == LBM_CONV_COEX) converged = st.calm >= 2;
+  else if (rule.conv == LBM_CONV_TREND) converged = trend_settled;
   if (o.diverged || !o.finite) return LBM_RUN_DIVERGED;
   if (converged) return LBM_RUN_CONVERGED;
   if (r.steps >= rule.max_steps) return LBM_RUN_CAPPED;

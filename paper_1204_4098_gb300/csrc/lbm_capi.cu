@@ -11,10 +11,54 @@
 #include <string>
 
 #include "lbm.h"
+#include "lbm_device.cuh"
 #include "lbm_geometry.h"
 #include "lbm_internal.h"
 
 namespace lbm {
+
+// One thread per cell: psi (Eqs. 8, 23) of the cell and its eight
+// neighbours (periodic), the force of Eq. 3, and u = -F / (2 rho).
+__global__ void rest_velocity_kernel(const double* __restrict__ rho, int nx, int ny,
+                                     Phys<double> P, double* ux, double* uy, unsigned* status) {
+  const size_t plane = size_t(nx) * ny;
+  bool bad = false;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < plane;
+       i += size_t(gridDim.x) * blockDim.x) {
+    const int x = int(i % nx), y = int(i / nx);
+    double sx = 0.0, sy = 0.0;
+    for (int a = 1; a < kQ; ++a) {
+      const int xn = (x + ex_of(a) + nx) % nx, yn = (y + ey_of(a) + ny) % ny;
+      const double w = (ex_of(a) != 0 && ey_of(a) != 0) ? 1.0 / 12.0 : 1.0 / 3.0;
+      const double pn = psi_of_rho(rho[size_t(yn) * nx + xn], P, bad);
+      sx += w * pn * ex_of(a);
+      sy += w * pn * ey_of(a);
+    }
+    const double r = rho[i];
+    const double pc = psi_of_rho(r, P, bad);
+    const double Fx = P.minus_G * pc * sx, Fy = P.minus_G * pc * sy;
+    const bool ok = r > 0.0;
+    ux[i] = ok ? -Fx / (2.0 * r) : 0.0;
+    uy[i] = ok ? -Fy / (2.0 * r) : 0.0;
+  }
+  if (bad && status) atomicOr(status, kStatusInvalidInitFlag);
+}
+
+cudaError_t rest_velocity_launch(const double* rho, int nx, int ny, double RT, double a,
+                                 double b, double G, double* ux, double* uy, unsigned* status,
+                                 cudaStream_t s) {
+  Phys<double> P{};
+  P.RT = RT;
+  P.a = a;
+  P.b4 = b / 4.0;
+  P.two_over_G = 2.0 / G;
+  P.minus_G = -G;
+  size_t blocks = (size_t(nx) * ny + 255) / 256;
+  if (blocks > 65535u * 8u) blocks = 65535u * 8u;
+  rest_velocity_kernel<<<int(blocks < 1 ? 1 : blocks), 256, 0, s>>>(rho, nx, ny, P, ux, uy,
+                                                                    status);
+  return cudaGetLastError();
+}
 
 static std::atomic<unsigned long long> g_launches{0};
 void count_launches(unsigned long long n) { g_launches += n; }
@@ -49,10 +93,14 @@ cudaError_t get_state_f32(const void*, const float*, int, int, size_t, double*, 
 cudaError_t get_state_f64(const void*, const float*, int, int, size_t, double*, cudaStream_t);
 cudaError_t get_state_bf16(const void*, const float*, int, int, size_t, double*, cudaStream_t);
 cudaError_t get_state_f16(const void*, const float*, int, int, size_t, double*, cudaStream_t);
-cudaError_t mass_f32(const void*, const float*, size_t, double*, int, double*, cudaStream_t);
-cudaError_t mass_f64(const void*, const float*, size_t, double*, int, double*, cudaStream_t);
-cudaError_t mass_bf16(const void*, const float*, size_t, double*, int, double*, cudaStream_t);
-cudaError_t mass_f16(const void*, const float*, size_t, double*, int, double*, cudaStream_t);
+cudaError_t mass_f32(const void*, const float*, size_t, size_t, size_t, double*, int, double*,
+                     cudaStream_t);
+cudaError_t mass_f64(const void*, const float*, size_t, size_t, size_t, double*, int, double*,
+                     cudaStream_t);
+cudaError_t mass_bf16(const void*, const float*, size_t, size_t, size_t, double*, int, double*,
+                     cudaStream_t);
+cudaError_t mass_f16(const void*, const float*, size_t, size_t, size_t, double*, int, double*,
+                     cudaStream_t);
 
 cudaError_t strip_launch(int precision, int scheme, int mode, const StripLaunch& L, int grid,
                          cudaStream_t s) {
@@ -119,12 +167,13 @@ cudaError_t get_state_launch(int precision, const void* src, const float* rs, in
   return cudaErrorInvalidValue;
 }
 cudaError_t mass_launch(int precision, const void* src, const float* rs, size_t plane,
-                        double* partial, int n_partial, double* out, cudaStream_t s) {
+                        size_t first, size_t count, double* partial, int n_partial, double* out,
+                        cudaStream_t s) {
   switch (precision) {
-    case kFP32: return mass_f32(src, rs, plane, partial, n_partial, out, s);
-    case kFP64: return mass_f64(src, rs, plane, partial, n_partial, out, s);
-    case kBF16Dev: return mass_bf16(src, rs, plane, partial, n_partial, out, s);
-    case kFP16Dev: return mass_f16(src, rs, plane, partial, n_partial, out, s);
+    case kFP32: return mass_f32(src, rs, plane, first, count, partial, n_partial, out, s);
+    case kFP64: return mass_f64(src, rs, plane, first, count, partial, n_partial, out, s);
+    case kBF16Dev: return mass_bf16(src, rs, plane, first, count, partial, n_partial, out, s);
+    case kFP16Dev: return mass_f16(src, rs, plane, first, count, partial, n_partial, out, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -167,6 +216,13 @@ struct lbm_ctx {
   int band_rows_override = 0;
   double mrt[3] = {0.0, 0.0, 0.0};  // s_e, s_eps, s_q of the MRT scheme (<= 0: 1/tau)
   int variant = LBM_VARIANT_AUTO;
+  // A band of a y-decomposed lattice keeps kGhostRows ghost rows below and
+  // above its p.ny owned rows: ny_buf = p.ny + 2 kGhostRows rows in every
+  // buffer, owned rows from row0 = kGhostRows.  A whole lattice has
+  // ny_buf = p.ny and row0 = 0.
+  bool band = false;
+  int ny_buf = 0;
+  int row0 = 0;
   std::string err;
 };
 
@@ -211,7 +267,10 @@ EosCheck eos_check(lbm_ctx* c) {
 StripLaunch base_launch(lbm_ctx* c) {
   StripLaunch L{};
   L.nx = c->p.nx;
-  L.ny = c->p.ny;
+  L.ny = c->ny_buf;
+  L.y_begin = c->row0;
+  L.y_end = c->row0 + c->p.ny;
+  L.out_row0 = c->row0;
   L.plane = c->plane;
   L.status = c->d_status;
   L.RT = c->p.R * c->T;
@@ -273,6 +332,8 @@ lbm_status queue_steps(lbm_ctx* c, int n, int scheme, double tau, double sigma) 
   if (!(tau > 0.5) || !std::isfinite(tau)) return fail(c, LBM_E_INVAL, "tau must be > 1/2");
   if (!std::isfinite(sigma)) return fail(c, LBM_E_INVAL, "sigma must be finite");
   if (!c->initialized) return fail(c, LBM_E_STATE, "state not initialised");
+  if (c->band && n > 1)
+    return fail(c, LBM_E_INVAL, "a band advances one step per call (exchange halos between)");
   if (n == 0) return LBM_OK;
   StripLaunch L = base_launch(c);
   L.tau = tau;
@@ -327,6 +388,61 @@ T* mapped_view(T* host) {
 
 }  // namespace
 
+namespace {
+
+// f = f_eq(rho, u): u from the caller (ux, uy; NULL = 0) or, at_rest, the
+// velocity of zero actual velocity computed on the device.
+lbm_status init_state(lbm_ctx* c, const double* rho, const double* ux, const double* uy,
+                      bool at_rest) {
+  if (!c) return LBM_E_INVAL;
+  if (!rho) return fail(c, LBM_E_INVAL, "rho is NULL");
+  DeviceGuard guard(c->p.device);
+  lbm_status st = ensure_tmp(c, &c->d_tmp, 3 * c->plane);
+  if (st != LBM_OK) return st;
+  const size_t bytes = c->plane * sizeof(double);
+  // pinned inputs are read in place by the kernel; pageable ones are staged
+  const double* in[3] = {rho, ux, uy};
+  const double* dev[3] = {nullptr, nullptr, nullptr};
+  for (int k = 0; k < 3; ++k) {
+    if (!in[k]) continue;
+    dev[k] = mapped_view(in[k]);
+    if (!dev[k]) {
+      double* stage = c->d_tmp + k * c->plane;
+      LBM_CUDA(c, cudaMemcpyAsync(stage, in[k], bytes, cudaMemcpyHostToDevice, c->stream));
+      dev[k] = stage;
+    }
+  }
+  const double *d_rho = dev[0], *d_ux = dev[1], *d_uy = dev[2];
+  LBM_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream));
+  if (at_rest) {
+    double* vu = c->d_tmp + c->plane;
+    double* vv = c->d_tmp + 2 * c->plane;
+    LBM_CUDA(c, rest_velocity_launch(d_rho, c->p.nx, c->ny_buf, c->p.R * c->T, c->p.a, c->p.b,
+                                     c->p.G, vu, vv, c->d_status, c->stream));
+    count_launches(1);
+    d_ux = vu;
+    d_uy = vv;
+  }
+  LBM_CUDA(c, set_state_launch(c->p.precision, c->f[c->cur], c->rho[c->cur], c->p.nx, c->ny_buf,
+                               c->plane, d_rho, d_ux, d_uy, nullptr, eos_check(c), c->stream));
+  count_launches(1);
+  LBM_CUDA(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(unsigned),
+                              cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (*c->h_status & kStatusInvalidInitFlag) {
+    c->initialized = false;
+    cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream);
+    cudaStreamSynchronize(c->stream);
+    return fail(c, LBM_E_INVAL,
+                "rho outside the domain of psi (rho <= 0, b rho/4 >= 1 or negative radicand)");
+  }
+  c->initialized = true;
+  c->last_scheme = LBM_SCHEME_SC;
+  return LBM_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 void lbm_default_params(lbm_params* p) {
@@ -342,15 +458,26 @@ void lbm_default_params(lbm_params* p) {
   p->cuda_stream = nullptr;
 }
 
-lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
+}  // extern "C"
+
+namespace {
+
+constexpr int kGhostRows = 2;  // the pull reaches one row, the psi stencil one more
+
+lbm_status create_impl(const lbm_params* p, bool band, lbm_ctx** out) {
   g_create_error.clear();
   if (!p || !out) {
     g_create_error = "null argument";
     return LBM_E_INVAL;
   }
   *out = nullptr;
-  if (p->nx < 1 || p->ny < 1 || (long long)p->nx * p->ny > 0x7fffffffLL) {
+  const long long ny_buf = band ? (long long)p->ny + 2 * kGhostRows : p->ny;
+  if (p->nx < 1 || p->ny < 1 || (long long)p->nx * ny_buf > 0x7fffffffLL) {
     g_create_error = "nx, ny must be >= 1 with nx * ny < 2^31";
+    return LBM_E_INVAL;
+  }
+  if (band && p->ny < kGhostRows) {
+    g_create_error = "a band must own at least 2 rows";
     return LBM_E_INVAL;
   }
   if (!(p->T_over_Tc > 0.0) || !(p->G < 0.0) || !(p->b > 0.0) || !(p->R > 0.0) ||
@@ -384,7 +511,10 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
   lbm_ctx* c = new lbm_ctx();
   c->p = *p;
   c->T = p->T_over_Tc * Tc;
-  c->plane = (size_t)p->nx * p->ny;
+  c->band = band;
+  c->ny_buf = int(ny_buf);
+  c->row0 = band ? kGhostRows : 0;
+  c->plane = (size_t)p->nx * ny_buf;
   auto bail = [&](lbm_status st, const char* msg) {
     g_create_error = msg;
     lbm_destroy(c);
@@ -423,6 +553,16 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
   return LBM_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) { return create_impl(p, false, out); }
+
+lbm_status lbm_create_band(const lbm_params* p, lbm_ctx** out) {
+  return create_impl(p, true, out);
+}
+
 lbm_status lbm_destroy(lbm_ctx* c) {
   if (!c) return LBM_OK;
   DeviceGuard guard(c->p.device);
@@ -454,42 +594,11 @@ lbm_status lbm_get_temperature(const lbm_ctx* c, double* T) {
 
 lbm_status lbm_init_density(lbm_ctx* c, const double* rho, const double* ux,
                             const double* uy) {
-  if (!c) return LBM_E_INVAL;
-  if (!rho) return fail(c, LBM_E_INVAL, "rho is NULL");
-  DeviceGuard guard(c->p.device);
-  lbm_status st = ensure_tmp(c, &c->d_tmp, 3 * c->plane);
-  if (st != LBM_OK) return st;
-  const size_t bytes = c->plane * sizeof(double);
-  // pinned inputs are read in place by the kernel; pageable ones are staged
-  const double* in[3] = {rho, ux, uy};
-  const double* dev[3] = {nullptr, nullptr, nullptr};
-  for (int k = 0; k < 3; ++k) {
-    if (!in[k]) continue;
-    dev[k] = mapped_view(in[k]);
-    if (!dev[k]) {
-      double* stage = c->d_tmp + k * c->plane;
-      LBM_CUDA(c, cudaMemcpyAsync(stage, in[k], bytes, cudaMemcpyHostToDevice, c->stream));
-      dev[k] = stage;
-    }
-  }
-  const double *d_rho = dev[0], *d_ux = dev[1], *d_uy = dev[2];
-  LBM_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream));
-  LBM_CUDA(c, set_state_launch(c->p.precision, c->f[c->cur], c->rho[c->cur], c->p.nx, c->p.ny,
-                               c->plane, d_rho, d_ux, d_uy, nullptr, eos_check(c), c->stream));
-  count_launches(1);
-  LBM_CUDA(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(unsigned),
-                              cudaMemcpyDeviceToHost, c->stream));
-  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
-  if (*c->h_status & kStatusInvalidInitFlag) {
-    c->initialized = false;
-    cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream);
-    cudaStreamSynchronize(c->stream);
-    return fail(c, LBM_E_INVAL,
-                "rho outside the domain of psi (rho <= 0, b rho/4 >= 1 or negative radicand)");
-  }
-  c->initialized = true;
-  c->last_scheme = LBM_SCHEME_SC;
-  return LBM_OK;
+  return init_state(c, rho, ux, uy, false);
+}
+
+lbm_status lbm_init_density_at_rest(lbm_ctx* c, const double* rho) {
+  return init_state(c, rho, nullptr, nullptr, true);
 }
 
 lbm_status lbm_step_async(lbm_ctx* c, int n, int scheme, double tau, double sigma) {
@@ -552,7 +661,7 @@ lbm_status lbm_get_moments(lbm_ctx* c, double* rho, double* vx, double* vy) {
   else
     LBM_CUDA(c, strip_launch(c->p.precision, LBM_SCHEME_SC, mode, L, grid, c->stream));
   count_launches(1);
-  const size_t bytes = c->plane * sizeof(double);
+  const size_t bytes = (size_t)c->p.nx * c->p.ny * sizeof(double);  // owned rows
   for (int k = 0; k < 3; ++k)
     if (out[k] && staged[k])
       LBM_CUDA(c, cudaMemcpyAsync(out[k], dev[k], bytes, cudaMemcpyDeviceToHost, c->stream));
@@ -563,7 +672,8 @@ lbm_status lbm_get_mass(lbm_ctx* c, double* mass) {
   if (!c || !mass) return fail(c, LBM_E_INVAL, "null argument");
   if (!c->initialized) return fail(c, LBM_E_STATE, "state not initialised");
   DeviceGuard guard(c->p.device);
-  LBM_CUDA(c, mass_launch(c->p.precision, c->f[c->cur], c->rho[c->cur], c->plane, c->d_partial,
+  LBM_CUDA(c, mass_launch(c->p.precision, c->f[c->cur], c->rho[c->cur], c->plane,
+                          (size_t)c->row0 * c->p.nx, (size_t)c->p.ny * c->p.nx, c->d_partial,
                           c->n_partial, c->d_scalar, c->stream));
   count_launches(2);
   LBM_CUDA(c, cudaMemcpyAsync(mass, c->d_scalar, sizeof(double), cudaMemcpyDeviceToHost,
@@ -578,30 +688,103 @@ lbm_status lbm_get_populations(lbm_ctx* c, double* f) {
   DeviceGuard guard(c->p.device);
   lbm_status st = ensure_tmp(c, &c->d_pop, 9 * c->plane);
   if (st != LBM_OK) return st;
-  LBM_CUDA(c, get_state_launch(c->p.precision, c->f[c->cur], c->rho[c->cur], c->p.nx, c->p.ny,
-                               c->plane, c->d_pop, c->stream));
+  LBM_CUDA(c, get_state_launch(c->p.precision, c->f[c->cur], c->rho[c->cur], c->p.nx,
+                               c->ny_buf, c->plane, c->d_pop, c->stream));
   count_launches(1);
-  LBM_CUDA(c, cudaMemcpyAsync(f, c->d_pop, 9 * c->plane * sizeof(double),
-                              cudaMemcpyDeviceToHost, c->stream));
+  // owned rows of every plane: [9][ny][nx]
+  const size_t own = (size_t)c->p.nx * c->p.ny * sizeof(double);
+  LBM_CUDA(c, cudaMemcpy2DAsync(f, own, c->d_pop + (size_t)c->row0 * c->p.nx,
+                                c->plane * sizeof(double), own, 9, cudaMemcpyDeviceToHost,
+                                c->stream));
   LBM_CUDA(c, cudaStreamSynchronize(c->stream));
   return LBM_OK;
 }
 
 lbm_status lbm_set_populations(lbm_ctx* c, const double* f) {
   if (!c || !f) return fail(c, LBM_E_INVAL, "null argument");
+  if (c->band) return fail(c, LBM_E_INVAL, "a band is set from a density (init) only");
   DeviceGuard guard(c->p.device);
   lbm_status st = ensure_tmp(c, &c->d_pop, 9 * c->plane);
   if (st != LBM_OK) return st;
   LBM_CUDA(c, cudaMemcpyAsync(c->d_pop, f, 9 * c->plane * sizeof(double),
                               cudaMemcpyHostToDevice, c->stream));
-  LBM_CUDA(c, set_state_launch(c->p.precision, c->f[c->cur], c->rho[c->cur], c->p.nx, c->p.ny,
-                               c->plane, nullptr, nullptr, nullptr, c->d_pop, EosCheck{},
+  LBM_CUDA(c, set_state_launch(c->p.precision, c->f[c->cur], c->rho[c->cur], c->p.nx,
+                               c->ny_buf, c->plane, nullptr, nullptr, nullptr, c->d_pop, EosCheck{},
                                c->stream));
   count_launches(1);
   LBM_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream));
   LBM_CUDA(c, cudaStreamSynchronize(c->stream));
   c->initialized = true;
   return LBM_OK;
+}
+
+lbm_status lbm_band_halo_bytes(const lbm_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return LBM_E_INVAL;
+  if (!c->band) return LBM_E_STATE;
+  const size_t row = (size_t)c->p.nx;
+  *bytes = kGhostRows * row * (9 * storage_bytes(c->p.precision) + (c->rho[0] ? 4 : 0));
+  return LBM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Copy kGhostRows rows starting at buffer row `row` of the current state to
+// (to_msg) or from a packed message: [9][kGhostRows][nx] populations, then,
+// for deviation storage, [kGhostRows][nx] of the density plane.
+lbm_status halo_copy(lbm_ctx* c, int row, void* msg, bool to_msg) {
+  const size_t sb = storage_bytes(c->p.precision);
+  const size_t width = kGhostRows * (size_t)c->p.nx * sb;  // bytes of one plane's rows
+  char* buf = static_cast<char*>(c->f[c->cur]) + (size_t)row * c->p.nx * sb;
+  char* m = static_cast<char*>(msg);
+  const size_t pitch = c->plane * sb;
+  if (to_msg)
+    LBM_CUDA(c, cudaMemcpy2DAsync(m, width, buf, pitch, width, 9, cudaMemcpyDeviceToDevice,
+                                  c->stream));
+  else
+    LBM_CUDA(c, cudaMemcpy2DAsync(buf, pitch, m, width, width, 9, cudaMemcpyDeviceToDevice,
+                                  c->stream));
+  if (c->rho[c->cur]) {
+    float* r = c->rho[c->cur] + (size_t)row * c->p.nx;
+    char* mr = m + 9 * width;
+    const size_t rb = kGhostRows * (size_t)c->p.nx * sizeof(float);
+    if (to_msg)
+      LBM_CUDA(c, cudaMemcpyAsync(mr, r, rb, cudaMemcpyDeviceToDevice, c->stream));
+    else
+      LBM_CUDA(c, cudaMemcpyAsync(r, mr, rb, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  return LBM_OK;
+}
+
+lbm_status halo_check(lbm_ctx* c, const void* a, const void* b) {
+  if (!c) return LBM_E_INVAL;
+  if (!a || !b) return fail(c, LBM_E_INVAL, "null halo buffer");
+  if (!c->band) return fail(c, LBM_E_STATE, "not a band context");
+  if (!c->initialized) return fail(c, LBM_E_STATE, "state not initialised");
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_band_halo_pack(lbm_ctx* c, void* d_lo, void* d_hi) {
+  lbm_status st = halo_check(c, d_lo, d_hi);
+  if (st != LBM_OK) return st;
+  DeviceGuard guard(c->p.device);
+  st = halo_copy(c, c->row0, d_lo, true);  // the two lowest owned rows
+  if (st != LBM_OK) return st;
+  return halo_copy(c, c->row0 + c->p.ny - kGhostRows, d_hi, true);  // the two highest
+}
+
+lbm_status lbm_band_halo_unpack(lbm_ctx* c, const void* d_below, const void* d_above) {
+  lbm_status st = halo_check(c, d_below, d_above);
+  if (st != LBM_OK) return st;
+  DeviceGuard guard(c->p.device);
+  st = halo_copy(c, 0, const_cast<void*>(d_below), false);
+  if (st != LBM_OK) return st;
+  return halo_copy(c, c->row0 + c->p.ny, const_cast<void*>(d_above), false);
 }
 
 unsigned long long lbm_kernel_launch_count(void) { return g_launches.load(); }

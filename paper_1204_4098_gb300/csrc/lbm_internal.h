@@ -17,7 +17,9 @@ struct StripLaunch {
   double* out_vx;
   double* out_vy;
   unsigned* status;
-  int nx, ny;
+  int nx, ny;                  // ny: rows of the buffers
+  int y_begin, y_end;          // rows computed
+  int out_row0;                // observe mode: buffer row of output row 0
   int n_strips, band_rows, n_bands;
   size_t plane;
   // physics (converted to the compute type by each translation unit)
@@ -62,13 +64,22 @@ cudaError_t set_state_launch(int precision, void* dst, float* rho_dst, int nx, i
                              size_t plane, const double* rho, const double* ux,
                              const double* uy, const double* f_in, const EosCheck& chk,
                              cudaStream_t s);
+// u = -F / (2 rho) at every cell, F the force of Eq. 3 on the device density
+// field rho (FP64): the velocity whose equilibrium is at rest, i.e. has zero
+// actual velocity v = u + F / (2 rho) (Table I).  Cells outside the domain of
+// psi get u = 0 and set kStatusInvalidInitFlag in *status (if non-NULL).
+cudaError_t rest_velocity_launch(const double* rho, int nx, int ny, double RT, double a,
+                                 double b, double G, double* ux, double* uy, unsigned* status,
+                                 cudaStream_t s);
 // f_a(x, t) = f*_a(x - e_a) into f_out (FP64).
 cudaError_t get_state_launch(int precision, const void* src, const float* rho_src, int nx,
                              int ny, size_t plane, double* f_out, cudaStream_t s);
-// Sum of all populations in FP64: partial sums into `partial` (n_partial
-// doubles of scratch), then the total into *out (device pointer).
+// Sum of the populations of cells [first, first + count) of every plane in
+// FP64: partial sums into `partial` (n_partial doubles of scratch), then the
+// total into *out (device pointer).
 cudaError_t mass_launch(int precision, const void* src, const float* rho_src, size_t plane,
-                        double* partial, int n_partial, double* out, cudaStream_t s);
+                        size_t first, size_t count, double* partial, int n_partial,
+                        double* out, cudaStream_t s);
 
 size_t storage_bytes(int precision);  // bytes per population
 

@@ -50,10 +50,12 @@ struct StripArgs {
   double* out_vx;
   double* out_vy;
   unsigned* status;           // device status word
-  int nx, ny;
+  int nx, ny;                 // ny: rows of the buffers
+  int y_begin, y_end;         // rows computed (a domain band: the owned rows)
+  int out_row0;               // observe mode: output row of buffer row out_row0 is 0
   int n_strips;               // ceil(nx / 32)
   int band_rows;              // rows per warp
-  int n_bands;                // ceil(ny / band_rows)
+  int n_bands;                // ceil((y_end - y_begin) / band_rows)
   size_t plane;               // nx * ny
   Phys<typename S::C> P;
 };
@@ -90,8 +92,8 @@ __device__ __forceinline__ void strip_run(const StripArgs<S>& A, int strip, int 
                               (MODE == kModeStep && SCHEME == kNoForce));
   const unsigned FULL = 0xffffffffu;
   const int nx = A.nx, ny = A.ny;
-  const int y0 = band * A.band_rows;
-  const int y1 = min(y0 + A.band_rows, ny);
+  const int y0 = A.y_begin + band * A.band_rows;
+  const int y1 = min(y0 + A.band_rows, A.y_end);
 
   const int x = strip * 32 + lane;
   const bool active = x < nx;
@@ -184,8 +186,9 @@ __device__ __forceinline__ void strip_run(const StripArgs<S>& A, int strip, int 
     }
 
     const int idx = y * nx + c;
+    const int oidx = (y - A.out_row0) * nx + c;
     if constexpr (MODE == kModeStep) {
-      collide<C, SCHEME>(Pcur, rho0, Fx, Fy, Cz, A.P);
+      collide<SCHEME>(Pcur, rho0, Fx, Fy, Cz, A.P);
       if (active) {
         if constexpr (S::kDev) {
           // the density plane absorbs the 16-bit rounding of the deviations,
@@ -193,7 +196,7 @@ __device__ __forceinline__ void strip_run(const StripArgs<S>& A, int strip, int 
           C resid = rho0;
 #pragma unroll
           for (int a = 0; a < kQ; ++a) {
-            const typename S::T d = S::from_c(sub_rn(Pcur[a], mul_rn(w_of<C>(a), rho0)));
+            const typename S::T d = S::from_c(fma_rn(-w_of<C>(a), rho0, Pcur[a]));
             A.dst[a * A.plane + idx] = d;
             resid = sub_rn(resid, S::to_c(d));
           }
@@ -208,9 +211,9 @@ __device__ __forceinline__ void strip_run(const StripArgs<S>& A, int strip, int 
         const C jx = (Pcur[1] - Pcur[3]) + (Pcur[5] - Pcur[6]) + (Pcur[8] - Pcur[7]);
         const C jy = (Pcur[2] - Pcur[4]) + (Pcur[5] + Pcur[6]) - (Pcur[7] + Pcur[8]);
         const double r = double(rho0);
-        A.out_rho[idx] = r;
-        A.out_vx[idx] = (double(jx) + 0.5 * double(Fx)) / r;
-        A.out_vy[idx] = (double(jy) + 0.5 * double(Fy)) / r;
+        A.out_rho[oidx] = r;
+        A.out_vx[oidx] = (double(jx) + 0.5 * double(Fx)) / r;
+        A.out_vy[oidx] = (double(jy) + 0.5 * double(Fy)) / r;
       }
     }
     Wm = Wz; Cm = Cz; Em = Ez;
@@ -295,12 +298,13 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
   using C = typename S::C;
   using T = typename S::T;
   using V = typename Vec2<T>::type;
+  using P2 = Pair<C>;  // the lane's two cells (columns ca, ca + 1)
   constexpr bool kNeedPsi = !(MODE == kModeObserveNoForce ||
                               (MODE == kModeStep && SCHEME == kNoForce));
   const unsigned FULL = 0xffffffffu;
   const int nx = A.nx, ny = A.ny;
-  const int y0 = band * A.band_rows;
-  const int y1 = min(y0 + A.band_rows, ny);
+  const int y0 = A.y_begin + band * A.band_rows;
+  const int y1 = min(y0 + A.band_rows, A.y_end);
   const int x0 = strip * 64;
   const int xa = x0 + 2 * lane;         // left column of this lane
   const bool active_a = xa < nx, active_b = xa + 1 < nx;
@@ -339,6 +343,11 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
     C h;
     float2 rr[3];
   };
+  // Deviation storage: rows are fetched in sequence (y0 - 1, y0, y0 + 1, ...),
+  // and row y needs the density plane of rows y - 1, y, y + 1, so the planes
+  // of the last fetch's rows y and y + 1 are kept (ring) and one row is loaded.
+  float2 ring0 = make_float2(0.f, 0.f), ring1 = make_float2(0.f, 0.f);
+  bool ring_ok = false;
   auto fetch_row = [&](int y, Raw& R) {
     const int ym = y == 0 ? ny - 1 : y - 1;
     const int yp = y == ny - 1 ? 0 : y + 1;
@@ -349,10 +358,20 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
       R.h = qlane ? pull_one<S, kCoherent>(A, qa, qy * nx + qsx) : C(0);
     }
     if constexpr (S::kDev) {
-#pragma unroll
-      for (int j = 0; j < 3; ++j)
-        R.rr[j] = load2<kCoherent>(
-            reinterpret_cast<const float2*>(A.rho_src + size_t(rows[j]) * nx + ca));
+      auto plane_row = [&](int r) {
+        return load2<kCoherent>(reinterpret_cast<const float2*>(A.rho_src + size_t(r) * nx + ca));
+      };
+      if (ring_ok) {  // warp-uniform
+        R.rr[0] = ring0;
+        R.rr[1] = ring1;
+      } else {
+        R.rr[0] = plane_row(rows[0]);
+        R.rr[1] = plane_row(rows[1]);
+        ring_ok = true;
+      }
+      R.rr[2] = plane_row(rows[2]);
+      ring0 = R.rr[1];
+      ring1 = R.rr[2];
     }
 #pragma unroll
     for (int a = 0; a < kQ; ++a) {
@@ -361,152 +380,146 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
           load2<kCoherent>(reinterpret_cast<const V*>(A.src + a * A.plane + size_t(r) * nx + ca));
     }
   };
-  auto assemble = [&](const Raw& R, C (&PA)[kQ], C (&PB)[kQ], C& h) {
+  // pulled populations of the lane's two cells (P[a].x at ca, .y at ca + 1)
+  auto assemble = [&](const Raw& R, P2 (&P)[kQ], C& h) {
     h = R.h;
 #pragma unroll
     for (int a = 0; a < kQ; ++a) {
       const int ex = ex_of(a), ey = ey_of(a);
-      C lo, hi;  // pulled values at ca, ca + 1
+      P2 v;  // the two values loaded at ca, ca + 1
       if constexpr (S::kDev) {
-        const float2 d = S::to_c2(R.v[a]);
-        lo = fma_rn(w_of<C>(a), C(R.rr[1 - ey].x), d.x);
-        hi = fma_rn(w_of<C>(a), C(R.rr[1 - ey].y), d.y);
+        v = fma_rn(P2(w_of<C>(a)), P2(R.rr[1 - ey]), P2(S::to_c2(R.v[a])));
       } else {
-        lo = S::to_c(R.v[a].x);
-        hi = S::to_c(R.v[a].y);
+        v = P2(S::to_c(R.v[a].x), S::to_c(R.v[a].y));
       }
       if (ex == 0) {
-        PA[a] = lo;
-        PB[a] = hi;
+        P[a] = v;
       } else if (ex == 1) {  // sources x-1: (prev lane's upper, own lower)
         const int k = a == 1 ? 9 : (a == 5 ? 10 : 11);
         const C fromL = __shfl_sync(FULL, h, k);
-        const C up = __shfl_up_sync(FULL, hi, 1);
-        PA[a] = lane == 0 ? fromL : up;
-        PB[a] = lo;
+        const C up = __shfl_up_sync(FULL, v.y(), 1);
+        P[a] = P2(lane == 0 ? fromL : up, v.x());
       } else {  // sources x+1: (own upper, next lane's lower)
         const int k = a == 3 ? 25 : (a == 6 ? 26 : 27);
         const C fromR = __shfl_sync(FULL, h, k);
-        const C dn = __shfl_down_sync(FULL, lo, 1);
-        PA[a] = hi;
-        PB[a] = lane == 31 ? fromR : dn;
+        const C dn = __shfl_down_sync(FULL, v.x(), 1);
+        P[a] = P2(v.y(), lane == 31 ? fromR : dn);
       }
     }
   };
-  auto load_row = [&](int y, C (&PA)[kQ], C (&PB)[kQ], C& h) {
+  auto load_row = [&](int y, P2 (&P)[kQ], C& h) {
     Raw R;
     fetch_row(y, R);
-    assemble(R, PA, PB, h);
+    assemble(R, P, h);
   };
-  auto rho_of = [](const C (&P)[kQ]) {
-    C r = P[0];
+  auto rho_of = [](const P2 (&P)[kQ]) {
+    P2 r = P[0];
 #pragma unroll
     for (int a = 1; a < kQ; ++a) r = add_rn(r, P[a]);
     return r;
   };
-  // psi of the row's cells; Wa = psi(xa - 1), Eb = psi(xa + 2)
-  auto psi_row = [&](const C (&PA)[kQ], const C (&PB)[kQ], C h, C& Wa, C& Ca, C& Cb, C& Eb,
-                     C& ra, C& rb) {
-    ra = rho_of(PA);
-    rb = rho_of(PB);
+  // psi of a row around the lane's cells: Cc = (psi(ca), psi(ca + 1)),
+  // Wc = (psi(ca - 1), psi(ca)), Ec = (psi(ca + 1), psi(ca + 2))
+  auto psi_row = [&](const P2 (&P)[kQ], C h, P2& Wc, P2& Cc, P2& Ec, P2& r) {
+    r = rho_of(P);
     if constexpr (kNeedPsi) {
-      Ca = psi_of_rho(ra, A.P, bad);
-      Cb = psi_of_rho(rb, A.P, bad);
+      Cc = psi_of_rho(r, A.P, bad);
       C hr = __shfl_sync(FULL, h, hbase);
 #pragma unroll
       for (int a = 1; a < kQ; ++a) hr = add_rn(hr, __shfl_sync(FULL, h, hbase + a));
       const C hp = psi_of_rho(hr, A.P, bad);
-      Wa = __shfl_up_sync(FULL, Cb, 1);
-      Eb = __shfl_down_sync(FULL, Ca, 1);
-      if (lane == 0) Wa = hp;
-      if (lane == 31) Eb = hp;
+      C w = __shfl_up_sync(FULL, Cc.y(), 1);
+      C e = __shfl_down_sync(FULL, Cc.x(), 1);
+      if (lane == 0) w = hp;
+      if (lane == 31) e = hp;
+      Wc = P2(w, Cc.x());
+      Ec = P2(Cc.y(), e);
     }
   };
-  auto force = [&](C Wm, C Cm, C Em, C Wz, C Cz, C Ez, C Wp, C Cp, C Ep, C& Fx, C& Fy) {
-    const C third = C(1) / C(3), twelfth = C(1) / C(12);
-    const C sx = fma_rn(third, sub_rn(Ez, Wz),
-                        mul_rn(twelfth, add_rn(sub_rn(Ep, Wp), sub_rn(Em, Wm))));
-    const C sy = fma_rn(third, sub_rn(Cp, Cm),
-                        mul_rn(twelfth, sub_rn(add_rn(Ep, Wp), add_rn(Em, Wm))));
-    const C gpsi = mul_rn(A.P.minus_G, Cz);
+  // Eq. 3: F = -G psi(x) sum_a w(|e_a|^2) psi(x + e_a) e_a for both cells
+  auto force = [&](P2 Wm, P2 Cm, P2 Em, P2 Wz, P2 Cz, P2 Ez, P2 Wp, P2 Cp, P2 Ep, P2& Fx,
+                   P2& Fy) {
+    const P2 third = P2(C(1) / C(3)), twelfth = P2(C(1) / C(12));
+    const P2 sx = fma_rn(third, sub_rn(Ez, Wz),
+                         mul_rn(twelfth, add_rn(sub_rn(Ep, Wp), sub_rn(Em, Wm))));
+    const P2 sy = fma_rn(third, sub_rn(Cp, Cm),
+                         mul_rn(twelfth, sub_rn(add_rn(Ep, Wp), add_rn(Em, Wm))));
+    const P2 gpsi = mul_rn(P2(A.P.minus_G), Cz);
     Fx = mul_rn(gpsi, sx);
     Fy = mul_rn(gpsi, sy);
   };
 
-  C PA0[kQ], PB0[kQ], PA1[kQ], PB1[kQ];
+  P2 P0[kQ], P1[kQ];
   C h1 = C(0);
-  // psi ring per row: (Wa, Ca, Cb, Eb) for rows y-1 (m), y (z)
-  C Wam = 0, Cam = 0, Cbm = 0, Ebm = 0, Waz = 0, Caz = 0, Cbz = 0, Ebz = 0;
-  C ra0, rb0;
+  // psi ring: rows y-1 (m), y (z)
+  P2 Wm = P2(C(0)), Cm = P2(C(0)), Em = P2(C(0)), Wz = P2(C(0)), Cz = P2(C(0)), Ez = P2(C(0));
+  P2 r0;
   {
-    C rda, rdb;
-    load_row(y0 == 0 ? ny - 1 : y0 - 1, PA0, PB0, h1);
-    psi_row(PA0, PB0, h1, Wam, Cam, Cbm, Ebm, rda, rdb);
-    load_row(y0, PA0, PB0, h1);
-    psi_row(PA0, PB0, h1, Waz, Caz, Cbz, Ebz, ra0, rb0);
-    load_row(y0 + 1 == ny ? 0 : y0 + 1, PA1, PB1, h1);
+    P2 rd;
+    load_row(y0 == 0 ? ny - 1 : y0 - 1, P0, h1);
+    psi_row(P0, h1, Wm, Cm, Em, rd);
+    load_row(y0, P0, h1);
+    psi_row(P0, h1, Wz, Cz, Ez, r0);
+    load_row(y0 + 1 == ny ? 0 : y0 + 1, P1, h1);
   }
   Raw next;
   for (int y = y0; y < y1; ++y) {
     const bool more = y + 2 <= y1;
     if (more) fetch_row(y + 2 >= ny ? y + 2 - ny : y + 2, next);
-    C Wap = 0, Cap = 0, Cbp = 0, Ebp = 0, ra1, rb1;
-    psi_row(PA1, PB1, h1, Wap, Cap, Cbp, Ebp, ra1, rb1);
-    C Fxa = C(0), Fya = C(0), Fxb = C(0), Fyb = C(0);
-    if constexpr (kNeedPsi) {
-      force(Wam, Cam, Cbm, Waz, Caz, Cbz, Wap, Cap, Cbp, Fxa, Fya);
-      force(Cam, Cbm, Ebm, Caz, Cbz, Ebz, Cap, Cbp, Ebp, Fxb, Fyb);
-    }
+    P2 Wp = P2(C(0)), Cp = P2(C(0)), Ep = P2(C(0)), r1;
+    psi_row(P1, h1, Wp, Cp, Ep, r1);
+    P2 Fx = P2(C(0)), Fy = P2(C(0));
+    if constexpr (kNeedPsi) force(Wm, Cm, Em, Wz, Cz, Ez, Wp, Cp, Ep, Fx, Fy);
     const size_t idx = size_t(y) * nx + ca;
     if constexpr (MODE == kModeStep) {
-      collide<C, SCHEME>(PA0, ra0, Fxa, Fya, Caz, A.P);
-      collide<C, SCHEME>(PB0, rb0, Fxb, Fyb, Cbz, A.P);
+      collide<SCHEME>(P0, r0, Fx, Fy, Cz, A.P);
       if (active_a) {  // nx even: both cells of an active lane are inside
         if constexpr (S::kDev) {
           // the density plane absorbs the 16-bit rounding of the deviations
-          C resa = ra0, resb = rb0;
+          P2 res = r0;
 #pragma unroll
           for (int a = 0; a < kQ; ++a) {
-            const V v = S::from_c2(sub_rn(PA0[a], mul_rn(w_of<C>(a), ra0)),
-                                   sub_rn(PB0[a], mul_rn(w_of<C>(a), rb0)));
+            const P2 d = fma_rn(P2(-w_of<C>(a)), r0, P0[a]);
+            const V v = S::from_c2(d.x(), d.y());
             *reinterpret_cast<V*>(A.dst + a * A.plane + idx) = v;
-            const float2 d = S::to_c2(v);
-            resa = sub_rn(resa, d.x);
-            resb = sub_rn(resb, d.y);
+            res = sub_rn(res, P2(S::to_c2(v)));
           }
-          *reinterpret_cast<float2*>(A.rho_dst + idx) = make_float2(float(resa), float(resb));
+          *reinterpret_cast<float2*>(A.rho_dst + idx) = make_float2(float(res.x()), float(res.y()));
         } else {
 #pragma unroll
           for (int a = 0; a < kQ; ++a) {
             V v;
-            v.x = S::from_c(PA0[a]);
-            v.y = S::from_c(PB0[a]);
+            v.x = S::from_c(P0[a].x());
+            v.y = S::from_c(P0[a].y());
             *reinterpret_cast<V*>(A.dst + a * A.plane + idx) = v;
           }
         }
       }
     } else {
-      auto out = [&](const C (&P)[kQ], C r0, C Fx, C Fy, size_t i) {
-        const C jx = (P[1] - P[3]) + (P[5] - P[6]) + (P[8] - P[7]);
-        const C jy = (P[2] - P[4]) + (P[5] + P[6]) - (P[7] + P[8]);
-        const double r = double(r0);
+      auto out = [&](C p0, C p1, C p2, C p3, C p4, C p5, C p6, C p7, C p8, C rr, C fx, C fy,
+                     size_t i) {
+        const C jx = (p1 - p3) + (p5 - p6) + (p8 - p7);
+        const C jy = (p2 - p4) + (p5 + p6) - (p7 + p8);
+        (void)p0;
+        const double r = double(rr);
         A.out_rho[i] = r;
-        A.out_vx[i] = (double(jx) + 0.5 * double(Fx)) / r;
-        A.out_vy[i] = (double(jy) + 0.5 * double(Fy)) / r;
+        A.out_vx[i] = (double(jx) + 0.5 * double(fx)) / r;
+        A.out_vy[i] = (double(jy) + 0.5 * double(fy)) / r;
       };
-      if (active_a) out(PA0, ra0, Fxa, Fya, idx);
-      if (active_b) out(PB0, rb0, Fxb, Fyb, idx + 1);
+      const size_t oidx = size_t(y - A.out_row0) * nx + ca;
+      if (active_a)
+        out(P0[0].x(), P0[1].x(), P0[2].x(), P0[3].x(), P0[4].x(), P0[5].x(), P0[6].x(),
+            P0[7].x(), P0[8].x(), r0.x(), Fx.x(), Fy.x(), oidx);
+      if (active_b)
+        out(P0[0].y(), P0[1].y(), P0[2].y(), P0[3].y(), P0[4].y(), P0[5].y(), P0[6].y(),
+            P0[7].y(), P0[8].y(), r0.y(), Fx.y(), Fy.y(), oidx + 1);
     }
-    Wam = Waz; Cam = Caz; Cbm = Cbz; Ebm = Ebz;
-    Waz = Wap; Caz = Cap; Cbz = Cbp; Ebz = Ebp;
-    ra0 = ra1;
-    rb0 = rb1;
+    Wm = Wz; Cm = Cz; Em = Ez;
+    Wz = Wp; Cz = Cp; Ez = Ep;
+    r0 = r1;
 #pragma unroll
-    for (int a = 0; a < kQ; ++a) {
-      PA0[a] = PA1[a];
-      PB0[a] = PB1[a];
-    }
-    if (more) assemble(next, PA1, PB1, h1);  // warp-uniform
+    for (int a = 0; a < kQ; ++a) P0[a] = P1[a];
+    if (more) assemble(next, P1, h1);  // warp-uniform
   }
   if (__any_sync(FULL, bad) && lane == 0) atomicOr(A.status, kStatusDiverged);
 }
@@ -593,8 +606,8 @@ strip_tma_kernel(const StripArgs<StoreF32> A) {
   const int band = gwarp / A.n_strips;
   if (band >= A.n_bands) return;  // warp-uniform
   const int nx = A.nx, ny = A.ny;
-  const int y0 = band * A.band_rows;
-  const int y1 = min(y0 + A.band_rows, ny);
+  const int y0 = A.y_begin + band * A.band_rows;
+  const int y1 = min(y0 + A.band_rows, A.y_end);
   const int x0 = strip * 32;
   const bool active = x0 + lane < nx;
   float(*stage)[kQ][kTmaSpan] = s_stage[wib];
@@ -719,7 +732,7 @@ strip_tma_kernel(const StripArgs<StoreF32> A) {
       Fx = mul_rn(gpsi, sx);
       Fy = mul_rn(gpsi, sy);
     }
-    collide<C, SCHEME>(Pcur, rho0, Fx, Fy, Cz, A.P);
+    collide<SCHEME>(Pcur, rho0, Fx, Fy, Cz, A.P);
     if (active) {
       const int idx = y * nx + x0 + lane;
 #pragma unroll
@@ -832,11 +845,11 @@ __device__ __forceinline__ double block_sum(double v, double* smem) {
 
 template <class S>
 __global__ void __launch_bounds__(kReduceThreads)
-mass_partial_kernel(const typename S::T* src, const float* rho_src, size_t plane,
-                    double* partial) {
+mass_partial_kernel(const typename S::T* src, const float* rho_src, size_t plane, size_t first,
+                    size_t count, double* partial) {
   __shared__ double smem[kReduceThreads / 32];
   double acc = 0.0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < plane;
+  for (size_t i = first + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < first + count;
        i += (size_t)gridDim.x * blockDim.x) {
     double cell = 0.0;
 #pragma unroll

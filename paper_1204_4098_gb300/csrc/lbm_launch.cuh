@@ -22,6 +22,9 @@ StripArgs<S> make_args(const StripLaunch& L) {
   A.status = L.status;
   A.nx = L.nx;
   A.ny = L.ny;
+  A.y_begin = L.y_begin;
+  A.y_end = L.y_end;
+  A.out_row0 = L.out_row0;
   A.n_strips = L.n_strips;
   A.band_rows = L.band_rows;
   A.n_bands = L.n_bands;
@@ -204,10 +207,10 @@ cudaError_t get_state_t(const void* src, const float* rho_src, int nx, int ny, s
 }
 
 template <class S>
-cudaError_t mass_t(const void* src, const float* rho_src, size_t plane, double* partial,
-                   int n_partial, double* out, cudaStream_t s) {
+cudaError_t mass_t(const void* src, const float* rho_src, size_t plane, size_t first,
+                   size_t count, double* partial, int n_partial, double* out, cudaStream_t s) {
   mass_partial_kernel<S><<<n_partial, kReduceThreads, 0, s>>>(
-      static_cast<const typename S::T*>(src), rho_src, plane, partial);
+      static_cast<const typename S::T*>(src), rho_src, plane, first, count, partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   sum_partials_kernel<<<1, kReduceThreads, 0, s>>>(partial, n_partial, out);
@@ -250,9 +253,9 @@ cudaError_t mass_t(const void* src, const float* rho_src, size_t plane, double* 
                                  size_t plane, double* f_out, cudaStream_t s) {         \
     return get_state_t<STORE>(src, rs, nx, ny, plane, f_out, s);                        \
   }                                                                                     \
-  cudaError_t mass_##SUFFIX(const void* src, const float* rs, size_t plane,              \
-                            double* partial, int n_partial, double* out,               \
+  cudaError_t mass_##SUFFIX(const void* src, const float* rs, size_t plane, size_t first, \
+                            size_t count, double* partial, int n_partial, double* out,  \
                             cudaStream_t s) {                                           \
-    return mass_t<STORE>(src, rs, plane, partial, n_partial, out, s);                   \
+    return mass_t<STORE>(src, rs, plane, first, count, partial, n_partial, out, s);      \
   }                                                                                     \
   }

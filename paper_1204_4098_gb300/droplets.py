@@ -14,9 +14,11 @@ profile, liquid inside, periodic lattice):
   velocity exceeds 0.3 at the end of the budget.  Runs that fail do so in the
   first ~50 steps, while the initial profile relaxes, so the thresholds of
   the improved scheme and of EDM with C_e = 1/tau depend on the initial
-  interface width W, which the paper does not give; W = 3 reproduces the
-  printed thresholds best (those of Shan-Chen, EDM and Guo's scheme do not
-  move between W = 2 and 5).
+  state, which the paper does not give.  Started at rest -- zero actual
+  velocity v = u + F/(2 rho) (Table I), i.e. u = -F/(2 rho) -- with width
+  W = 4, the thresholds printed for the improved scheme, Shan-Chen and both
+  EDM forms at tau = 0.7 are reproduced; from u = 0 the interface starts
+  with the velocity F/(2 rho) and the improved scheme fails up to 0.67.
 
 Observables (cell-index coordinates, centre (nx/2, ny/2)): rho_in = density
 at the centre cell, rho_out = density at the corner (0, 0), R =
@@ -62,18 +64,28 @@ def laplace_instances(n=256, radii=(20, 30, 40, 50), temps=(0.6, 0.7, 0.8, 0.9),
             for t, tau, (s, sg), r in itertools.product(temps, taus, schemes, radii)]
 
 
-def run(instances, steps, W=5.0, tc_mode=0, window=1000, device=0, mode=lbm.BATCH_AUTO):
+def run(instances, steps, W=5.0, tc_mode=0, window=1000, device=0, mode=lbm.BATCH_AUTO,
+        at_rest=False, densities=None):
     """Every instance from the Eq. 24 droplet at the Maxwell densities of its
-    temperature, at rest, for `steps` steps (no convergence stop) on one
-    batch.  Returns (results, info): results carry the status and, for runs
-    that did not diverge, the observables."""
+    temperature (or `densities[k]` = (rho_g, rho_l)) for `steps` steps (no
+    convergence stop) on one batch.  The initial velocity is u = 0, or with
+    `at_rest` the one of zero actual velocity (u = -F/(2 rho), Table I).
+    Returns (results, info): results carry the status and, for runs that did
+    not diverge, the observables."""
     tc = lbm.critical_point()[1] if tc_mode == 0 else 0.094
     t0 = time.perf_counter()
     with lbm.Batch(instances, window=window, tol=0.0, max_steps=steps, conv=lbm.CONV_NONE,
                    tc_mode=tc_mode, device=device, mode=mode) as b:
         for k, d in enumerate(instances):
-            rg, rl, _ = lbm.maxwell(d["T_over_Tc"] * tc)
-            b.init_density(k, inputs.droplet(d["nx"], d["ny"], rg, rl, d["r0"], W=W))
+            if densities is None:
+                rg, rl, _ = lbm.maxwell(d["T_over_Tc"] * tc)
+            else:
+                rg, rl = densities[k]
+            rho = inputs.droplet(d["nx"], d["ny"], rg, rl, d["r0"], W=W)
+            if at_rest:
+                b.init_density_at_rest(k, rho)
+            else:
+                b.init_density(k, rho)
         b.run()
         stats = b.stats()
         res = []

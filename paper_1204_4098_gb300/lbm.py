@@ -46,7 +46,8 @@ class lbm_batch_params(ctypes.Structure):
                 ("cuda_stream", ctypes.c_void_p), ("window", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_steps", ctypes.c_int), ("mode", ctypes.c_int),
                 ("rows_per_item", ctypes.c_int), ("conv", ctypes.c_int),
-                ("variant", ctypes.c_int), ("conv_rel", ctypes.c_double)]
+                ("variant", ctypes.c_int), ("conv_rel", ctypes.c_double),
+                ("trend_tol", ctypes.c_double)]
 
 
 class lbm_result(ctypes.Structure):
@@ -62,7 +63,7 @@ class lbm_batch_stats(ctypes.Structure):
 
 
 BATCH_AUTO, BATCH_WORKLIST, BATCH_PERSISTENT, BATCH_COOPERATIVE = range(4)
-CONV_COEX, CONV_CELL, CONV_NONE = range(3)
+CONV_COEX, CONV_CELL, CONV_NONE, CONV_TREND = range(4)
 RUN_ACTIVE, RUN_CONVERGED, RUN_DIVERGED, RUN_CAPPED = range(4)
 
 
@@ -83,6 +84,11 @@ SIGNATURES = {
     "lbm_default_params": (None, [ctypes.POINTER(lbm_params)]),
     "lbm_create": (_I, [ctypes.POINTER(lbm_params), ctypes.POINTER(_P)]),
     "lbm_init_density": (_I, [_P, _P, _P, _P]),
+    "lbm_init_density_at_rest": (_I, [_P, _P]),
+    "lbm_create_band": (_I, [_P, _P]),
+    "lbm_band_halo_bytes": (_I, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "lbm_band_halo_pack": (_I, [_P, _P, _P]),
+    "lbm_band_halo_unpack": (_I, [_P, _P, _P]),
     "lbm_step": (_I, [_P, _I, _I, _D, _D]),
     "lbm_step_async": (_I, [_P, _I, _I, _D, _D]),
     "lbm_sync_status": (_I, [_P]),
@@ -108,6 +114,7 @@ SIGNATURES = {
     "lbm_batch_create": (_I, [ctypes.POINTER(lbm_batch_params), ctypes.POINTER(lbm_instance),
                               _I, ctypes.POINTER(_P)]),
     "lbm_batch_init_density": (_I, [_P, _I, _P]),
+    "lbm_batch_init_density_at_rest": (_I, [_P, _I, _P]),
     "lbm_batch_init_slabs": (_I, [_P, _P, _P, _P]),
     "lbm_batch_run": (_I, [_P, _I, _IP]),
     "lbm_batch_get_result": (_I, [_P, _I, ctypes.POINTER(lbm_result)]),
@@ -216,7 +223,9 @@ class Lattice:
     """A context of the C ABI with numpy in/out (same life cycle as lbm_*)."""
 
     def __init__(self, nx, ny, T_over_Tc, precision=FP32, tc_mode=0, a=1.0, b=4.0,
-                 R=1.0, G=-1.0, device=0, stream=None):
+                 R=1.0, G=-1.0, device=0, stream=None, band=False):
+        """band=True: ny rows of a y-decomposed lattice (lbm_create_band); its
+        initial densities then have ny + 4 rows (two halo rows each side)."""
         p = lbm_params()
         lib().lbm_default_params(ctypes.byref(p))
         p.nx, p.ny, p.T_over_Tc, p.tc_mode = int(nx), int(ny), float(T_over_Tc), int(tc_mode)
@@ -224,12 +233,30 @@ class Lattice:
         p.precision, p.device = int(precision), int(device)
         p.cuda_stream = None if stream is None else ctypes.c_void_p(int(stream))
         ctx = _P()
-        st = lib().lbm_create(ctypes.byref(p), ctypes.byref(ctx))
+        create = lib().lbm_create_band if band else lib().lbm_create
+        st = create(ctypes.byref(p), ctypes.byref(ctx))
         if st:
             raise LbmError(st, lib().lbm_last_error(None).decode())
         self.ctx = ctx
         self.nx, self.ny = int(nx), int(ny)
         self.precision = precision
+        self.band = bool(band)
+        self.init_rows = self.ny + 4 if band else self.ny
+
+    def halo_bytes(self):
+        n = ctypes.c_size_t()
+        self._check(lib().lbm_band_halo_bytes(self.ctx, ctypes.byref(n)), "lbm_band_halo_bytes")
+        return n.value
+
+    def halo_pack(self, d_lo, d_hi):
+        """Queue the copies of the two lowest / highest owned rows into the
+        device buffers at addresses d_lo, d_hi."""
+        self._check(lib().lbm_band_halo_pack(self.ctx, _P(int(d_lo)), _P(int(d_hi))),
+                    "lbm_band_halo_pack")
+
+    def halo_unpack(self, d_below, d_above):
+        self._check(lib().lbm_band_halo_unpack(self.ctx, _P(int(d_below)), _P(int(d_above))),
+                    "lbm_band_halo_unpack")
 
     def _check(self, st, what):
         if st:
@@ -262,9 +289,16 @@ class Lattice:
         rho = np.ascontiguousarray(rho, dtype=np.float64)
         ux = None if ux is None else np.ascontiguousarray(ux, dtype=np.float64)
         uy = None if uy is None else np.ascontiguousarray(uy, dtype=np.float64)
-        assert rho.shape == (self.ny, self.nx)
+        assert rho.shape == (self.init_rows, self.nx)
         self._check(lib().lbm_init_density(self.ctx, _dptr(rho), _dptr(ux), _dptr(uy)),
                     "lbm_init_density")
+
+    def init_density_at_rest(self, rho):
+        """f = f_eq(rho, u) with u = -F / (2 rho): zero actual velocity."""
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        assert rho.shape == (self.init_rows, self.nx)
+        self._check(lib().lbm_init_density_at_rest(self.ctx, _dptr(rho)),
+                    "lbm_init_density_at_rest")
 
     def step(self, n, scheme, tau, sigma=0.0, raise_on_error=True):
         st = lib().lbm_step(self.ctx, int(n), int(scheme), float(tau), float(sigma))
@@ -340,13 +374,15 @@ class Batch:
 
     def __init__(self, instances, window=1000, tol=1e-9, max_steps=200000, mode=BATCH_AUTO,
                  rows_per_item=0, tc_mode=0, device=0, stream=None, conv=CONV_COEX,
-                 variant=VARIANT_AUTO, conv_rel=None):
+                 variant=VARIANT_AUTO, conv_rel=None, trend_tol=None):
         p = lbm_batch_params()
         lib().lbm_batch_default_params(ctypes.byref(p))
         p.window, p.tol, p.max_steps, p.conv = int(window), float(tol), int(max_steps), int(conv)
         p.variant = int(variant)
         if conv_rel is not None:
             p.conv_rel = float(conv_rel)
+        if trend_tol is not None:
+            p.trend_tol = float(trend_tol)
         p.mode, p.rows_per_item, p.tc_mode, p.device = int(mode), int(rows_per_item), \
             int(tc_mode), int(device)
         p.cuda_stream = None if stream is None else ctypes.c_void_p(int(stream))
@@ -392,6 +428,14 @@ class Batch:
         assert rho.shape == (d["ny"], d["nx"])
         self._check(lib().lbm_batch_init_density(self.h, int(i), _dptr(rho)),
                     "lbm_batch_init_density")
+
+    def init_density_at_rest(self, i, rho):
+        """Instance i from rho at zero actual velocity (u = -F / (2 rho))."""
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        d = self.instances[i]
+        assert rho.shape == (d["ny"], d["nx"])
+        self._check(lib().lbm_batch_init_density_at_rest(self.h, int(i), _dptr(rho)),
+                    "lbm_batch_init_density_at_rest")
 
     def init_slabs(self, rho_g, rho_l, width):
         g, l, w = (np.ascontiguousarray(v, dtype=np.float64) for v in (rho_g, rho_l, width))

@@ -33,13 +33,13 @@ def cold_start_profiles(instances, tc_mode=0):
 
 def run_batched(instances, rho_g, rho_l, width, window=1000, tol=1e-9, max_steps=200000,
                 mode=lbm.BATCH_AUTO, rows_per_item=0, device=0, stream=None,
-                conv=lbm.CONV_COEX, conv_rel=None):
+                conv=lbm.CONV_COEX, conv_rel=None, trend_tol=None):
     """Run every instance to convergence in one batch; returns (results, stats,
     wall seconds).  width <= 0 starts from a sharp slab."""
     t0 = time.perf_counter()
     with lbm.Batch(instances, window=window, tol=tol, max_steps=max_steps, mode=mode,
                    rows_per_item=rows_per_item, device=device, stream=stream,
-                   conv=conv, conv_rel=conv_rel) as b:
+                   conv=conv, conv_rel=conv_rel, trend_tol=trend_tol) as b:
         b.init_slabs(rho_g, rho_l, width)
         b.run()
         res, stats = b.results(), b.stats()
@@ -89,24 +89,51 @@ def _coexistence(rho):
 
 
 COEX_REL = 8 * F32_EPS  # the batch engine's default relative floor
+TREND_TOL = 1e-4        # the batch engine's default TREND bound
 
 
 def _calm(new, old, tol, rel=COEX_REL):
     return abs(new - old) < max(tol, rel * abs(new))
 
 
-def window_status(conv, c, prev_c, calm, cell, finite, steps, tol, max_steps, rel=COEX_REL):
+def trend_remaining(d, d_prev):
+    """Estimated distance to the limit from the last two window changes: a
+    geometric decay (same sign, shrinking: r = d / d_prev) has |d| r / (1 - r)
+    left; any other pair is noise of amplitude |d| + |d_prev|."""
+    if d * d_prev > 0.0 and abs(d) < abs(d_prev):
+        r = d / d_prev
+        return abs(d) * r / (1.0 - r)
+    return abs(d) + abs(d_prev)
+
+
+def _settled(c, prev_c, prev2_c, tol, trend_tol):
+    return all(trend_remaining(c[i] - prev_c[i], prev_c[i] - prev2_c[i])
+               <= max(tol, trend_tol * abs(c[i])) for i in (0, 1))
+
+
+def window_status(conv, c, prev_c, calm, cell, finite, steps, tol, max_steps, rel=COEX_REL,
+                  prev2_c=None, trend_tol=TREND_TOL):
     """The batch engine's rule after one window, for runs checked on the host:
-    c and prev_c are (rho_g, rho_l) now and one window earlier (prev_c None
-    for the first window after a start, which is never calm); calm counts
-    consecutive windows in which both changed by less than max(tol, rel value);
-    cell says every cell changed by less than its tolerance.  Returns
-    (status, calm): DIVERGED (a non-finite density) before CONVERGED (CELL:
-    cell; COEX: two calm windows in a row; NONE: never) before CAPPED (steps
-    reached max_steps) before ACTIVE."""
+    c, prev_c and prev2_c are (rho_g, rho_l) now, one and two windows earlier
+    (None when that window precedes the last start, which makes the first
+    window never calm and TREND wait for its third); calm counts consecutive
+    windows in which both changed by less than max(tol, rel value); cell says
+    every cell changed by less than its tolerance.  Returns (status, calm):
+    DIVERGED (a non-finite density) before CONVERGED (CELL: cell; COEX: two
+    calm windows in a row; TREND: both densities within max(tol, trend_tol
+    value) of their limit as trend_remaining estimates it; NONE: never)
+    before CAPPED (steps reached max_steps) before ACTIVE."""
     calm = calm + 1 if (prev_c is not None and _calm(c[0], prev_c[0], tol, rel)
                         and _calm(c[1], prev_c[1], tol, rel)) else 0
-    converged = cell if conv == lbm.CONV_CELL else (conv == lbm.CONV_COEX and calm >= 2)
+    if conv == lbm.CONV_CELL:
+        converged = cell
+    elif conv == lbm.CONV_COEX:
+        converged = calm >= 2
+    elif conv == lbm.CONV_TREND:
+        converged = prev_c is not None and prev2_c is not None and \
+            _settled(c, prev_c, prev2_c, tol, trend_tol)
+    else:
+        converged = False
     if not finite:
         return lbm.RUN_DIVERGED, calm
     if converged:
@@ -117,14 +144,18 @@ def window_status(conv, c, prev_c, calm, cell, finite, steps, tol, max_steps, re
 
 
 def run_sequential(instances, rho_g, rho_l, width, window=1000, tol=1e-9, max_steps=200000,
-                   device=0, conv=lbm.CONV_COEX, conv_rel=None):
+                   device=0, conv=lbm.CONV_COEX, conv_rel=None, trend_tol=None):
     """Plain runs, one instance after another, through lbm_step; convergence
     is checked on the host with the batch engine's rule (window_status:
     CONV_COEX: rho_g and rho_l each changed by less than max(tol, conv_rel
     value) over two consecutive windows; CONV_CELL: every cell by less than
-    max(tol, 8 eps_32 rho) over a window; CONV_NONE: run to max_steps).
+    max(tol, 8 eps_32 rho) over a window; CONV_TREND: both within
+    max(tol, trend_tol value) of their extrapolated limits; CONV_NONE: run to
+    max_steps).  A smooth profile (width > 0) starts at rest (zero actual
+    velocity), a sharp one at u = 0, as in the batch engine's init_slabs.
     Returns (results, wall seconds)."""
     rel = COEX_REL if conv_rel is None else conv_rel
+    ttol = TREND_TOL if trend_tol is None else trend_tol
     out = []
     t0 = time.perf_counter()
     for k, d in enumerate(instances):
@@ -136,9 +167,12 @@ def run_sequential(instances, rho_g, rho_l, width, window=1000, tol=1e-9, max_st
         else:
             rho0 = inputs.slab_step(nx, ny, rho_g[k], rho_l[k])
         with lbm.Lattice(nx, ny, d["T_over_Tc"], precision=lbm.FP32, device=device) as lat:
-            lat.init_density(rho0)
+            if width[k] > 0 and d["scheme"] != lbm.NOFORCE:
+                lat.init_density_at_rest(rho0)
+            else:
+                lat.init_density(rho0)
             prev = lat.observe()[0]
-            prev_c = None
+            prev_c = prev2_c = None
             steps, status, calm = 0, lbm.RUN_ACTIVE, 0
             while status == lbm.RUN_ACTIVE:
                 st = lat.step(window, d["scheme"], d["tau"], d.get("sigma", 0.0),
@@ -152,8 +186,8 @@ def run_sequential(instances, rho_g, rho_l, width, window=1000, tol=1e-9, max_st
                 cell = np.all(np.abs(rho - prev) < np.maximum(tol, 8 * F32_EPS * np.abs(rho)))
                 status, calm = window_status(conv, c, prev_c, calm, cell,
                                              bool(np.all(np.isfinite(rho))), steps, tol,
-                                             max_steps, rel)
-                prev, prev_c = rho, c
+                                             max_steps, rel, prev2_c, ttol)
+                prev, prev_c, prev2_c = rho, c, prev_c
                 history.append((steps, c[0], c[1], len(history)))
             g, l = _coexistence(prev) if status != lbm.RUN_DIVERGED else (np.nan, np.nan)
         out.append(dict(status=status, steps=steps, rho_g=g, rho_l=l, history=history,

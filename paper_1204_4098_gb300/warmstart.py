@@ -5,15 +5,18 @@ library's kernels) maps a sweep point (T/Tc, tau, sigma, scheme) to the
 relaxed slab's (rho_l, rho_g, interface width W).  New runs then start from
 the Eq. 36 profile with the predicted values instead of the Maxwell step
 (cold start).  Fallback: a warm run that diverges restarts cold, and so
-does one whose prediction error exceeds 1e-2 -- its rho_l or rho_g differs
-from the prediction by more than 1e-2 (relative) -- checked after its first
-window (default), when it has converged, or not at all (run_warm's
-`fallback`); the steps already spent are counted.  (After the first window
-the interface relaxing from the initial tanh profile still moves the bulk
-densities by ~0.5-1 % even when the prediction is right to 1e-3, so the
-first-window check also restarts some good predictions; it is the cheapest
-point to restart.)  Cold runs remain the reference for the error: the tests and
-the sweep report compare warm and cold coexistence densities.
+does one whose prediction error exceeds 1e-2 -- the limits of its rho_l or
+rho_g, extrapolated from its first three windows (extrapolated_limit),
+differ from the prediction by more than 1e-2 (relative); the steps already
+spent are counted.  (The bulk densities themselves are still moved by
+~0.5-1 % in the first window while the interface relaxes from the initial
+tanh profile, even when the prediction is right to 1e-3, so comparing them
+directly restarts good predictions too; run_warm's `fallback` keeps that
+rule, the check at convergence and divergence-only for comparison.)  Warm
+and cold runs stop by the same batch rule, TREND by default: both
+coexistence densities within 1e-4 of their extrapolated limits.  Cold runs
+remain the reference for the error: the tests and the sweep report compare
+warm and cold coexistence densities.
 
 Inputs are scaled to [-1, 1] over the sweep ranges.  The network learns
 the answer relative to the Maxwell construction at the same temperature
@@ -75,14 +78,15 @@ def targets(instances, rho_l, rho_g, width):
 
 
 def training_data(n_draws, seed=40, ny_range=(128, 512), max_steps=100000, window=1000,
-                  conv_rel=None):
+                  conv_rel=None, conv=lbm.CONV_TREND, trend_tol=None):
     """Cold batched runs of narrow (nx = 32) slabs drawn from the sweep
     distribution; the converged ones give (features, targets).  Slabs are
     x-invariant, so the width of the lattice does not change the answer."""
     inst = inputs.sweep_instances(n_draws, seed=seed, nx_range=(32, 32), ny_range=ny_range)
     g, l = sweep.cold_start_profiles(inst)
     res, stats, wall = sweep.run_batched(inst, g, l, np.zeros(len(inst)), window=window,
-                                         max_steps=max_steps, conv_rel=conv_rel)
+                                         max_steps=max_steps, conv=conv, conv_rel=conv_rel,
+                                         trend_tol=trend_tol)
     keep = [k for k, r in enumerate(res)
             if r["status"] == lbm.RUN_CONVERGED and r["rho_g"] > 0 and r["width"] > 0]
     kept = [inst[k] for k in keep]
@@ -108,7 +112,27 @@ def train(X, Y, stages=((1500, 2e-3), (1500, 5e-4), (1500, 1e-4)), batch=128, se
     return WarmStartModel(mlp, mean, std, loss, time.perf_counter() - t0)
 
 
-FALLBACK_RULES = ("first_window", "converged", "diverged")
+FALLBACK_RULES = ("trend", "first_window", "converged", "diverged")
+
+
+def extrapolated_limit(history):
+    """(rho_g, rho_l) limits estimated from a run's last three window values
+    (history rows (steps, rho_g, rho_l, window)): with d and d_prev the last
+    two changes, a geometric decay (same sign, shrinking) ends
+    sweep.trend_remaining(d, d_prev) further on in the direction of d; any
+    other pair leaves the last value."""
+    out = []
+    for col in (1, 2):
+        q = [h[col] for h in history[-3:]]
+        if len(q) < 3:
+            out.append(q[-1])
+            continue
+        d, d_prev = q[2] - q[1], q[1] - q[0]
+        if d * d_prev > 0.0 and abs(d) < abs(d_prev):
+            out.append(q[2] + np.sign(d) * sweep.trend_remaining(d, d_prev))
+        else:
+            out.append(q[2])
+    return out[0], out[1]
 
 
 def needs_fallback(rule, status, windows_run, fell, rho_l, rho_g, pred_l, pred_g, tol):
@@ -116,31 +140,40 @@ def needs_fallback(rule, status, windows_run, fell, rho_l, rho_g, pred_l, pred_g
     run falls back at most once (`fell`: it already has), always when it has
     diverged, and otherwise when the prediction-error check of `rule` is due
     and rho_l or rho_g differs from its prediction by more than `tol`
-    (relative): after the run's first window ("first_window"), when it has
-    converged ("converged"), or never ("diverged")."""
+    (relative): at the run's third window, with rho_l, rho_g the limits
+    extrapolated from its trend ("trend"; the caller passes them), after its
+    first window ("first_window"), when it has converged ("converged"), or
+    never ("diverged")."""
     if fell:
         return False
     if status == lbm.RUN_DIVERGED:
         return True
     off = abs(rho_l / pred_l - 1) > tol or abs(rho_g / pred_g - 1) > tol
     due = (rule == "converged" and status == lbm.RUN_CONVERGED) or \
-        (rule == "first_window" and windows_run == 1)
+        (rule == "first_window" and windows_run == 1) or \
+        (rule == "trend" and (windows_run == 3 or
+                              (windows_run < 3 and status == lbm.RUN_CONVERGED)))
     return due and off
 
 
 def run_warm(instances, model, window=1000, tol=1e-9, max_steps=200000, fallback_tol=1e-2,
-             device=0, conv_rel=None, fallback="first_window"):
+             device=0, conv_rel=None, fallback="trend", conv=lbm.CONV_TREND, trend_tol=None):
     """Warm-started batched runs with the cold-start fallback, checked after
     every window.  A warm run that diverges restarts at once from the cold
     start (its steps so far are counted; a run falls back at most once).  The
     prediction-error check (relative difference of rho_l or rho_g from the
     prediction above fallback_tol) is taken, by `fallback`:
-      "first_window" -- after the first window (default: a restart then
-                        wastes one window);
+      "trend"        -- at the third window, against the limits
+                        extrapolated from the run's trend (default: the
+                        relaxing interface still moves the bulk densities
+                        by ~1 % in the first window, not their limits);
+      "first_window" -- after the first window (a restart then wastes one
+                        window);
       "converged"    -- when the warm run has converged;
       "diverged"     -- never (divergence only).
     Returns (results, info); results carry per-window histories of the run
-    that produced the answer."""
+    that produced the answer.  Runs stop by the batch rule `conv` (TREND by
+    default, the same for the cold runs they are compared with)."""
     if fallback not in FALLBACK_RULES:
         raise ValueError(f"unknown fallback rule {fallback!r}")
     pl, pg, pw = model.predict(instances)
@@ -156,7 +189,7 @@ def run_warm(instances, model, window=1000, tol=1e-9, max_steps=200000, fallback
     times = []
     fell = set()
     with lbm.Batch(instances, window=window, tol=tol, max_steps=max_steps, device=device,
-                   conv_rel=conv_rel) as b:
+                   conv=conv, conv_rel=conv_rel, trend_tol=trend_tol) as b:
         b.init_slabs(pg, pl, pw)
         active = set(range(n))
         while active:
@@ -165,8 +198,11 @@ def run_warm(instances, model, window=1000, tol=1e-9, max_steps=200000, fallback
             for k in list(active):
                 r = b.result(k)
                 hist[k].append((r["steps"], r["rho_g"], r["rho_l"], len(times) - 1))
-                if needs_fallback(fallback, r["status"], len(hist[k]), k in fell, r["rho_l"],
-                                  r["rho_g"], pl[k], pg[k], fallback_tol):
+                el, eg = r["rho_l"], r["rho_g"]
+                if fallback == "trend":
+                    eg, el = extrapolated_limit(hist[k])
+                if needs_fallback(fallback, r["status"], len(hist[k]), k in fell, el, eg,
+                                  pl[k], pg[k], fallback_tol):
                     d = instances[k]
                     fell.add(k)
                     hist[k] = []
@@ -182,11 +218,11 @@ def run_warm(instances, model, window=1000, tol=1e-9, max_steps=200000, fallback
 
 
 def run_cold_batched(instances, window=1000, tol=1e-9, max_steps=200000, device=0,
-                     conv_rel=None):
+                     conv_rel=None, conv=lbm.CONV_TREND, trend_tol=None):
     cg, cl = sweep.cold_start_profiles(instances)
     t0 = time.perf_counter()
     with lbm.Batch(instances, window=window, tol=tol, max_steps=max_steps, device=device,
-                   conv_rel=conv_rel) as b:
+                   conv=conv, conv_rel=conv_rel, trend_tol=trend_tol) as b:
         b.init_slabs(cg, cl, np.zeros(len(instances)))
         hist, times = sweep.run_batch_with_history(b)
         res, stats = b.results(), b.stats()

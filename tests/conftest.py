@@ -44,5 +44,9 @@ def host_shim(tmp_path_factory):
     D = ctypes.c_double
     lib.shim_window_verdict.argtypes = [I, D, D, I, I, ctypes.POINTER(D), I, I, I, IP,
                                         ctypes.c_void_p]
+    lib.shim_window_verdict_trend.argtypes = [D, D, I, I, ctypes.POINTER(D), I,
+                                              ctypes.POINTER(D), ctypes.c_void_p]
+    lib.shim_trend_remaining.argtypes = [D, D]
+    lib.shim_trend_remaining.restype = D
     lib.shim_strip_geometry.argtypes = [I, I, I, ctypes.c_longlong, I, I, IP]
     return lib

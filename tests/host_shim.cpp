@@ -58,8 +58,43 @@ int shim_window_verdict(int conv, double tol, double conv_rel, int window, int m
   o.finite = finite != 0;
   o.diverged = diverged != 0;
   const lbm::ConvRule rule{conv, tol, conv_rel, window, max_steps};
-  return lbm::window_verdict(rule, o, first != 0, *calm, *r);
+  lbm::ConvState st;
+  st.calm = *calm;
+  st.windows = first ? 0 : 1;
+  const int v = lbm::window_verdict(rule, o, first != 0, st, *r);
+  *calm = st.calm;
+  return v;
 }
+
+// The TREND rule with its state carried by the caller in state[4] =
+// {calm, windows, dg, dl}; obs as above.
+int shim_window_verdict_trend(double tol, double trend_tol, int window, int max_steps,
+                              const double* obs, int first, double* state, lbm_result* r) {
+  lbm::WindowObs o;
+  o.rho_g = obs[0];
+  o.rho_l = obs[1];
+  o.width = obs[2];
+  o.mass = obs[3];
+  o.max_abs = obs[4];
+  o.max_dev = float(obs[5]);
+  o.finite = true;
+  o.diverged = false;
+  lbm::ConvRule rule{LBM_CONV_TREND, tol, 0.0, window, max_steps};
+  rule.trend_tol = trend_tol;
+  lbm::ConvState st;
+  st.calm = int(state[0]);
+  st.windows = int(state[1]);
+  st.dg = state[2];
+  st.dl = state[3];
+  const int v = lbm::window_verdict(rule, o, first != 0, st, *r);
+  state[0] = st.calm;
+  state[1] = st.windows;
+  state[2] = st.dg;
+  state[3] = st.dl;
+  return v;
+}
+
+double shim_trend_remaining(double d, double d_prev) { return lbm::trend_remaining(d, d_prev); }
 
 int shim_resolve_variant(int requested, int precision, int nx, int ny, int sm_count, int step) {
   return lbm::resolve_variant(requested, precision, nx, ny, sm_count, step != 0);

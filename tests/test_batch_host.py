@@ -300,3 +300,81 @@ def test_sequential_baseline_applies_the_batch_rule(S, conv, seed):
         prev_c = (g, l)
         if st_py != lbm.RUN_ACTIVE:
             break
+
+
+# ---- TREND rule ---------------------------------------------------------------
+
+def _trend_run(S, seq, tol=1e-9, trend_tol=1e-4, window=1000, max_steps=10 ** 7):
+    """Feed (rho_g, rho_l) pairs window after window; returns the 1-based
+    window at which the C++ rule says CONVERGED (None if never)."""
+    D = ctypes.c_double
+    state = (D * 4)(0, 0, 0, 0)
+    r = lbm.lbm_result()
+    for k, (g, l) in enumerate(seq):
+        obs = (D * 6)(g, l, 5.0, 1.0, 0.0, 2.0)
+        st = S.shim_window_verdict_trend(tol, trend_tol, window, max_steps, obs, int(k == 0),
+                                         state, ctypes.byref(r))
+        if st == lbm.RUN_CONVERGED:
+            return k + 1
+    return None
+
+
+def test_trend_remaining_cases(S):
+    # geometric decay 1e-3 -> 5e-4 (r = 0.5): 5e-4 left
+    assert S.shim_trend_remaining(5e-4, 1e-3) == pytest.approx(5e-4)
+    assert S.shim_trend_remaining(-9e-4, -1e-3) == pytest.approx(9e-4 * 0.9 / 0.1)
+    # sign change (noise, oscillation) and growth: the amplitude
+    assert S.shim_trend_remaining(2e-6, -3e-6) == pytest.approx(5e-6)
+    assert S.shim_trend_remaining(4e-6, 3e-6) == pytest.approx(7e-6)
+    assert S.shim_trend_remaining(0.0, 0.0) == 0.0
+
+
+@pytest.mark.parametrize("ratio", [0.3, 0.6, 0.8, 0.95])
+def test_trend_stops_a_geometric_decay_near_its_limit(S, ratio):
+    """q_k = q_inf (1 + A ratio^k): the rule stops once the extrapolated
+    distance is below trend_tol, and the true distance there is below it
+    too (the extrapolation is exact for a geometric sequence); it does not
+    stop a window earlier than needed by more than one window."""
+    q_inf, A, ttol = (0.02, 0.3), 0.05, 1e-4
+    seq = [(q_inf[0] * (1 + A * ratio ** k), q_inf[1] * (1 - A * ratio ** k))
+           for k in range(1, 400)]
+    k = _trend_run(S, seq, trend_tol=ttol)
+    assert k is not None and k >= 3
+    g, l = seq[k - 1]
+    assert abs(g / q_inf[0] - 1) <= ttol * 1.0001 and abs(l / q_inf[1] - 1) <= ttol * 1.0001
+    # the first window at which the true distance is below the bound
+    first_ok = next(j + 1 for j, (g, l) in enumerate(seq)
+                    if abs(g - q_inf[0]) <= ttol * g and abs(l - q_inf[1]) <= ttol * l)
+    assert k <= max(first_ok, 3) + 1
+
+
+def test_trend_stops_noise_at_the_third_window_and_keeps_a_slow_drift(S):
+    rng = np.random.default_rng(3)
+    noise = [(0.02 * (1 + 3e-6 * rng.standard_normal()), 0.3 * (1 + 3e-6 * rng.standard_normal()))
+             for _ in range(10)]
+    assert _trend_run(S, noise) == 3
+    # a drift decaying with ratio 0.999 per window: 0.3 % away after 200
+    # windows, changes of 3e-6 per window -- COEX-style floors would stop it
+    drift = [(0.02 * (1 + 0.01 * 0.999 ** k), 0.3) for k in range(1, 200)]
+    assert _trend_run(S, drift) is None
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_sequential_baseline_applies_the_batch_trend_rule(S, seed):
+    """sweep.window_status with CONV_TREND (the sequential runs' host check)
+    and the batch engine's rule stop at the same window."""
+    from paper_1204_4098_gb300 import sweep
+    rng = np.random.default_rng(seed)
+    r = rng.uniform(0.3, 0.95)
+    seq = [(0.02 * (1 + 0.02 * r ** k + 2e-6 * rng.standard_normal()),
+            0.3 * (1 - 0.01 * r ** k + 2e-6 * rng.standard_normal())) for k in range(1, 300)]
+    k_c = _trend_run(S, seq)
+    k_py, prev_c, prev2_c = None, None, None
+    for k, c in enumerate(seq):
+        st, _ = sweep.window_status(lbm.CONV_TREND, c, prev_c, 0, False, True, 1000 * (k + 1),
+                                    1e-9, 10 ** 7, prev2_c=prev2_c, trend_tol=1e-4)
+        if st == lbm.RUN_CONVERGED:
+            k_py = k + 1
+            break
+        prev_c, prev2_c = c, prev_c
+    assert k_py == k_c and k_c is not None

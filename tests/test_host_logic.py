@@ -110,6 +110,24 @@ def test_warm_start_fallback_rules():
     assert not f("converged", C, 7, False, good)
     assert not f("converged", A, 1, False, bad_l) and not f("converged", CAP, 9, False, bad_l)
     assert not any(f("diverged", st, w, False, bad_l) for st in (A, C, CAP) for w in (1, 7))
+    # trend: due at the third window (with the extrapolated limits passed in)
+    assert f("trend", A, 3, False, bad_l) and f("trend", C, 3, False, bad_g)
+    assert not f("trend", A, 3, False, good)
+    assert not f("trend", A, 1, False, bad_l) and not f("trend", A, 2, False, bad_l)
+    assert not f("trend", A, 4, False, bad_l)
+
+
+def test_extrapolated_limit():
+    """The fallback's estimate of a run's limits from its last three windows:
+    exact for a geometric approach, the last value for noise."""
+    q_inf, r = (0.05, 0.30), 0.6
+    hist = [(1000 * k, q_inf[0] * (1 - 0.02 * r ** k), q_inf[1] * (1 + 0.01 * r ** k), k)
+            for k in range(1, 4)]
+    g, l = warmstart.extrapolated_limit(hist)
+    assert g == pytest.approx(q_inf[0], rel=1e-12) and l == pytest.approx(q_inf[1], rel=1e-12)
+    noisy = [(1000, 0.05, 0.3, 0), (2000, 0.0501, 0.2999, 1), (3000, 0.0500, 0.3001, 2)]
+    assert warmstart.extrapolated_limit(noisy) == (0.0500, 0.3001)
+    assert warmstart.extrapolated_limit(noisy[:1]) == (0.05, 0.3)
 
 
 def test_shard_balances_cells_and_covers_every_instance():
@@ -229,13 +247,20 @@ def test_warm_start_host_loop(monkeypatch):
     monkeypatch.setattr(warmstart.sweep, "cold_start_profiles",
                         lambda inst: (np.array([0.05, 0.04, 0.03]), np.array([0.3, 0.32, 0.34])))
     inst = [dict(nx=4, ny=32, T_over_Tc=0.8, tau=1.0, sigma=0.0, scheme=lbm.SC)] * 3
-    res, info = warmstart.run_warm(inst, _StandInModel())
+    res, info = warmstart.run_warm(inst, _StandInModel(), fallback="first_window")
     assert [r["fallback"] for r in res] == [False, True, True]
     assert info["fallbacks"] == 2
     assert all(r["status"] == lbm.RUN_CONVERGED for r in res)
     # the restarted runs keep only the history of the run that gave the answer
     assert [len(r["history"]) for r in res] == [3, 3, 3]
     assert res[1]["steps"] == 4000 and res[2]["steps"] == 5000  # wasted steps are counted
+    # default: the prediction is judged at the third window against the
+    # extrapolated limits (here the settled values), so instance 1 restarts
+    # after three windows
+    res_t, info_t = warmstart.run_warm(inst, _StandInModel())
+    assert [r["fallback"] for r in res_t] == [False, True, True]
+    assert res_t[1]["steps"] == 6000 and res_t[2]["steps"] == 5000
+    assert all(r["status"] == lbm.RUN_CONVERGED for r in res_t)
     res_c, info_c = warmstart.run_warm(inst, _StandInModel(), fallback="converged")
     assert [r["fallback"] for r in res_c] == [False, True, True]
     res_d, info_d = warmstart.run_warm(inst, _StandInModel(), fallback="diverged")
