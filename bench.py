@@ -42,7 +42,9 @@ STORE_NAMES = {"fp32": "StoreF32", "fp64": "StoreF64", "bf16dev": "StoreBF16",
                "fp16dev": "StoreF16"}
 # DRAM bytes per launch of the step kernel from an ncu capture, keyed by the
 # hash of the kernel sources it was taken on (null once they change), the
-# storage type, the lattice side and the kernel variant.
+# storage type, the lattice side and the kernel variant.  Captures of the
+# whole 8192^2 workload take only timing; DRAM counters come from a 4096^2
+# capture of the same kernel, scaled by the cell count.
 MEASURED_TRAFFIC = {
     # ncu launch list, 25 launches of strip_kernel<StoreF32, improved, step> at
     # 8192^2: 2.437 GB read + 2.370 GB written per launch
@@ -59,6 +61,10 @@ MEASURED_TRAFFIC = {
     # after adding the MRT scheme (three rates in the kernel arguments):
     # 2.431 GB read + 2.368 GB written per launch
     ("7bc3668251e0d237", "fp32", 8192, "pair"): 4.7986e9,
+    # packed FP32x2 pair arithmetic, row range of a band: small-case capture
+    # (-k strip2_kernel -c 3 at 4096^2: 615.3 MB read + 555.5 MB written per
+    # launch on average), scaled to 8192^2 by the cell count (x 4)
+    ("ee1858b957fb85d9", "fp32", 8192, "pair"): 4.6832e9,
 }
 
 
@@ -543,10 +549,10 @@ def warmstart_measure(train_draws, epochs, held_out, device=0, seq_all=True, see
     t_warm, s_warm = warmstart.time_to_answer(warm, winfo, cold, among=both)
     warm_gpu, cold_gpu = winfo["gpu_ms"] / 1e3, cinfo["gpu_ms"] / 1e3
     return {"held_out": len(held), "grid": "256x256",
-            "rule": "TREND: rho_g, rho_l within 1e-4 of their limits extrapolated from the last "
-                    "two window changes (warm, cold batched and cold sequential alike); "
-                    "fallback: extrapolated limits > 1e-2 from the prediction at window 3, "
-                    "or divergence",
+            "rule": "TREND: rho_g, rho_l settled to 1e-4 over the last nine windows (range of "
+                    "the last six, geometric extrapolation of three-window block means), warm, "
+                    "cold batched and cold sequential alike; fallback: limits extrapolated from "
+                    "the first three windows > 1e-2 from the prediction, or divergence",
             "training": {**info, "data_wall_s": data_s, "train_loss": model.train_loss,
                          "train_s": model.train_seconds, "epochs": [epochs] * 3,
                          "learning_rates": [2e-3, 5e-4, 1e-4]},

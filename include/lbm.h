@@ -116,7 +116,10 @@ lbm_status lbm_create(const lbm_params *p, lbm_ctx **out);
  * (the band below rank 0 is the last rank's); x stays periodic in the band.
  *   - lbm_init_density / lbm_init_density_at_rest take (p->ny + 4) x nx
  *     densities: the band's rows with the two global rows below and above
- *     them (wrapped), so that the first step needs no exchange;
+ *     them (wrapped).  The owned rows are then exact; the ghost rows' own
+ *     pulls (and, for deviation storage, the density their deviations refer
+ *     to) reach beyond the given rows, so exchange halos once after the
+ *     initialisation, before the first step;
  *   - lbm_step / lbm_step_async advance one step per call (n <= 1; larger n
  *     is LBM_E_INVAL); between calls the caller exchanges halos:
  *     lbm_band_halo_pack, send / receive, lbm_band_halo_unpack;
@@ -289,17 +292,20 @@ enum { LBM_BATCH_AUTO = 0, LBM_BATCH_WORKLIST = 1, LBM_BATCH_PERSISTENT = 2,
  * max(tol, conv_rel * value) over two consecutive windows.  In FP32 the
  * interface position of a relaxed slab jitters by ~1e-4 cells per window
  * (rounding noise driving a nearly neutral mode), so CELL is met only by
- * some runs; COEX tests what a sweep reports.  TREND: from the third
- * window after a (re)start, each coexistence density is within
- * max(tol, trend_tol * value) of its limit as estimated from its last two
- * window-to-window changes: two changes of one sign, the later smaller, are
- * a geometric decay with ratio r = d / d_prev and remaining distance
- * |d| r / (1 - r); any other pair is noise (or oscillation) of amplitude
- * |d| + |d_prev|.  COEX's floor sits at FP32 rounding noise, which keeps a
- * settled slab running for tens of thousands of steps; TREND stops it once
- * the answer is known to trend_tol, while a slow monotone drift (r near 1)
- * keeps running.  The paper has no convergence test; this one serves the
- * sweeps (steps to convergence, warm against cold starts). */
+ * some runs; COEX tests what a sweep reports.  TREND: from the ninth window
+ * after a (re)start, each coexistence density is settled within
+ * max(tol, trend_tol * value): over its last nine window values, the range
+ * of the last six (a slab's standing sound wave has a period of a few
+ * windows, so the range bounds its amplitude) and the extrapolated drift of
+ * the means of three blocks of three windows (two block changes of one sign,
+ * the later smaller, are a geometric decay with ratio r = d / d_prev and
+ * remaining distance |d| r / (1 - r); any other pair is noise of amplitude
+ * |d| + |d_prev|) are both within it.  COEX's floor sits at FP32 rounding
+ * noise, which keeps a settled slab running for tens of thousands of steps;
+ * TREND stops it once the answer is known to trend_tol, while a slow
+ * monotone drift (r near 1) or a live sound wave keeps it running.  The
+ * paper has no convergence test; this one serves the sweeps (steps to
+ * convergence, warm against cold starts). */
 enum { LBM_CONV_COEX = 0, LBM_CONV_CELL = 1, LBM_CONV_NONE = 2 /* run to max_steps */,
        LBM_CONV_TREND = 3 };
 enum { LBM_RUN_ACTIVE = 0, LBM_RUN_CONVERGED = 1, LBM_RUN_DIVERGED = 2, LBM_RUN_CAPPED = 3 };

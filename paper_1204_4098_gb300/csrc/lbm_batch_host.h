@@ -170,16 +170,22 @@ struct ConvRule {
   double trend_tol = 1e-4;  // TREND: relative bound on the distance to the limit
 };
 
+// TREND looks at the last kTrendBlock * 3 window values of each coexistence
+// density (a flat slab's standing sound wave has a period of a few windows,
+// so a single window's change can sit at a turning point of it).
+constexpr int kTrendBlock = 3;
+constexpr int kTrendHist = 3 * kTrendBlock;
+
 // Per-instance state of the convergence rules, reset by a (re)start.
 struct ConvState {
   int calm = 0;       // COEX: consecutive calm windows
   int windows = 0;    // windows since the last (re)start
-  double dg = 0.0;    // TREND: change of rho_g over the last window
-  double dl = 0.0;    //        and of rho_l
+  double hg[kTrendHist] = {0.0};  // TREND: the last window values of rho_g
+  double hl[kTrendHist] = {0.0};  //        and of rho_l (oldest first)
 };
 
-// TREND: estimated distance to the limit of a quantity that changed by d
-// over the last window and by d_prev over the one before.  Two changes of the
+// Estimated distance to the limit of a quantity whose last two changes
+// (between consecutive block means) were d_prev and d: two changes of the
 // same sign, the later smaller, are taken as a geometric decay with ratio
 // r = d / d_prev, whose remaining distance is |d| r / (1 - r); anything else
 // (a sign change, a growing change) as noise or oscillation of amplitude
@@ -192,20 +198,37 @@ inline double trend_remaining(double d, double d_prev) {
   return std::fabs(d) + std::fabs(d_prev);
 }
 
+// TREND on one quantity's last kTrendHist window values h (oldest first):
+// the block means m0, m1, m2 of three consecutive blocks of kTrendBlock
+// windows give the drift's remaining distance trend_remaining(m2 - m1,
+// m1 - m0), and the range of the last 2 kTrendBlock values bounds the
+// oscillation; both must be within bound.
+inline bool trend_settled(const double* h, double bound) {
+  double m[3] = {0.0, 0.0, 0.0};
+  for (int b = 0; b < 3; ++b) {
+    for (int i = 0; i < kTrendBlock; ++i) m[b] += h[b * kTrendBlock + i];
+    m[b] /= kTrendBlock;
+  }
+  double lo = h[kTrendBlock], hi = h[kTrendBlock];
+  for (int i = kTrendBlock; i < kTrendHist; ++i) {
+    lo = std::min(lo, h[i]);
+    hi = std::max(hi, h[i]);
+  }
+  return hi - lo <= bound && trend_remaining(m[2] - m[1], m[1] - m[0]) <= bound;
+}
+
 // Apply one window to an instance's result: steps and observables are
 // updated, the rule state advanced, and the new status returned: DIVERGED
 // (device flag or a non-finite density) before CONVERGED before CAPPED (step
 // cap reached) before ACTIVE.  CONVERGED means, by rule: CELL every cell
 // within its tolerance; COEX two calm windows in a row, a calm window being
 // one in which rho_g and rho_l each changed by less than max(tol, conv_rel
-// value) (never the first window after a (re)start); TREND, from the third
-// window after a (re)start on, both coexistence densities within
-// max(tol, trend_tol value) of their limits as trend_remaining estimates
-// them; NONE never.
+// value) (never the first window after a (re)start); TREND, from the
+// kTrendHist-th window after a (re)start on, both coexistence densities
+// settled (trend_settled) within max(tol, trend_tol value); NONE never.
 inline int window_verdict(const ConvRule& rule, const WindowObs& o, bool first, ConvState& st,
                           lbm_result& r) {
   if (first) st = ConvState{};
-  st.windows += 1;
   const double dg = first ? 0.0 : o.rho_g - r.rho_g;
   const double dl = first ? 0.0 : o.rho_l - r.rho_l;
   const bool coex_calm =
@@ -213,12 +236,17 @@ inline int window_verdict(const ConvRule& rule, const WindowObs& o, bool first, 
       std::fabs(dg) < std::max(rule.tol, rule.conv_rel * std::fabs(o.rho_g)) &&
       std::fabs(dl) < std::max(rule.tol, rule.conv_rel * std::fabs(o.rho_l));
   st.calm = coex_calm ? st.calm + 1 : 0;
-  const bool trend_settled =
-      st.windows >= 3 &&
-      trend_remaining(dg, st.dg) <= std::max(rule.tol, rule.trend_tol * std::fabs(o.rho_g)) &&
-      trend_remaining(dl, st.dl) <= std::max(rule.tol, rule.trend_tol * std::fabs(o.rho_l));
-  st.dg = dg;
-  st.dl = dl;
+  for (int i = 0; i + 1 < kTrendHist; ++i) {
+    st.hg[i] = st.hg[i + 1];
+    st.hl[i] = st.hl[i + 1];
+  }
+  st.hg[kTrendHist - 1] = o.rho_g;
+  st.hl[kTrendHist - 1] = o.rho_l;
+  st.windows += 1;
+  const bool trend =
+      st.windows >= kTrendHist &&
+      trend_settled(st.hg, std::max(rule.tol, rule.trend_tol * std::fabs(o.rho_g))) &&
+      trend_settled(st.hl, std::max(rule.tol, rule.trend_tol * std::fabs(o.rho_l)));
   r.steps += rule.window;
   r.rho_g = o.rho_g;
   r.rho_l = o.rho_l;
@@ -228,7 +256,7 @@ inline int window_verdict(const ConvRule& rule, const WindowObs& o, bool first, 
   bool converged = false;
   if (rule.conv == LBM_CONV_CELL) converged = o.max_dev < 1.0f;
   else if (rule.conv == LBM_CONV_COEX) converged = st.calm >= 2;
-  else if (rule.conv == LBM_CONV_TREND) converged = trend_settled;
+  else if (rule.conv == LBM_CONV_TREND) converged = trend;
   if (o.diverged || !o.finite) return LBM_RUN_DIVERGED;
   if (converged) return LBM_RUN_CONVERGED;
   if (r.steps >= rule.max_steps) return LBM_RUN_CAPPED;

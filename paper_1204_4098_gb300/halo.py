@@ -104,17 +104,22 @@ class BandLattice:
         dev = torch.device("cuda", device)
         self.lo = torch.empty(n, dtype=torch.uint8, device=dev)
         self.hi = torch.empty(n, dtype=torch.uint8, device=dev)
+        self.exchange()  # ghost rows from the neighbours' exact boundary rows
+
+    def exchange(self):
+        """Pack, exchange and unpack the halo rows (on the band's stream)."""
+        with self.torch.cuda.stream(self.stream):
+            self.lat.halo_pack(self.lo.data_ptr(), self.hi.data_ptr())
+            below, above = exchange(self.lo, self.hi, self.rank, self.world, self.group)
+            self.lat.halo_unpack(below.data_ptr(), above.data_ptr())
 
     def step(self, n, scheme, tau, sigma=0.0):
         """n steps, each followed by a halo exchange; returns the status of
         the last step (lbm_sync_status)."""
-        torch = self.torch
-        with torch.cuda.stream(self.stream):
+        with self.torch.cuda.stream(self.stream):
             for _ in range(n):
                 self.lat.step_async(1, scheme, tau, sigma)
-                self.lat.halo_pack(self.lo.data_ptr(), self.hi.data_ptr())
-                below, above = exchange(self.lo, self.hi, self.rank, self.world, self.group)
-                self.lat.halo_unpack(below.data_ptr(), above.data_ptr())
+                self.exchange()
         return self.lat.sync()
 
     def observe(self):
@@ -152,10 +157,19 @@ class LocalBands:
             self.lats.append(lat)
             self.lo.append(torch.empty(n, dtype=torch.uint8, device=dev))
             self.hi.append(torch.empty(n, dtype=torch.uint8, device=dev))
+        self.exchange()  # ghost rows from the neighbours' exact boundary rows
 
     def set_variant(self, variant):
         for lat in self.lats:
             lat.set_variant(variant)
+
+    def exchange(self):
+        """Every band packs its boundary rows, then unpacks its neighbours'."""
+        for lat, lo, hi in zip(self.lats, self.lo, self.hi):
+            lat.halo_pack(lo.data_ptr(), hi.data_ptr())
+        for b, lat in enumerate(self.lats):
+            below, above = (b - 1) % self.k, (b + 1) % self.k
+            lat.halo_unpack(self.hi[below].data_ptr(), self.lo[above].data_ptr())
 
     def step(self, n, scheme, tau, sigma=0.0):
         """n steps of every band with an exchange after each; returns the
@@ -163,11 +177,7 @@ class LocalBands:
         for _ in range(n):
             for lat in self.lats:
                 lat.step_async(1, scheme, tau, sigma)
-            for lat, lo, hi in zip(self.lats, self.lo, self.hi):
-                lat.halo_pack(lo.data_ptr(), hi.data_ptr())
-            for b, lat in enumerate(self.lats):
-                below, above = (b - 1) % self.k, (b + 1) % self.k
-                lat.halo_unpack(self.hi[below].data_ptr(), self.lo[above].data_ptr())
+            self.exchange()
         return max(lat.sync() for lat in self.lats)
 
     def observe(self):

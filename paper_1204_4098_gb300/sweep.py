@@ -96,32 +96,41 @@ def _calm(new, old, tol, rel=COEX_REL):
     return abs(new - old) < max(tol, rel * abs(new))
 
 
+TREND_BLOCK = 3                # windows per block of the TREND rule
+TREND_HIST = 3 * TREND_BLOCK   # windows it looks at
+
+
 def trend_remaining(d, d_prev):
-    """Estimated distance to the limit from the last two window changes: a
-    geometric decay (same sign, shrinking: r = d / d_prev) has |d| r / (1 - r)
-    left; any other pair is noise of amplitude |d| + |d_prev|."""
+    """Estimated distance to the limit from the last two changes of block
+    means: a geometric decay (same sign, shrinking: r = d / d_prev) has
+    |d| r / (1 - r) left; any other pair is noise of amplitude |d| + |d_prev|."""
     if d * d_prev > 0.0 and abs(d) < abs(d_prev):
         r = d / d_prev
         return abs(d) * r / (1.0 - r)
     return abs(d) + abs(d_prev)
 
 
-def _settled(c, prev_c, prev2_c, tol, trend_tol):
-    return all(trend_remaining(c[i] - prev_c[i], prev_c[i] - prev2_c[i])
-               <= max(tol, trend_tol * abs(c[i])) for i in (0, 1))
+def trend_settled(h, bound):
+    """TREND on one quantity's last TREND_HIST window values (oldest first):
+    the drift of the means of three blocks of TREND_BLOCK windows, and the
+    range of the last two blocks (a standing sound wave's amplitude), both
+    within bound."""
+    m = [float(np.mean(h[b * TREND_BLOCK:(b + 1) * TREND_BLOCK])) for b in range(3)]
+    tail = h[TREND_BLOCK:]
+    return max(tail) - min(tail) <= bound and trend_remaining(m[2] - m[1], m[1] - m[0]) <= bound
 
 
 def window_status(conv, c, prev_c, calm, cell, finite, steps, tol, max_steps, rel=COEX_REL,
-                  prev2_c=None, trend_tol=TREND_TOL):
+                  hist=None, trend_tol=TREND_TOL):
     """The batch engine's rule after one window, for runs checked on the host:
-    c, prev_c and prev2_c are (rho_g, rho_l) now, one and two windows earlier
-    (None when that window precedes the last start, which makes the first
-    window never calm and TREND wait for its third); calm counts consecutive
-    windows in which both changed by less than max(tol, rel value); cell says
-    every cell changed by less than its tolerance.  Returns (status, calm):
-    DIVERGED (a non-finite density) before CONVERGED (CELL: cell; COEX: two
-    calm windows in a row; TREND: both densities within max(tol, trend_tol
-    value) of their limit as trend_remaining estimates it; NONE: never)
+    c and prev_c are (rho_g, rho_l) now and one window earlier (prev_c None
+    for the first window after a start, which is never calm); hist holds the
+    (rho_g, rho_l) of every window since the last start, c last; calm counts
+    consecutive windows in which both changed by less than max(tol, rel
+    value); cell says every cell changed by less than its tolerance.  Returns
+    (status, calm): DIVERGED (a non-finite density) before CONVERGED (CELL:
+    cell; COEX: two calm windows in a row; TREND: from the TREND_HIST-th window
+    on, both densities settled within max(tol, trend_tol value); NONE: never)
     before CAPPED (steps reached max_steps) before ACTIVE."""
     calm = calm + 1 if (prev_c is not None and _calm(c[0], prev_c[0], tol, rel)
                         and _calm(c[1], prev_c[1], tol, rel)) else 0
@@ -130,8 +139,9 @@ def window_status(conv, c, prev_c, calm, cell, finite, steps, tol, max_steps, re
     elif conv == lbm.CONV_COEX:
         converged = calm >= 2
     elif conv == lbm.CONV_TREND:
-        converged = prev_c is not None and prev2_c is not None and \
-            _settled(c, prev_c, prev2_c, tol, trend_tol)
+        converged = hist is not None and len(hist) >= TREND_HIST and all(
+            trend_settled([h[i] for h in hist[-TREND_HIST:]], max(tol, trend_tol * abs(c[i])))
+            for i in (0, 1))
     else:
         converged = False
     if not finite:
@@ -149,8 +159,8 @@ def run_sequential(instances, rho_g, rho_l, width, window=1000, tol=1e-9, max_st
     is checked on the host with the batch engine's rule (window_status:
     CONV_COEX: rho_g and rho_l each changed by less than max(tol, conv_rel
     value) over two consecutive windows; CONV_CELL: every cell by less than
-    max(tol, 8 eps_32 rho) over a window; CONV_TREND: both within
-    max(tol, trend_tol value) of their extrapolated limits; CONV_NONE: run to
+    max(tol, 8 eps_32 rho) over a window; CONV_TREND: both settled within
+    max(tol, trend_tol value) over the last nine windows; CONV_NONE: run to
     max_steps).  A smooth profile (width > 0) starts at rest (zero actual
     velocity), a sharp one at u = 0, as in the batch engine's init_slabs.
     Returns (results, wall seconds)."""
@@ -172,7 +182,7 @@ def run_sequential(instances, rho_g, rho_l, width, window=1000, tol=1e-9, max_st
             else:
                 lat.init_density(rho0)
             prev = lat.observe()[0]
-            prev_c = prev2_c = None
+            prev_c, hist_c = None, []
             steps, status, calm = 0, lbm.RUN_ACTIVE, 0
             while status == lbm.RUN_ACTIVE:
                 st = lat.step(window, d["scheme"], d["tau"], d.get("sigma", 0.0),
@@ -183,11 +193,12 @@ def run_sequential(instances, rho_g, rho_l, width, window=1000, tol=1e-9, max_st
                     break
                 rho = lat.observe()[0]
                 c = _coexistence(rho)
+                hist_c.append(c)
                 cell = np.all(np.abs(rho - prev) < np.maximum(tol, 8 * F32_EPS * np.abs(rho)))
                 status, calm = window_status(conv, c, prev_c, calm, cell,
                                              bool(np.all(np.isfinite(rho))), steps, tol,
-                                             max_steps, rel, prev2_c, ttol)
-                prev, prev_c, prev2_c = rho, c, prev_c
+                                             max_steps, rel, hist_c, ttol)
+                prev, prev_c = rho, c
                 history.append((steps, c[0], c[1], len(history)))
             g, l = _coexistence(prev) if status != lbm.RUN_DIVERGED else (np.nan, np.nan)
         out.append(dict(status=status, steps=steps, rho_g=g, rho_l=l, history=history,

@@ -14,7 +14,8 @@ tanh profile, even when the prediction is right to 1e-3, so comparing them
 directly restarts good predictions too; run_warm's `fallback` keeps that
 rule, the check at convergence and divergence-only for comparison.)  Warm
 and cold runs stop by the same batch rule, TREND by default: both
-coexistence densities within 1e-4 of their extrapolated limits.  Cold runs
+coexistence densities settled to 1e-4 over nine windows (sound-wave range
+and extrapolated drift).  Cold runs
 remain the reference for the error: the tests and the sweep report compare
 warm and cold coexistence densities.
 

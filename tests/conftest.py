@@ -48,5 +48,6 @@ def host_shim(tmp_path_factory):
                                               ctypes.POINTER(D), ctypes.c_void_p]
     lib.shim_trend_remaining.argtypes = [D, D]
     lib.shim_trend_remaining.restype = D
+    lib.shim_trend_hist.restype = I
     lib.shim_strip_geometry.argtypes = [I, I, I, ctypes.c_longlong, I, I, IP]
     return lib

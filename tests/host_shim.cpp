@@ -66,8 +66,8 @@ int shim_window_verdict(int conv, double tol, double conv_rel, int window, int m
   return v;
 }
 
-// The TREND rule with its state carried by the caller in state[4] =
-// {calm, windows, dg, dl}; obs as above.
+// The TREND rule with its state carried by the caller in state[2 + 2 H] =
+// {calm, windows, hg[H], hl[H]}, H = lbm::kTrendHist; obs as above.
 int shim_window_verdict_trend(double tol, double trend_tol, int window, int max_steps,
                               const double* obs, int first, double* state, lbm_result* r) {
   lbm::WindowObs o;
@@ -81,18 +81,25 @@ int shim_window_verdict_trend(double tol, double trend_tol, int window, int max_
   o.diverged = false;
   lbm::ConvRule rule{LBM_CONV_TREND, tol, 0.0, window, max_steps};
   rule.trend_tol = trend_tol;
+  const int H = lbm::kTrendHist;
   lbm::ConvState st;
   st.calm = int(state[0]);
   st.windows = int(state[1]);
-  st.dg = state[2];
-  st.dl = state[3];
+  for (int i = 0; i < H; ++i) {
+    st.hg[i] = state[2 + i];
+    st.hl[i] = state[2 + H + i];
+  }
   const int v = lbm::window_verdict(rule, o, first != 0, st, *r);
   state[0] = st.calm;
   state[1] = st.windows;
-  state[2] = st.dg;
-  state[3] = st.dl;
+  for (int i = 0; i < H; ++i) {
+    state[2 + i] = st.hg[i];
+    state[2 + H + i] = st.hl[i];
+  }
   return v;
 }
+
+int shim_trend_hist() { return lbm::kTrendHist; }
 
 double shim_trend_remaining(double d, double d_prev) { return lbm::trend_remaining(d, d_prev); }
 

@@ -308,7 +308,8 @@ def _trend_run(S, seq, tol=1e-9, trend_tol=1e-4, window=1000, max_steps=10 ** 7)
     """Feed (rho_g, rho_l) pairs window after window; returns the 1-based
     window at which the C++ rule says CONVERGED (None if never)."""
     D = ctypes.c_double
-    state = (D * 4)(0, 0, 0, 0)
+    H = S.shim_trend_hist()
+    state = (D * (2 + 2 * H))()
     r = lbm.lbm_result()
     for k, (g, l) in enumerate(seq):
         obs = (D * 6)(g, l, 5.0, 1.0, 0.0, 2.0)
@@ -329,32 +330,60 @@ def test_trend_remaining_cases(S):
     assert S.shim_trend_remaining(0.0, 0.0) == 0.0
 
 
+def _expected_stop(seq, q_inf, ttol, H=9, B=3):
+    """First window at which, for both quantities, the range of the last two
+    blocks and the last block mean's true distance to the limit are within
+    the bound (what the rule computes exactly for a geometric sequence)."""
+    for j in range(H, len(seq) + 1):
+        ok = True
+        for i in (0, 1):
+            h = [x[i] for x in seq[j - H:j]]
+            bound = ttol * abs(h[-1])
+            m2 = np.mean(h[2 * B:])
+            ok &= max(h[B:]) - min(h[B:]) <= bound and abs(m2 - q_inf[i]) <= bound * (1 + 1e-9)
+        if ok:
+            return j
+    return None
+
+
 @pytest.mark.parametrize("ratio", [0.3, 0.6, 0.8, 0.95])
-def test_trend_stops_a_geometric_decay_near_its_limit(S, ratio):
-    """q_k = q_inf (1 + A ratio^k): the rule stops once the extrapolated
-    distance is below trend_tol, and the true distance there is below it
-    too (the extrapolation is exact for a geometric sequence); it does not
-    stop a window earlier than needed by more than one window."""
+def test_trend_stops_a_geometric_decay_when_settled(S, ratio):
+    """q_k = q_inf (1 + A ratio^k): block means decay geometrically too, so
+    the extrapolation is exact and the rule stops exactly when the last
+    blocks' range and mean are within trend_tol -- and the value there is
+    within trend_tol of the limit."""
     q_inf, A, ttol = (0.02, 0.3), 0.05, 1e-4
     seq = [(q_inf[0] * (1 + A * ratio ** k), q_inf[1] * (1 - A * ratio ** k))
-           for k in range(1, 400)]
+           for k in range(1, 600)]
     k = _trend_run(S, seq, trend_tol=ttol)
-    assert k is not None and k >= 3
+    assert k is not None and k >= 9
+    assert k == _expected_stop(seq, q_inf, ttol)
     g, l = seq[k - 1]
-    assert abs(g / q_inf[0] - 1) <= ttol * 1.0001 and abs(l / q_inf[1] - 1) <= ttol * 1.0001
-    # the first window at which the true distance is below the bound
-    first_ok = next(j + 1 for j, (g, l) in enumerate(seq)
-                    if abs(g - q_inf[0]) <= ttol * g and abs(l - q_inf[1]) <= ttol * l)
-    assert k <= max(first_ok, 3) + 1
+    assert abs(g / q_inf[0] - 1) <= ttol and abs(l / q_inf[1] - 1) <= ttol
 
 
-def test_trend_stops_noise_at_the_third_window_and_keeps_a_slow_drift(S):
+def test_trend_does_not_stop_at_a_turning_point_of_a_sound_wave(S):
+    """A slab's standing sound wave sampled once per window (period ~4.5
+    windows) decaying over ~15 windows: changes of one sign that shrink
+    sharply at a turning point must not pass for a settled decay; the rule
+    waits until the oscillation itself is below trend_tol."""
+    q_inf, ttol = (0.0244, 0.3397), 1e-4
+    amp = lambda k: 0.013 * np.exp(-k / 15.0)
+    seq = [(q_inf[0] * (1 + amp(k) * np.cos(2 * np.pi * k / 4.5)),
+            q_inf[1] * (1 - 0.3 * amp(k) * np.cos(2 * np.pi * k / 4.5))) for k in range(1, 400)]
+    k = _trend_run(S, seq, trend_tol=ttol)
+    assert k is not None
+    assert amp(k) * 1.05 <= 2 * ttol  # the wave has died down to the bound
+    assert abs(seq[k - 1][0] / q_inf[0] - 1) <= 2 * ttol
+
+
+def test_trend_stops_noise_at_the_ninth_window_and_keeps_a_slow_drift(S):
     rng = np.random.default_rng(3)
     noise = [(0.02 * (1 + 3e-6 * rng.standard_normal()), 0.3 * (1 + 3e-6 * rng.standard_normal()))
-             for _ in range(10)]
-    assert _trend_run(S, noise) == 3
+             for _ in range(20)]
+    assert _trend_run(S, noise) == 9
     # a drift decaying with ratio 0.999 per window: 0.3 % away after 200
-    # windows, changes of 3e-6 per window -- COEX-style floors would stop it
+    # windows, changes of 3e-6 per window -- a floor on single changes would stop it
     drift = [(0.02 * (1 + 0.01 * 0.999 ** k), 0.3) for k in range(1, 200)]
     assert _trend_run(S, drift) is None
 
@@ -366,15 +395,18 @@ def test_sequential_baseline_applies_the_batch_trend_rule(S, seed):
     from paper_1204_4098_gb300 import sweep
     rng = np.random.default_rng(seed)
     r = rng.uniform(0.3, 0.95)
-    seq = [(0.02 * (1 + 0.02 * r ** k + 2e-6 * rng.standard_normal()),
+    P = rng.uniform(3.0, 7.0)
+    seq = [(0.02 * (1 + 0.02 * r ** k + 2e-3 * np.exp(-k / 12) * np.cos(2 * np.pi * k / P)
+                    + 2e-6 * rng.standard_normal()),
             0.3 * (1 - 0.01 * r ** k + 2e-6 * rng.standard_normal())) for k in range(1, 300)]
     k_c = _trend_run(S, seq)
-    k_py, prev_c, prev2_c = None, None, None
+    k_py, prev_c, hist = None, None, []
     for k, c in enumerate(seq):
+        hist.append(c)
         st, _ = sweep.window_status(lbm.CONV_TREND, c, prev_c, 0, False, True, 1000 * (k + 1),
-                                    1e-9, 10 ** 7, prev2_c=prev2_c, trend_tol=1e-4)
+                                    1e-9, 10 ** 7, hist=hist, trend_tol=1e-4)
         if st == lbm.RUN_CONVERGED:
             k_py = k + 1
             break
-        prev_c, prev2_c = c, prev_c
+        prev_c = c
     assert k_py == k_c and k_c is not None
