@@ -520,7 +520,7 @@ def run_sweep_workload(args, world, rank, local):
 
 
 def warmstart_measure(train_draws, epochs, held_out, device=0, seq_all=True, seed_train=40,
-                      seed_held=41, train_max_steps=100000):
+                      seed_held=41, train_max_steps=100000, trend_tol=None):
     """Config 5: train the network on converged cold runs of narrow slabs,
     then start held-out points on 256 x 256 grids from its predictions and
     compare the whole sweep with cold batched runs and with cold sequential
@@ -529,18 +529,19 @@ def warmstart_measure(train_draws, epochs, held_out, device=0, seq_all=True, see
 
     from paper_1204_4098_gb300 import inputs, lbm, sweep, warmstart
     t0 = time.perf_counter()
-    X, Y, info = warmstart.training_data(train_draws, seed=seed_train, max_steps=train_max_steps)
+    X, Y, info = warmstart.training_data(train_draws, seed=seed_train, max_steps=train_max_steps,
+                                         trend_tol=trend_tol)
     data_s = time.perf_counter() - t0
     model = warmstart.train(X, Y, stages=((epochs, 2e-3), (epochs, 5e-4), (epochs, 1e-4)),
                             batch=128, seed=1, device=device)
     held = inputs.sweep_instances(held_out, seed=seed_held, nx_range=(256, 256),
                                   ny_range=(256, 256))
-    warm, winfo = warmstart.run_warm(held, model, device=device)
-    cold, cinfo = warmstart.run_cold_batched(held, device=device)
+    warm, winfo = warmstart.run_warm(held, model, device=device, trend_tol=trend_tol)
+    cold, cinfo = warmstart.run_cold_batched(held, device=device, trend_tol=trend_tol)
     g, l = sweep.cold_start_profiles(held)
     ns = len(held) if seq_all else min(32, len(held))
     seq, seq_wall = sweep.run_sequential(held[:ns], g[:ns], l[:ns], np.zeros(ns), device=device,
-                                         conv=lbm.CONV_TREND)
+                                         conv=lbm.CONV_TREND, trend_tol=trend_tol)
     seq_all_s = seq_wall * len(held) / ns
     err, n_both = _coex_agreement(warm, cold)
     err_seq, n_both_seq = _coex_agreement(warm[:ns], seq)
@@ -549,6 +550,7 @@ def warmstart_measure(train_draws, epochs, held_out, device=0, seq_all=True, see
     t_warm, s_warm = warmstart.time_to_answer(warm, winfo, cold, among=both)
     warm_gpu, cold_gpu = winfo["gpu_ms"] / 1e3, cinfo["gpu_ms"] / 1e3
     return {"held_out": len(held), "grid": "256x256",
+            "trend_tol": sweep.TREND_TOL if trend_tol is None else trend_tol,
             "rule": "TREND: rho_g, rho_l settled to 1e-4 over the last nine windows (range of "
                     "the last six, geometric extrapolation of three-window block means), warm, "
                     "cold batched and cold sequential alike; fallback: limits extrapolated from "
@@ -578,7 +580,8 @@ def run_warmstart_workload(args, world, rank, local):
     """Config 5 in full (about 11,000 training draws, 256 held-out points)."""
     import torch
     torch.cuda.set_device(local)
-    res = warmstart_measure(args.train_draws, args.epochs, args.held_out, device=local)
+    res = warmstart_measure(args.train_draws, args.epochs, args.held_out, device=local,
+                            trend_tol=args.trend_tol)
     line = {"metric": METRIC, "workload": "learned warm start (config 5)",
             "value": res["whole_sweep_cold_sequential_over_warm_batched"],
             "unit": "x less whole-sweep time: warm batched GPU vs cold sequential plain runs",
@@ -760,6 +763,8 @@ def main():
     ap.add_argument("--train-draws", type=int, default=11000)
     ap.add_argument("--epochs", type=int, default=1500)
     ap.add_argument("--held-out", type=int, default=256)
+    ap.add_argument("--trend-tol", type=float, default=None,
+                    help="TREND stopping bound of the warm-start workload (default 1e-4)")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-warmstart", action="store_true")
     ap.add_argument("--kernel-variant", choices=("auto", "register", "pair", "staged"),

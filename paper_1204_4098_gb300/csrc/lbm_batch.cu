@@ -122,6 +122,31 @@ __device__ __forceinline__ void class_range(const int* counts, bool pair, int& a
   a1 = pair ? counts[0] : counts[1];
 }
 
+// Work-list item `item` (an index into the prefix table's range [a0, a1)):
+// find its instance, stage the instance's arguments in the warp's shared
+// slot (the body reloads them there instead of holding registers, like
+// kernel parameters in the constant bank) and advance its strip x band.
+template <bool kPair>
+__device__ __forceinline__ void worklist_item(const BatchInst* __restrict__ inst,
+                                              const int* __restrict__ active,
+                                              const int* __restrict__ prefix, int a0, int a1,
+                                              int item, const float* src, float* dst,
+                                              unsigned* inst_status,
+                                              StripArgs<StoreF32>& args, int lane) {
+  int lo = a0, hi = a1;  // prefix[lo] <= item < prefix[lo + 1]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= item) lo = mid; else hi = mid;
+  }
+  const int i = active[lo];
+  const BatchInst I = inst[i];
+  const int local = item - prefix[lo];
+  __syncwarp();
+  if (lane == 0) args = inst_args(I, src, dst, inst_status + i, false);
+  __syncwarp();
+  run_item<kPair, false>(args, I.scheme, local % I.n_strips, local / I.n_strips, lane);
+}
+
 // One step of every active instance of one class; warp w takes items
 // w, w + W, ... of the class's range of the prefix table.
 template <bool kPair>
@@ -137,21 +162,34 @@ batch_worklist_kernel(const BatchInst* __restrict__ inst, const int* __restrict_
   class_range(counts, kPair, a0, a1);
   const int end = prefix[a1];
   for (int item = prefix[a0] + ((blockIdx.x * kWorklistThreads + threadIdx.x) >> 5); item < end;
-       item += nwarps) {
-    int lo = a0, hi = a1;  // prefix[lo] <= item < prefix[lo + 1]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (prefix[mid] <= item) lo = mid; else hi = mid;
-    }
-    const int i = active[lo];
-    const BatchInst I = inst[i];
-    const int local = item - prefix[lo];
-    // the item's arguments live in shared memory, like kernel parameters in
-    // the constant bank: the body reloads them instead of holding registers
-    __syncwarp();
-    if (lane == 0) args[warp] = inst_args(I, src, dst, inst_status + i, false);
-    __syncwarp();
-    run_item<kPair, false>(args[warp], I.scheme, local % I.n_strips, local / I.n_strips, lane);
+       item += nwarps)
+    worklist_item<kPair>(inst, active, prefix, a0, a1, item, src, dst, inst_status, args[warp],
+                         lane);
+}
+
+// The same step with the items handed out dynamically: a warp that finishes
+// an item takes the next one from the step's counter (zeroed at the start of
+// the window), so warps whose items were short take more of them and the
+// step ends when the work does, not when the unluckiest warp's fixed share
+// does.  The order in which items are taken does not change any result.
+template <bool kPair>
+__global__ void __launch_bounds__(kWorklistThreads,
+                                  kPair ? LBM_BATCH_PAIR_MIN_BLOCKS : LBM_BATCH_ODD_MIN_BLOCKS)
+batch_worklist_dyn_kernel(const BatchInst* __restrict__ inst, const int* __restrict__ active,
+                          const int* __restrict__ prefix, const int* __restrict__ counts,
+                          const float* src, float* dst, unsigned* inst_status, int* counter) {
+  __shared__ StripArgs<StoreF32> args[kWorklistThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int a0, a1;
+  class_range(counts, kPair, a0, a1);
+  const int first = prefix[a0], end = prefix[a1];
+  for (;;) {
+    int k = 0;
+    if (lane == 0) k = atomicAdd(counter, 1);
+    const int item = first + __shfl_sync(0xffffffffu, k, 0);
+    if (item >= end) break;  // warp-uniform
+    worklist_item<kPair>(inst, active, prefix, a0, a1, item, src, dst, inst_status, args[warp],
+                         lane);
   }
 }
 
@@ -459,6 +497,7 @@ struct lbm_batch {
   unsigned* d_status = nullptr;  // per instance
   double* d_prof = nullptr;      // 3 per instance
   double* d_tmp = nullptr;       // staging for one instance's density
+  int* d_counters = nullptr;     // dynamic work list: item counter per step and class
   size_t tmp_cells = 0;
   // device work tables and their pinned host staging
   int* d_active = nullptr;
@@ -647,6 +686,21 @@ lbm_status window_graph(lbm_batch* b, int mode, cudaGraphExec_t* out) {
             b->buf[(s + 1) & 1], b->d_status);
       join();
     }
+  } else if (mode == LBM_BATCH_WORKLIST_DYNAMIC) {
+    // one item counter per step and class, zeroed once per window
+    cudaMemsetAsync(b->d_counters, 0, 2 * size_t(W) * sizeof(int), b->stream);
+    for (int s = 0; s < W; ++s) {
+      fork();
+      if (g0 > 0)
+        batch_worklist_dyn_kernel<true><<<g0, kWorklistThreads, 0, b->stream>>>(
+            b->d_inst, b->d_active, b->d_prefix, b->d_n_active, b->buf[s & 1],
+            b->buf[(s + 1) & 1], b->d_status, b->d_counters + s);
+      if (g1 > 0)
+        batch_worklist_dyn_kernel<false><<<g1, kWorklistThreads, 0, s1>>>(
+            b->d_inst, b->d_active, b->d_prefix, b->d_n_active, b->buf[s & 1],
+            b->buf[(s + 1) & 1], b->d_status, b->d_counters + W + s);
+      join();
+    }
   } else {
     fork();
     if (g0 > 0)
@@ -701,7 +755,8 @@ void choose_config(lbm_batch* b, int& mode, int& rows) {
   const size_t cells = active_cells(b);
   const auto eligible = [&](size_t k) {
     const auto& c = b->tuner.candidates[k];
-    if (b->p.rows_per_item > 0 && c.first == LBM_BATCH_WORKLIST &&
+    if (b->p.rows_per_item > 0 &&
+        (c.first == LBM_BATCH_WORKLIST || c.first == LBM_BATCH_WORKLIST_DYNAMIC) &&
         c.second != b->p.rows_per_item)
       return false;
     // a persistent window puts each instance on one SM: only worth trying
@@ -741,7 +796,7 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
   if (!p || !in || !out || count < 1) return LBM_E_INVAL;
   *out = nullptr;
   if (p->window < 2 || p->window % 2 || p->max_steps < 1 || !(p->tol >= 0) ||
-      p->mode < LBM_BATCH_AUTO || p->mode > LBM_BATCH_COOPERATIVE || p->rows_per_item < 0 ||
+      p->mode < LBM_BATCH_AUTO || p->mode > LBM_BATCH_WORKLIST_DYNAMIC || p->rows_per_item < 0 ||
       p->conv < LBM_CONV_COEX || p->conv > LBM_CONV_TREND || !(p->conv_rel >= 0.0) ||
       !(p->trend_tol >= 0.0) ||
       !(p->variant == LBM_VARIANT_AUTO || p->variant == LBM_VARIANT_PAIR ||
@@ -844,6 +899,7 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
   ok &= cudaMalloc(&b->d_status, count * sizeof(unsigned)) == cudaSuccess;
   ok &= cudaMalloc(&b->d_prof, 3 * count * sizeof(double)) == cudaSuccess;
   ok &= cudaMalloc(&b->d_tmp, 3 * b->tmp_cells * sizeof(double)) == cudaSuccess;
+  ok &= cudaMalloc(&b->d_counters, 2 * size_t(p->window) * sizeof(int)) == cudaSuccess;
   ok &= cudaMalloc(&b->d_active, count * sizeof(int)) == cudaSuccess;
   ok &= cudaMalloc(&b->d_prefix, (count + 1) * sizeof(int)) == cudaSuccess;
   ok &= cudaMalloc(&b->d_n_active, 2 * sizeof(int)) == cudaSuccess;
@@ -870,6 +926,7 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
       cudaStreamSynchronize(b->stream) != cudaSuccess)
     return bail(LBM_E_CUDA, "memset");
   for (int rows : {8, 16, 32, 64, 128}) b->tuner.add(LBM_BATCH_WORKLIST, rows);
+  for (int rows : {8, 16, 32, 64}) b->tuner.add(LBM_BATCH_WORKLIST_DYNAMIC, rows);
   b->tuner.add(LBM_BATCH_PERSISTENT, 0);
   {
     // cooperative windows: every CTA resident, one launch per window
@@ -905,6 +962,7 @@ lbm_status lbm_batch_destroy(lbm_batch* b) {
   cudaFree(b->d_status);
   cudaFree(b->d_prof);
   cudaFree(b->d_tmp);
+  cudaFree(b->d_counters);
   cudaFree(b->d_active);
   cudaFree(b->d_prefix);
   cudaFree(b->d_n_active);
@@ -1073,8 +1131,8 @@ lbm_status lbm_batch_run(lbm_batch* b, int max_windows, int* n_active) {
         mode == LBM_BATCH_COOPERATIVE
             ? 1
             : (class_grid(b, mode, 0) > 0 ? 1 : 0) + (class_grid(b, mode, 1) > 0 ? 1 : 0);
-    const unsigned long long nl =
-        (mode == LBM_BATCH_WORKLIST ? kernels * b->p.window : kernels) + 1;
+    const bool per_step = mode == LBM_BATCH_WORKLIST || mode == LBM_BATCH_WORKLIST_DYNAMIC;
+    const unsigned long long nl = (per_step ? kernels * b->p.window : kernels) + 1;
     count_launches(nl);
     b->stats.launches += nl;
     LBM_BCUDA(b, cudaMemcpyAsync(b->h_out, b->d_out, b->count * sizeof(BatchOut),

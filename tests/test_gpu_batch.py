@@ -29,6 +29,8 @@ def droplet(d, seed):
 
 
 @pytest.mark.parametrize("mode,rows", [(lbm.BATCH_WORKLIST, 8), (lbm.BATCH_WORKLIST, 64),
+                                       (lbm.BATCH_WORKLIST_DYNAMIC, 8),
+                                       (lbm.BATCH_WORKLIST_DYNAMIC, 32),
                                        (lbm.BATCH_PERSISTENT, 0), (lbm.BATCH_COOPERATIVE, 16),
                                        (lbm.BATCH_COOPERATIVE, 64), (lbm.BATCH_AUTO, 0)])
 def test_batch_matches_single_domain_bitwise(mode, rows):
