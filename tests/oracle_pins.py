@@ -270,6 +270,8 @@ def pin_step_conservation(lib):
         lat = _lattice(lib, 12, 10, 0.9)
         lat.init_density(rho0)
         m0 = lat.mass()
+        # the mass of f_eq(rho, 0) is the sum of the densities (sum_a w_a = 1)
+        fails += _close("mass of the initial state", m0, float(np.sum(rho0)), rtol=1e-14)
         rc, _ = lat.step(200, sch, tau, sig)
         if rc:
             fails.append(f"scheme {sch} diverged")

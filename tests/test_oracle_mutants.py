@@ -58,6 +58,8 @@ MUTANTS = {
                                     "ux[c] = Fx[c] / (2.0 * rho[c]);\n    uy[c] = Fy[c] / (2.0 * rho[c]);"),
     "at-rest velocity -F/rho": ("ux[c] = -Fx[c] / (2.0 * rho[c]);\n    uy[c] = -Fy[c] / (2.0 * rho[c]);",
                                 "ux[c] = -Fx[c] / rho[c];\n    uy[c] = -Fy[c] / rho[c];"),
+    "mass skips the rest population": ("for (size_t i = 0; i < Q * n; ++i) m += f[i];",
+                                       "for (size_t i = n; i < Q * n; ++i) m += f[i];"),
     "EOS attraction sign": ("return rho * RT * num / den - a * rho * rho;",
                             "return rho * RT * num / den + a * rho * rho;"),
     "EOS denominator (1 - eta)^2": ("double den = (1.0 - eta) * (1.0 - eta) * (1.0 - eta);",
