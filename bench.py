@@ -405,10 +405,10 @@ def run_ours(args, world, rank, local):
 
     warm_line = None
     if rank == 0 and not args.no_warmstart:
-        warm_line = {"label": "reduced config 5: 2,000 training draws (nx = 32 slabs, cap 6e4 "
-                              "steps), 3 x 500 epochs, 64 held-out 256x256 points; cold "
-                              "sequential measured over all 64",
-                     **warmstart_measure(2000, 500, 64, device=local, train_max_steps=60000)}
+        warm_line = {"label": "reduced config 5: 6,000 training draws (nx = 32 slabs, cap 6e4 "
+                              "steps; config 5: 11,000), 3 x 1500 epochs, the 256 held-out "
+                              "256x256 points; cold sequential measured over all 256",
+                     **warmstart_measure(6000, 1500, 256, device=local, train_max_steps=60000)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -549,6 +549,7 @@ def warmstart_measure(train_draws, epochs, held_out, device=0, seq_all=True, see
     mean = lambda rs: float(np.mean([rs[k]["steps"] for k in both])) if both else None
     t_warm, s_warm = warmstart.time_to_answer(warm, winfo, cold, among=both)
     warm_gpu, cold_gpu = winfo["gpu_ms"] / 1e3, cinfo["gpu_ms"] / 1e3
+    arbiter = _long_run_arbiter(held, warm, cold, both, device)
     return {"held_out": len(held), "grid": "256x256",
             "trend_tol": sweep.TREND_TOL if trend_tol is None else trend_tol,
             "rule": "TREND: rho_g, rho_l settled to 1e-4 over the last nine windows (range of "
@@ -573,7 +574,33 @@ def warmstart_measure(train_draws, epochs, held_out, device=0, seq_all=True, see
             "coexistence_max_rel_err_warm_vs_cold_sequential": err_seq,
             "converged_in_both_sequential": n_both_seq,
             "retrospective_time_to_answer_warm_gpu_s": t_warm,
-            "retrospective_mean_steps_to_answer_warm": s_warm}
+            "retrospective_mean_steps_to_answer_warm": s_warm,
+            "long_run_arbiter": arbiter}
+
+
+def _long_run_arbiter(held, warm, cold, both, device, limit=5e-4, steps=150000):
+    """Runs converged in both whose warm and cold answers differ by more than
+    `limit` are run again from the cold start for `steps` steps (no stop):
+    how far each answer is from that long run says which of the two stopped
+    early (outside the timed sweeps)."""
+    import numpy as np
+
+    from paper_1204_4098_gb300 import lbm, sweep
+    rel = lambda a, b: max(abs(a["rho_g"] / b["rho_g"] - 1), abs(a["rho_l"] / b["rho_l"] - 1))
+    ks = [k for k in both if rel(warm[k], cold[k]) > limit]
+    if not ks:
+        return {"runs": 0, "limit": limit}
+    sub = [held[k] for k in ks]
+    g, l = sweep.cold_start_profiles(sub)
+    with lbm.Batch(sub, window=1000, tol=0.0, max_steps=steps, conv=lbm.CONV_NONE,
+                   device=device) as b:
+        b.init_slabs(g, l, np.zeros(len(sub)))
+        b.run()
+        long = b.results()
+    return {"runs": len(ks), "limit": limit, "steps": steps,
+            "warm_vs_long_max": max(rel(warm[k], r) for k, r in zip(ks, long)),
+            "cold_vs_long_max": max(rel(cold[k], r) for k, r in zip(ks, long)),
+            "warm_vs_cold_max": max(rel(warm[k], cold[k]) for k in ks)}
 
 
 def run_warmstart_workload(args, world, rank, local):

@@ -51,11 +51,13 @@ def test_training_matches_oracle_adam():
     assert ref.loss(got.astype(np.float64), X, T) == pytest.approx(ref.loss(want, X, T), rel=1e-3)
 
 
-def test_warm_start_converges_faster_to_the_same_coexistence():
+def test_warm_start_cuts_whole_sweep_gpu_time():
     """Train on cold runs of narrow slabs, then start held-out sweep points
-    from the network's prediction: they converge to the same coexistence
-    densities (within 1e-3) as cold runs, and settle within 1e-3 of them in
-    fewer steps (on average) than runs started from the Maxwell step."""
+    from the network's prediction.  Warm and cold batched runs stop by the
+    same rule (TREND); the whole warm sweep -- fallbacks, divergences and the
+    slowest run included -- takes less GPU time than the whole cold sweep,
+    converges in fewer steps on average, and reaches the same coexistence
+    densities (within 1e-3) on every run converged in both."""
     X, Y, info = warmstart.training_data(1500, seed=40, ny_range=(112, 160), max_steps=60000)
     assert info["converged"] >= 300, info
     model = warmstart.train(X, Y, stages=((800, 3e-3), (800, 5e-4), (800, 1e-4)), batch=64,
@@ -69,9 +71,11 @@ def test_warm_start_converges_faster_to_the_same_coexistence():
     for k in both:
         assert warm[k]["rho_l"] == pytest.approx(cold[k]["rho_l"], rel=1e-3)
         assert warm[k]["rho_g"] == pytest.approx(cold[k]["rho_g"], rel=1e-3)
-    t_warm, s_warm = warmstart.time_to_answer(warm, winfo, cold, among=both)
-    t_cold, s_cold = warmstart.time_to_answer(cold, cinfo, cold, among=both)
-    print(f"warm start: {len(both)} converged in both; to the answer within 1e-3: warm "
-          f"{s_warm:.0f} steps / {t_warm:.2f} s, cold {s_cold:.0f} steps / {t_cold:.2f} s; "
-          f"fallbacks {winfo['fallbacks']}, train loss {model.train_loss:.3e}")
+    s_warm = np.mean([warm[k]["steps"] for k in both])
+    s_cold = np.mean([cold[k]["steps"] for k in both])
+    print(f"warm start: {len(both)} converged in both; whole sweep GPU warm "
+          f"{winfo['gpu_ms'] / 1e3:.2f} s, cold {cinfo['gpu_ms'] / 1e3:.2f} s; mean steps warm "
+          f"{s_warm:.0f}, cold {s_cold:.0f}; fallbacks {winfo['fallbacks']}, train loss "
+          f"{model.train_loss:.3e}")
+    assert winfo["gpu_ms"] < cinfo["gpu_ms"]
     assert s_warm < s_cold
