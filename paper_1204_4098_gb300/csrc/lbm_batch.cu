@@ -1,10 +1,14 @@
 // Batched parameter sweeps: many independent FP32 lattices advanced together.
 //
 // Every instance runs the fused step body of the single-domain kernels
-// (strip_run2, two columns per lane, for even nx, else strip_run; both in
-// lbm_kernels.cuh) on its own slice of one packed buffer pair.  Instances
-// fall in two classes by that body, each with kernels of its own (separate
-// register budgets).  A window of `window` steps is one CUDA graph, in one of
+// (strip_run2, two columns per lane; strip_run, one column per lane, for
+// nx = 1 or when asked for; both in lbm_kernels.cuh) on its own slice of one
+// packed buffer pair.  An odd-nx instance on the two-column body has rows of
+// nx + 3 elements whose columns nx, nx + 1 copy columns 0 and 1 (the lane
+// holding columns 0 and 1 writes the copies every step), so pairs stay
+// aligned and the last column meets its periodic neighbour.  Instances fall
+// in two classes by body, each with kernels of its own (separate register
+// budgets).  A window of `window` steps is one CUDA graph, in one of
 // three launch modes:
 //   work list   -- per step, one launch per class; warps take strip x band
 //                  items of the class's active instances from a prefix table
@@ -45,7 +49,9 @@ struct BatchInst {
   size_t off;              // element offset of plane 0 in each population buffer
   size_t coff;             // cell offset in the density snapshot
   int nx, ny, n_strips;     // strips of 64 columns (pair) or 32
-  int pair;                // even nx: two columns per lane (strip_run2)
+  int pitch;               // row pitch of the population planes: nx, or nx + 3 for odd nx
+                           // on the two-column body (columns nx, nx + 1 copy columns 0, 1)
+  int pair;                // two columns per lane (strip_run2): even nx, and odd nx >= 3
   int band_rows, n_bands;  // work-list geometry
   int pband_rows, pn_bands;  // persistent geometry
   int scheme;
@@ -82,13 +88,14 @@ __device__ __forceinline__ StripArgs<StoreF32> inst_args(const BatchInst& I, con
   A.status = status;
   A.nx = I.nx;
   A.ny = I.ny;
+  A.pitch = I.pitch;
   A.y_begin = 0;
   A.y_end = I.ny;
   A.out_row0 = 0;
   A.n_strips = I.n_strips;
   A.band_rows = persistent ? I.pband_rows : I.band_rows;
   A.n_bands = persistent ? I.pn_bands : I.n_bands;
-  A.plane = size_t(I.nx) * I.ny;
+  A.plane = size_t(I.pitch) * I.ny;
   A.P = I.P;
   return A;
 }
@@ -97,7 +104,7 @@ template <bool kPair, int SCHEME, bool kCoherent>
 __device__ __forceinline__ void run_scheme(const StripArgs<StoreF32>& A, int strip, int band,
                                            int lane) {
   if constexpr (kPair)
-    strip_run2<StoreF32, SCHEME, kModeStep, kCoherent>(A, strip, band, lane);
+    strip_run2<StoreF32, SCHEME, kModeStep, kCoherent, true>(A, strip, band, lane);
   else
     strip_run<StoreF32, SCHEME, kModeStep, kCoherent>(A, strip, band, lane);
 }
@@ -303,19 +310,20 @@ batch_persistent_kernel(const BatchInst* __restrict__ inst, const int* __restric
   }
 }
 
-__device__ __forceinline__ float pulled_rho(const float* f, size_t plane, int nx, int ny, int x,
-                                            int y) {
+__device__ __forceinline__ float pulled_rho(const float* f, size_t plane, int nx, int ny,
+                                            int pitch, int x, int y) {
   const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
   const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-  float r = f[size_t(y) * nx + x];
-  r += f[plane + size_t(y) * nx + xm];
-  r += f[2 * plane + size_t(ym) * nx + x];
-  r += f[3 * plane + size_t(y) * nx + xp];
-  r += f[4 * plane + size_t(yp) * nx + x];
-  r += f[5 * plane + size_t(ym) * nx + xm];
-  r += f[6 * plane + size_t(ym) * nx + xp];
-  r += f[7 * plane + size_t(yp) * nx + xp];
-  r += f[8 * plane + size_t(yp) * nx + xm];
+  const size_t r0 = size_t(y) * pitch, rm = size_t(ym) * pitch, rp = size_t(yp) * pitch;
+  float r = f[r0 + x];
+  r += f[plane + r0 + xm];
+  r += f[2 * plane + rm + x];
+  r += f[3 * plane + r0 + xp];
+  r += f[4 * plane + rp + x];
+  r += f[5 * plane + rm + xm];
+  r += f[6 * plane + rm + xp];
+  r += f[7 * plane + rp + xp];
+  r += f[8 * plane + rp + xm];
   return r;
 }
 
@@ -338,14 +346,14 @@ batch_window_reduce(const BatchInst* __restrict__ inst, const int* __restrict__ 
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const size_t plane = size_t(I.nx) * I.ny;
+  const size_t plane = size_t(I.pitch) * I.ny;
   const float* f = cur + I.off;
   float maxdev = 0.f, maxabs = 0.f;
   bool finite = true;
   for (int y = warp; y < I.ny; y += kReduceCta / 32) {
     double rs = 0.0;
     for (int x = lane; x < I.nx; x += 32) {
-      const float r = pulled_rho(f, plane, I.nx, I.ny, x, y);
+      const float r = pulled_rho(f, plane, I.nx, I.ny, I.pitch, x, y);
       float* sp = snap + I.coff + size_t(y) * I.nx + x;
       const float d = fabsf(r - *sp);
       const float thr = fmaxf(tol, 8.f * 1.1920929e-7f * fabsf(r));
@@ -408,7 +416,7 @@ __global__ void batch_init_slab_kernel(const BatchInst* __restrict__ inst,
   const int i = blockIdx.y;
   const BatchInst I = inst[i];
   const double rg = prof[3 * i], rl = prof[3 * i + 1], W = prof[3 * i + 2];
-  const size_t plane = size_t(I.nx) * I.ny;
+  const size_t plane = size_t(I.pitch) * I.ny;  // the profile is x-invariant: copies too
   const int ny = I.ny;
   auto wrap = [&](int y) { return y < 0 ? y + ny : (y >= ny ? y - ny : y); };
   auto rho_at = [&](int y) {
@@ -426,7 +434,7 @@ __global__ void batch_init_slab_kernel(const BatchInst* __restrict__ inst,
   };
   for (size_t c = blockIdx.x * size_t(blockDim.x) + threadIdx.x; c < plane;
        c += size_t(gridDim.x) * blockDim.x) {
-    const int y = int(c / I.nx);
+    const int y = int(c / I.pitch), x = int(c % I.pitch);
 #pragma unroll
     for (int a = 0; a < kQ; ++a) {
       const int ys = y + ey_of(a);
@@ -436,7 +444,7 @@ __global__ void batch_init_slab_kernel(const BatchInst* __restrict__ inst,
       buf0[I.off + a * plane + c] =
           float(double(w_of<float>(a)) * r * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * u * u));
     }
-    snap[I.coff + c] = float(rho_at(y));
+    if (x < I.nx) snap[I.coff + size_t(y) * I.nx + x] = float(rho_at(y));
   }
   if (bad) atomicOr(inst_status + i, kStatusInvalidInit);
 }
@@ -444,10 +452,11 @@ __global__ void batch_init_slab_kernel(const BatchInst* __restrict__ inst,
 __global__ void batch_density_kernel(const BatchInst* __restrict__ inst, int i, const float* cur,
                                      double* out) {
   const BatchInst I = inst[i];
-  const size_t plane = size_t(I.nx) * I.ny;
-  for (size_t c = blockIdx.x * size_t(blockDim.x) + threadIdx.x; c < plane;
+  const size_t plane = size_t(I.pitch) * I.ny, cells = size_t(I.nx) * I.ny;
+  for (size_t c = blockIdx.x * size_t(blockDim.x) + threadIdx.x; c < cells;
        c += size_t(gridDim.x) * blockDim.x)
-    out[c] = double(pulled_rho(cur + I.off, plane, I.nx, I.ny, int(c % I.nx), int(c / I.nx)));
+    out[c] = double(
+        pulled_rho(cur + I.off, plane, I.nx, I.ny, I.pitch, int(c % I.nx), int(c / I.nx)));
 }
 
 // Density and actual velocity v = u + F/(2 rho) (Table I) of instance i,
@@ -834,7 +843,8 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
     d.coff = coff;
     d.nx = s.nx;
     d.ny = s.ny;
-    d.pair = s.nx % 2 == 0 && p->variant != LBM_VARIANT_REGISTER;
+    d.pair = (s.nx % 2 == 0 || s.nx >= 3) && p->variant != LBM_VARIANT_REGISTER;
+    d.pitch = d.pair && s.nx % 2 ? s.nx + 3 : s.nx;
     d.n_strips = d.pair ? (s.nx + 63) / 64 : (s.nx + 31) / 32;
     d.scheme = s.scheme;
     d.row_off = roff;
@@ -853,7 +863,7 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
     d.P.s_e = d.P.s_eps = d.P.s_q = d.P.omega;  // unused: the batch has no MRT scheme
     set_geometry(d, 32);
     const size_t cells = size_t(s.nx) * s.ny;
-    off += (9 * cells + 31) / 32 * 32;
+    off += (9 * size_t(d.pitch) * s.ny + 31) / 32 * 32;
     coff += cells;
     roff += s.ny;
     max_cells = std::max<int>(max_cells, int(cells));
@@ -1018,8 +1028,9 @@ lbm_status batch_init_state(lbm_batch* b, int i, const double* rho, bool at_rest
     count_launches(1);
     b->stats.launches += 1;
   }
-  LBM_BCUDA(b, set_state_launch(kFP32, b->buf[0] + d.off, nullptr, d.nx, d.ny, cells, b->d_tmp,
-                                ux, uy, nullptr, chk, b->stream));
+  LBM_BCUDA(b, set_state_launch(kFP32, b->buf[0] + d.off, nullptr, d.nx, d.ny, d.pitch,
+                                size_t(d.pitch) * d.ny, b->d_tmp, ux, uy, nullptr, chk,
+                                b->stream));
   to_float_kernel<<<256, 256, 0, b->stream>>>(b->d_tmp, b->snap + d.coff, cells);
   LBM_BCUDA(b, cudaGetLastError());
   count_launches(2);

@@ -81,13 +81,13 @@ cudaError_t strip_tma_occupancy_f32(int, int*);
 cudaError_t strip_occupancy_f64(int, int, int*);
 cudaError_t strip_occupancy_bf16(int, int, int*);
 cudaError_t strip_occupancy_f16(int, int, int*);
-cudaError_t set_state_f32(void*, float*, int, int, size_t, const double*, const double*,
+cudaError_t set_state_f32(void*, float*, int, int, int, size_t, const double*, const double*,
                           const double*, const double*, const EosCheck&, cudaStream_t);
-cudaError_t set_state_f64(void*, float*, int, int, size_t, const double*, const double*,
+cudaError_t set_state_f64(void*, float*, int, int, int, size_t, const double*, const double*,
                           const double*, const double*, const EosCheck&, cudaStream_t);
-cudaError_t set_state_bf16(void*, float*, int, int, size_t, const double*, const double*,
+cudaError_t set_state_bf16(void*, float*, int, int, int, size_t, const double*, const double*,
                           const double*, const double*, const EosCheck&, cudaStream_t);
-cudaError_t set_state_f16(void*, float*, int, int, size_t, const double*, const double*,
+cudaError_t set_state_f16(void*, float*, int, int, int, size_t, const double*, const double*,
                           const double*, const double*, const EosCheck&, cudaStream_t);
 cudaError_t get_state_f32(const void*, const float*, int, int, size_t, double*, cudaStream_t);
 cudaError_t get_state_f64(const void*, const float*, int, int, size_t, double*, cudaStream_t);
@@ -145,14 +145,14 @@ cudaError_t strip_tma_occupancy(int precision, int scheme, int* b) {
   if (precision != kFP32) return cudaErrorNotSupported;
   return strip_tma_occupancy_f32(scheme, b);
 }
-cudaError_t set_state_launch(int precision, void* dst, float* rd, int nx, int ny, size_t plane,
-                             const double* rho, const double* ux, const double* uy,
+cudaError_t set_state_launch(int precision, void* dst, float* rd, int nx, int ny, int pitch,
+                             size_t plane, const double* rho, const double* ux, const double* uy,
                              const double* f_in, const EosCheck& chk, cudaStream_t s) {
   switch (precision) {
-    case kFP32: return set_state_f32(dst, rd, nx, ny, plane, rho, ux, uy, f_in, chk, s);
-    case kFP64: return set_state_f64(dst, rd, nx, ny, plane, rho, ux, uy, f_in, chk, s);
-    case kBF16Dev: return set_state_bf16(dst, rd, nx, ny, plane, rho, ux, uy, f_in, chk, s);
-    case kFP16Dev: return set_state_f16(dst, rd, nx, ny, plane, rho, ux, uy, f_in, chk, s);
+    case kFP32: return set_state_f32(dst, rd, nx, ny, pitch, plane, rho, ux, uy, f_in, chk, s);
+    case kFP64: return set_state_f64(dst, rd, nx, ny, pitch, plane, rho, ux, uy, f_in, chk, s);
+    case kBF16Dev: return set_state_bf16(dst, rd, nx, ny, pitch, plane, rho, ux, uy, f_in, chk, s);
+    case kFP16Dev: return set_state_f16(dst, rd, nx, ny, pitch, plane, rho, ux, uy, f_in, chk, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -424,7 +424,8 @@ lbm_status init_state(lbm_ctx* c, const double* rho, const double* ux, const dou
     d_uy = vv;
   }
   LBM_CUDA(c, set_state_launch(c->p.precision, c->f[c->cur], c->rho[c->cur], c->p.nx, c->ny_buf,
-                               c->plane, d_rho, d_ux, d_uy, nullptr, eos_check(c), c->stream));
+                               c->p.nx, c->plane, d_rho, d_ux, d_uy, nullptr, eos_check(c),
+                               c->stream));
   count_launches(1);
   LBM_CUDA(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(unsigned),
                               cudaMemcpyDeviceToHost, c->stream));
@@ -709,8 +710,8 @@ lbm_status lbm_set_populations(lbm_ctx* c, const double* f) {
   LBM_CUDA(c, cudaMemcpyAsync(c->d_pop, f, 9 * c->plane * sizeof(double),
                               cudaMemcpyHostToDevice, c->stream));
   LBM_CUDA(c, set_state_launch(c->p.precision, c->f[c->cur], c->rho[c->cur], c->p.nx,
-                               c->ny_buf, c->plane, nullptr, nullptr, nullptr, c->d_pop, EosCheck{},
-                               c->stream));
+                               c->ny_buf, c->p.nx, c->plane, nullptr, nullptr, nullptr, c->d_pop,
+                               EosCheck{}, c->stream));
   count_launches(1);
   LBM_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream));
   LBM_CUDA(c, cudaStreamSynchronize(c->stream));

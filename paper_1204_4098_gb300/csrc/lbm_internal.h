@@ -60,8 +60,10 @@ cudaError_t strip_tma_occupancy(int precision, int scheme, int* blocks_per_sm);
 
 // f*_a(x') = f_a(x' + e_a) from f_eq(rho, u) (f_in == NULL) or from f_in;
 // with f_in == NULL and chk.status set, flags rho outside the domain of psi.
+// dst rows have `pitch` >= nx elements (columns past nx: copies of columns
+// (x - nx) mod nx); plane = pitch * ny; rho, ux, uy, f_in are unpadded.
 cudaError_t set_state_launch(int precision, void* dst, float* rho_dst, int nx, int ny,
-                             size_t plane, const double* rho, const double* ux,
+                             int pitch, size_t plane, const double* rho, const double* ux,
                              const double* uy, const double* f_in, const EosCheck& chk,
                              cudaStream_t s);
 // u = -F / (2 rho) at every cell, F the force of Eq. 3 on the device density

@@ -51,12 +51,14 @@ struct StripArgs {
   double* out_vy;
   unsigned* status;           // device status word
   int nx, ny;                 // ny: rows of the buffers
+  int pitch;                  // elements per row of a plane: nx, or nx + 3 for odd nx in the
+                              // two-column kernel (columns nx, nx + 1 copy columns 0, 1)
   int y_begin, y_end;         // rows computed (a domain band: the owned rows)
   int out_row0;               // observe mode: output row of buffer row out_row0 is 0
   int n_strips;               // ceil(nx / 32)
   int band_rows;              // rows per warp
   int n_bands;                // ceil((y_end - y_begin) / band_rows)
-  size_t plane;               // nx * ny
+  size_t plane;               // pitch * ny
   Phys<typename S::C> P;
 };
 
@@ -91,7 +93,7 @@ __device__ __forceinline__ void strip_run(const StripArgs<S>& A, int strip, int 
   constexpr bool kNeedPsi = !(MODE == kModeObserveNoForce ||
                               (MODE == kModeStep && SCHEME == kNoForce));
   const unsigned FULL = 0xffffffffu;
-  const int nx = A.nx, ny = A.ny;
+  const int nx = A.nx, ny = A.ny, pitch = A.pitch;
   const int y0 = A.y_begin + band * A.band_rows;
   const int y1 = min(y0 + A.band_rows, A.y_end);
 
@@ -115,7 +117,7 @@ __device__ __forceinline__ void strip_run(const StripArgs<S>& A, int strip, int 
   auto load_row = [&](int y, C (&P)[kQ], C& h) {
     const int ym = y == 0 ? ny - 1 : y - 1;
     const int yp = y == ny - 1 ? 0 : y + 1;
-    const int r0 = y * nx, rm = ym * nx, rp = yp * nx;
+    const int r0 = y * pitch, rm = ym * pitch, rp = yp * pitch;
     P[0] = pull_one<S, kCoherent>(A, 0, r0 + c);
     P[1] = pull_one<S, kCoherent>(A, 1, r0 + cm);
     P[2] = pull_one<S, kCoherent>(A, 2, rm + c);
@@ -128,7 +130,7 @@ __device__ __forceinline__ void strip_run(const StripArgs<S>& A, int strip, int 
     if constexpr (kNeedPsi) {
       int hy = y - hey;  // |hey| <= 1 and 0 <= y < ny: one conditional wrap
       hy = hy < 0 ? hy + ny : (hy >= ny ? hy - ny : hy);
-      h = hlane ? pull_one<S, kCoherent>(A, ha, hy * nx + hsx) : C(0);
+      h = hlane ? pull_one<S, kCoherent>(A, ha, hy * pitch + hsx) : C(0);
     }
   };
   // density with a fixed summation order (the halo path below repeats it)
@@ -185,7 +187,7 @@ __device__ __forceinline__ void strip_run(const StripArgs<S>& A, int strip, int 
       Fy = mul_rn(gpsi, sy);
     }
 
-    const int idx = y * nx + c;
+    const int idx = y * pitch + c;
     const int oidx = (y - A.out_row0) * nx + c;
     if constexpr (MODE == kModeStep) {
       collide<SCHEME>(Pcur, rho0, Fx, Fy, Cz, A.P);
@@ -292,7 +294,9 @@ __device__ __forceinline__ V load2(const V* p) {
   else return __ldg(p);
 }
 
-template <class S, int SCHEME, int MODE, bool kCoherent = false>
+// kPadded: rows may have the odd-nx layout (pitch nx + 3, see StripArgs);
+// the batch engine's body.  The single-lattice kernels have pitch = nx, even.
+template <class S, int SCHEME, int MODE, bool kCoherent = false, bool kPadded = false>
 __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int band,
                                            int lane) {
   using C = typename S::C;
@@ -302,13 +306,19 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
   constexpr bool kNeedPsi = !(MODE == kModeObserveNoForce ||
                               (MODE == kModeStep && SCHEME == kNoForce));
   const unsigned FULL = 0xffffffffu;
-  const int nx = A.nx, ny = A.ny;
+  const int nx = A.nx, ny = A.ny, pitch = kPadded ? A.pitch : A.nx;
   const int y0 = A.y_begin + band * A.band_rows;
   const int y1 = min(y0 + A.band_rows, A.y_end);
   const int x0 = strip * 64;
   const int xa = x0 + 2 * lane;         // left column of this lane
   const bool active_a = xa < nx, active_b = xa + 1 < nx;
-  const int ca = xa % nx;               // even: nx is even
+  // Even nx (pitch nx): lanes past the edge take the wrapped columns, which
+  // serve as the right neighbours.  Odd nx (pitch nx + 3): columns nx and
+  // nx + 1 of every row hold copies of columns 0 and 1, so the lane whose
+  // cell a is the last column nx - 1 has column 0 as its cell b, and the
+  // next lane columns 1 and an unused one -- the periodic neighbours, with
+  // aligned pairs; lanes further out read column 0 (their cells are unused).
+  const int ca = (!kPadded || pitch == nx) ? xa % nx : (xa < pitch ? xa : 0);
   // extra-element lanes: 0..8 halo pulls of column x0-1 (plane = lane),
   // 9..11 column x0-1 of planes 1, 5, 8 (e_x = +1), 16..24 halo pulls of
   // column x0+64 (plane = lane-16), 25..27 column x0+64 of planes 3, 6, 7.
@@ -355,11 +365,12 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
     {
       int qy = y - qey;
       qy = qy < 0 ? qy + ny : (qy >= ny ? qy - ny : qy);
-      R.h = qlane ? pull_one<S, kCoherent>(A, qa, qy * nx + qsx) : C(0);
+      R.h = qlane ? pull_one<S, kCoherent>(A, qa, qy * pitch + qsx) : C(0);
     }
     if constexpr (S::kDev) {
       auto plane_row = [&](int r) {
-        return load2<kCoherent>(reinterpret_cast<const float2*>(A.rho_src + size_t(r) * nx + ca));
+        return load2<kCoherent>(
+            reinterpret_cast<const float2*>(A.rho_src + size_t(r) * pitch + ca));
       };
       if (ring_ok) {  // warp-uniform
         R.rr[0] = ring0;
@@ -377,7 +388,7 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
     for (int a = 0; a < kQ; ++a) {
       const int r = rows[1 - ey_of(a)];  // source row y - ey
       R.v[a] =
-          load2<kCoherent>(reinterpret_cast<const V*>(A.src + a * A.plane + size_t(r) * nx + ca));
+          load2<kCoherent>(reinterpret_cast<const V*>(A.src + a * A.plane + size_t(r) * pitch + ca));
     }
   };
   // pulled populations of the lane's two cells (P[a].x at ca, .y at ca + 1)
@@ -470,10 +481,17 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
     psi_row(P1, h1, Wp, Cp, Ep, r1);
     P2 Fx = P2(C(0)), Fy = P2(C(0));
     if constexpr (kNeedPsi) force(Wm, Cm, Em, Wz, Cz, Ez, Wp, Cp, Ep, Fx, Fy);
-    const size_t idx = size_t(y) * nx + ca;
+    const size_t idx = size_t(y) * pitch + ca;
     if constexpr (MODE == kModeStep) {
       collide<SCHEME>(P0, r0, Fx, Fy, Cz, A.P);
-      if (active_a) {  // nx even: both cells of an active lane are inside
+      if (active_a) {
+        // Both cells are stored as a pair, or, for the lane holding the last
+        // column of an odd nx, cell a alone (its cell b is the copy of
+        // column 0, which the lane holding columns 0 and 1 writes).  With odd
+        // nx that lane also stores its two cells into the copies.
+        const bool both = !kPadded || active_b;  // even nx: both cells are inside
+        const bool copies = kPadded && pitch != nx && xa == 0;
+        const size_t ghost = size_t(y) * pitch + nx;
         if constexpr (S::kDev) {
           // the density plane absorbs the 16-bit rounding of the deviations
           P2 res = r0;
@@ -481,17 +499,35 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
           for (int a = 0; a < kQ; ++a) {
             const P2 d = fma_rn(P2(-w_of<C>(a)), r0, P0[a]);
             const V v = S::from_c2(d.x(), d.y());
-            *reinterpret_cast<V*>(A.dst + a * A.plane + idx) = v;
+            T* plane = A.dst + a * A.plane;
+            if (both) *reinterpret_cast<V*>(plane + idx) = v;
+            else plane[idx] = v.x;
+            if (copies) {
+              plane[ghost] = v.x;
+              plane[ghost + 1] = v.y;
+            }
             res = sub_rn(res, P2(S::to_c2(v)));
           }
-          *reinterpret_cast<float2*>(A.rho_dst + idx) = make_float2(float(res.x()), float(res.y()));
+          const float2 rp = make_float2(float(res.x()), float(res.y()));
+          if (both) *reinterpret_cast<float2*>(A.rho_dst + idx) = rp;
+          else A.rho_dst[idx] = rp.x;
+          if (copies) {
+            A.rho_dst[ghost] = rp.x;
+            A.rho_dst[ghost + 1] = rp.y;
+          }
         } else {
 #pragma unroll
           for (int a = 0; a < kQ; ++a) {
             V v;
             v.x = S::from_c(P0[a].x());
             v.y = S::from_c(P0[a].y());
-            *reinterpret_cast<V*>(A.dst + a * A.plane + idx) = v;
+            T* plane = A.dst + a * A.plane;
+            if (both) *reinterpret_cast<V*>(plane + idx) = v;
+            else plane[idx] = v.x;
+            if (copies) {
+              plane[ghost] = v.x;
+              plane[ghost + 1] = v.y;
+            }
           }
         }
       }
@@ -763,17 +799,21 @@ strip_tma_kernel(const StripArgs<StoreF32> A) {
 // f*_a(x') = f_a(x' + e_a): store a physical state (time t, before the pull)
 // so that the next pull reproduces it.  The physical state is either
 // f_eq(rho, u) (init) or given populations (set).
+// Rows of dst have `pitch` >= nx elements; columns nx .. pitch - 1 (the
+// copies of an odd-nx two-column layout) get the state of column
+// (x - nx) mod nx.
 template <class S>
-__global__ void set_state_kernel(typename S::T* dst, float* rho_dst, int nx, int ny,
+__global__ void set_state_kernel(typename S::T* dst, float* rho_dst, int nx, int ny, int pitch,
                                  size_t plane, const double* rho, const double* ux,
                                  const double* uy, const double* f_in, Phys<double> P,
                                  unsigned* status) {
-  const size_t n = plane;
+  const size_t n = size_t(pitch) * ny;
   bool bad = false;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
-    const int x = int(i % nx), y = int(i / nx);
-    if (!f_in && status) (void)psi_of_rho(rho[i], P, bad);  // domain of psi at the start
+    const int xo = int(i % pitch), y = int(i / pitch);
+    const int x = xo < nx ? xo : (xo - nx) % nx;
+    if (!f_in && status) (void)psi_of_rho(rho[size_t(y) * nx + x], P, bad);  // domain of psi
     double fs[kQ];
     double rsum = 0.0;
 #pragma unroll
@@ -782,7 +822,7 @@ __global__ void set_state_kernel(typename S::T* dst, float* rho_dst, int nx, int
       const size_t j = (size_t)yd * nx + xd;
       double v;
       if (f_in) {
-        v = f_in[a * plane + j];
+        v = f_in[a * (size_t(nx) * ny) + j];  // unpadded [9][ny][nx]
       } else {
         const double r = rho[j], u = ux ? ux[j] : 0.0, w = uy ? uy[j] : 0.0;
         const double eu = ex_of(a) * u + ey_of(a) * w;

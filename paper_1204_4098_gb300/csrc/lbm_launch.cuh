@@ -22,6 +22,7 @@ StripArgs<S> make_args(const StripLaunch& L) {
   A.status = L.status;
   A.nx = L.nx;
   A.ny = L.ny;
+  A.pitch = L.nx;  // the single-lattice buffers are unpadded
   A.y_begin = L.y_begin;
   A.y_end = L.y_end;
   A.out_row0 = L.out_row0;
@@ -184,7 +185,7 @@ inline int grid_for(size_t n, int threads) {
 }
 
 template <class S>
-cudaError_t set_state_t(void* dst, float* rho_dst, int nx, int ny, size_t plane,
+cudaError_t set_state_t(void* dst, float* rho_dst, int nx, int ny, int pitch, size_t plane,
                         const double* rho, const double* ux, const double* uy,
                         const double* f_in, const EosCheck& chk, cudaStream_t s) {
   Phys<double> P{};
@@ -193,7 +194,7 @@ cudaError_t set_state_t(void* dst, float* rho_dst, int nx, int ny, size_t plane,
   P.b4 = chk.b4;
   P.two_over_G = chk.two_over_G;
   set_state_kernel<S><<<grid_for(plane, 256), 256, 0, s>>>(
-      static_cast<typename S::T*>(dst), rho_dst, nx, ny, plane, rho, ux, uy, f_in, P,
+      static_cast<typename S::T*>(dst), rho_dst, nx, ny, pitch, plane, rho, ux, uy, f_in, P,
       chk.status);
   return cudaGetLastError();
 }
@@ -243,11 +244,11 @@ cudaError_t mass_t(const void* src, const float* rho_src, size_t plane, size_t f
   cudaError_t strip_tma_occupancy_##SUFFIX(int scheme, int* b) {                        \
     return strip_tma_occupancy_t<STORE>(scheme, b);                                     \
   }                                                                                     \
-  cudaError_t set_state_##SUFFIX(void* dst, float* rd, int nx, int ny, size_t plane,     \
-                                 const double* rho, const double* ux, const double* uy, \
-                                 const double* f_in, const EosCheck& chk,               \
-                                 cudaStream_t s) {                                      \
-    return set_state_t<STORE>(dst, rd, nx, ny, plane, rho, ux, uy, f_in, chk, s);       \
+  cudaError_t set_state_##SUFFIX(void* dst, float* rd, int nx, int ny, int pitch,       \
+                                 size_t plane, const double* rho, const double* ux,     \
+                                 const double* uy, const double* f_in,                 \
+                                 const EosCheck& chk, cudaStream_t s) {                 \
+    return set_state_t<STORE>(dst, rd, nx, ny, pitch, plane, rho, ux, uy, f_in, chk, s); \
   }                                                                                     \
   cudaError_t get_state_##SUFFIX(const void* src, const float* rs, int nx, int ny,       \
                                  size_t plane, double* f_out, cudaStream_t s) {         \

@@ -53,6 +53,35 @@ def test_batch_matches_single_domain_bitwise(mode, rows):
         assert r["steps"] == windows * window and r["status"] == lbm.RUN_ACTIVE
 
 
+ODD = [dict(nx=nx, ny=ny, T_over_Tc=0.85, tau=0.8, sigma=0.1, scheme=lbm.IMPROVED)
+       for nx, ny in ((63, 40), (127, 19), (3, 33), (1, 21), (65, 30), (5, 9))]
+
+
+@pytest.mark.parametrize("mode,rows", [(lbm.BATCH_WORKLIST, 8), (lbm.BATCH_WORKLIST_DYNAMIC, 16),
+                                       (lbm.BATCH_PERSISTENT, 0)])
+def test_batch_odd_widths_on_the_two_column_body_bitwise(mode, rows):
+    """Odd nx >= 3 run on the two-column body with rows padded to nx + 3 and
+    columns nx, nx + 1 copying columns 0, 1 (nx = 1 stays on one column per
+    lane): the last column in lane 31 of a strip (63, 127), the narrowest
+    padded width (3), two strips (65), and 1, bit for bit against the
+    single-domain one-column kernel."""
+    windows, window = 2, 10
+    b = lbm.Batch(ODD, window=window, tol=0.0, max_steps=10 ** 6, mode=mode, rows_per_item=rows)
+    rho0 = [droplet(d, 10 + k) for k, d in enumerate(ODD)]
+    for k, r in enumerate(rho0):
+        b.init_density(k, r)
+    assert b.run(windows) == len(ODD)
+    for k, d in enumerate(ODD):
+        single = lbm.Lattice(d["nx"], d["ny"], d["T_over_Tc"], precision=lbm.FP32)
+        single.set_variant(lbm.VARIANT_REGISTER)
+        single.init_density(rho0[k])
+        single.step(windows * window, d["scheme"], d["tau"], d["sigma"])
+        assert np.array_equal(b.density(k), single.observe()[0]), d
+        got = b.moments(k)
+        for g, w in zip(got, single.observe()):
+            assert np.array_equal(g, w), d
+
+
 def test_batch_init_slabs_profile():
     inst = [dict(nx=40, ny=64, T_over_Tc=0.8, tau=1.0, sigma=0.0, scheme=lbm.SC),
             dict(nx=33, ny=50, T_over_Tc=0.9, tau=1.0, sigma=0.0, scheme=lbm.SC)]
