@@ -65,6 +65,10 @@ MEASURED_TRAFFIC = {
     # (-k strip2_kernel -c 3 at 4096^2: 615.3 MB read + 555.5 MB written per
     # launch on average), scaled to 8192^2 by the cell count (x 4)
     ("ee1858b957fb85d9", "fp32", 8192, "pair"): 4.6832e9,
+    # the same kernel source after the padded-pitch template parameter of the
+    # batch body (single lattices unpadded): 4096^2 capture 615.3 MB read +
+    # 555.6 MB written per launch, x4 cells
+    ("8f05beea9b05b658", "fp32", 8192, "pair"): 4.6838e9,
 }
 
 
@@ -622,7 +626,9 @@ def run_band_workload(args, world, rank, local):
     y-slabs (halo.band_partition), one per rank, each step followed by the
     halo exchange (two rows x 9 populations to each neighbour, NCCL point to
     point on device buffers).  At N = 1 the band exchanges with itself (the
-    periodic wrap).  value = all cells x steps / the slowest rank's time."""
+    periodic wrap).  For N > 1 the exchange runs on a second stream while the
+    interior rows are computed; the other path is timed beside it.
+    value = all cells x steps / the slowest rank's time."""
     import torch
     import torch.distributed as dist
 
@@ -635,18 +641,22 @@ def run_band_workload(args, world, rank, local):
     rho0, _ = workload_density(n, 0)
     band = halo.BandLattice(n, n, 0.85, rho0, rank=rank, world=world, device=local,
                             group=group)
-    band.step(args.warmup, lbm.IMPROVED, 0.8, 0.1)
-    torch.cuda.synchronize()
-    dist_barrier(world)
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    launches0 = lbm.launch_count()
-    start.record(band.stream)
-    st = band.step(args.steps, lbm.IMPROVED, 0.8, 0.1)
-    end.record(band.stream)
-    torch.cuda.synchronize()
-    dist_barrier(world)
-    assert st == lbm.LBM_OK
-    ms = dist_max(start.elapsed_time(end), world)
+    def timed(overlap):
+        band.step(args.warmup, lbm.IMPROVED, 0.8, 0.1, overlap=overlap)
+        torch.cuda.synchronize()
+        dist_barrier(world)
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        launches0 = lbm.launch_count()
+        start.record(band.stream)
+        st = band.step(args.steps, lbm.IMPROVED, 0.8, 0.1, overlap=overlap)
+        end.record(band.stream)
+        torch.cuda.synchronize()
+        dist_barrier(world)
+        assert st == lbm.LBM_OK
+        return dist_max(start.elapsed_time(end), world), lbm.launch_count() - launches0
+
+    ms_other, _ = timed(world == 1)
+    ms, launches = timed(world > 1)  # the default of halo.BandLattice.step
     if rank == 0:
         line = {"metric": METRIC, "workload": f"{n}x{n} single lattice in {world} y-slabs "
                                               "with halo exchange (strong scaling)",
@@ -655,7 +665,11 @@ def run_band_workload(args, world, rank, local):
                 "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong",
                 "data": "synthetic", "dtype": "f32", "rows_per_rank": band.rows,
                 "halo_bytes_per_message": band.lat.halo_bytes(),
-                "gpu_launches": lbm.launch_count() - launches0}
+                "exchange": "overlapped with the interior rows (boundary rows first)"
+                            if world > 1 else "self-exchange after the step (nothing to hide)",
+                ("without_overlap_MLUPS" if world > 1 else "with_overlap_MLUPS"):
+                    n * n * args.steps / (ms_other * 1e-3) / 1e6,
+                "gpu_launches": launches}
         print(json.dumps(line), flush=True)
     band.close()
 

@@ -147,6 +147,20 @@ lbm_status lbm_band_halo_pack(lbm_ctx *ctx, void *d_lo, void *d_hi);
  * waiting; the next step on the context stream reads them. */
 lbm_status lbm_band_halo_unpack(lbm_ctx *ctx, const void *d_below, const void *d_above);
 
+/* One step of a band with its halo exchange overlapped with the interior:
+ * queues on the context stream the step of the two lowest and the two
+ * highest owned rows, their copies into d_lo and d_hi (as
+ * lbm_band_halo_pack), an event that comm_stream (a CUDA stream of the
+ * caller, may be NULL) is made to wait for, and then the step of the
+ * interior rows.  The caller sends d_lo / d_hi and receives the neighbours'
+ * on comm_stream, makes the context stream wait for that, and unpacks
+ * (lbm_band_halo_unpack) before the next step.  Bands of fewer than 5 rows
+ * compute all rows before packing.  Same results as lbm_step + pack: the
+ * rows are the same computations, only their order differs.  Returns
+ * without waiting; the errors of lbm_step_async and lbm_band_halo_pack. */
+lbm_status lbm_band_step_overlap(lbm_ctx *ctx, int scheme, double tau, double sigma,
+                                 void *d_lo, void *d_hi, void *comm_stream);
+
 /* Set the state to f_a = f_eq(rho, u) (Eq. 2) at every cell.  rho is a host
  * array of ny*nx doubles; ux and uy may be NULL (zero velocity).  Copied to
  * the device during the call.  LBM_E_INVAL if any rho is outside the domain

@@ -223,6 +223,7 @@ struct lbm_ctx {
   bool band = false;
   int ny_buf = 0;
   int row0 = 0;
+  cudaEvent_t packed = nullptr;  // overlapped band step: boundary rows packed
   std::string err;
 };
 
@@ -294,7 +295,7 @@ int pick_variant(const lbm_ctx* c, int mode) {
 
 // Warp-strip geometry of one wave (strip_geometry) over the resident warp
 // slots of the variant's kernel.
-lbm_status geometry(lbm_ctx* c, int scheme, int mode, StripLaunch& L, int& grid) {
+lbm_status geometry(lbm_ctx* c, int scheme, int mode, StripLaunch& L, int& grid, int rows = -1) {
   int bps = 0;
   const int variant = pick_variant(c, mode);
   if (variant == LBM_VARIANT_STAGED)
@@ -306,8 +307,8 @@ lbm_status geometry(lbm_ctx* c, int scheme, int mode, StripLaunch& L, int& grid)
   if (bps < 1) bps = 1;
   const int warps_per_cta = kStripCtaThreads / 32;
   const long long resident = (long long)c->sm_count * bps * warps_per_cta;
-  const StripGeometry g = strip_geometry(c->p.nx, c->p.ny, variant, resident, warps_per_cta,
-                                         c->band_rows_override);
+  const StripGeometry g = strip_geometry(c->p.nx, rows < 0 ? c->p.ny : rows, variant, resident,
+                                         warps_per_cta, c->band_rows_override);
   L.n_strips = g.n_strips;
   L.band_rows = g.band_rows;
   L.n_bands = g.n_bands;
@@ -325,6 +326,43 @@ lbm_status ensure_tmp(lbm_ctx* c, double** buf, size_t count) {
   return LBM_OK;
 }
 
+// Launch arguments of a step with relaxation time tau and sigma.
+StripLaunch step_launch(lbm_ctx* c, double tau, double sigma) {
+  StripLaunch L = base_launch(c);
+  L.tau = tau;
+  L.omega = 1.0 / tau;
+  L.sigma_ups = sigma / (tau - 0.5);
+  L.guo = 1.0 - 1.0 / (2.0 * tau);
+  L.s_e = c->mrt[0] > 0.0 ? c->mrt[0] : 1.0 / tau;
+  L.s_eps = c->mrt[1] > 0.0 ? c->mrt[1] : 1.0 / tau;
+  L.s_q = c->mrt[2] > 0.0 ? c->mrt[2] : 1.0 / tau;
+  return L;
+}
+
+// One step of buffer rows [r0, r1) from buffer s into buffer d (no flip).
+lbm_status launch_rows(lbm_ctx* c, int scheme, StripLaunch L, int r0, int r1, int s, int d) {
+  if (r1 <= r0) return LBM_OK;
+  L.y_begin = r0;
+  L.y_end = r1;
+  L.src = c->f[s];
+  L.dst = c->f[d];
+  L.rho_src = c->rho[s];
+  L.rho_dst = c->rho[d];
+  int grid = 0;
+  lbm_status st = geometry(c, scheme, kStepMode, L, grid, r1 - r0);
+  if (st != LBM_OK) return st;
+  const int variant = pick_variant(c, kStepMode);
+  cudaError_t e =
+      variant == LBM_VARIANT_STAGED
+          ? strip_tma_launch(c->p.precision, scheme, L, grid, c->stream)
+          : variant == LBM_VARIANT_PAIR
+                ? strip2_launch(c->p.precision, scheme, kStepMode, L, grid, c->stream)
+                : strip_launch(c->p.precision, scheme, kStepMode, L, grid, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
+  count_launches(1);
+  return LBM_OK;
+}
+
 lbm_status queue_steps(lbm_ctx* c, int n, int scheme, double tau, double sigma) {
   if (!c) return LBM_E_INVAL;
   if (n < 0) return fail(c, LBM_E_INVAL, "n must be >= 0");
@@ -335,14 +373,7 @@ lbm_status queue_steps(lbm_ctx* c, int n, int scheme, double tau, double sigma) 
   if (c->band && n > 1)
     return fail(c, LBM_E_INVAL, "a band advances one step per call (exchange halos between)");
   if (n == 0) return LBM_OK;
-  StripLaunch L = base_launch(c);
-  L.tau = tau;
-  L.omega = 1.0 / tau;
-  L.sigma_ups = sigma / (tau - 0.5);
-  L.guo = 1.0 - 1.0 / (2.0 * tau);
-  L.s_e = c->mrt[0] > 0.0 ? c->mrt[0] : 1.0 / tau;
-  L.s_eps = c->mrt[1] > 0.0 ? c->mrt[1] : 1.0 / tau;
-  L.s_q = c->mrt[2] > 0.0 ? c->mrt[2] : 1.0 / tau;
+  StripLaunch L = step_launch(c, tau, sigma);
   int grid = 0;
   lbm_status st = geometry(c, scheme, kStepMode, L, grid);
   if (st != LBM_OK) return st;
@@ -577,6 +608,7 @@ lbm_status lbm_destroy(lbm_ctx* c) {
   cudaFree(c->d_scalar);
   cudaFree(c->d_tmp);
   cudaFree(c->d_pop);
+  if (c->packed) cudaEventDestroy(c->packed);
   if (c->h_status) cudaFreeHost(c->h_status);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -786,6 +818,39 @@ lbm_status lbm_band_halo_unpack(lbm_ctx* c, const void* d_below, const void* d_a
   st = halo_copy(c, 0, const_cast<void*>(d_below), false);
   if (st != LBM_OK) return st;
   return halo_copy(c, c->row0 + c->p.ny, const_cast<void*>(d_above), false);
+}
+
+lbm_status lbm_band_step_overlap(lbm_ctx* c, int scheme, double tau, double sigma, void* d_lo,
+                                 void* d_hi, void* comm_stream) {
+  lbm_status st = halo_check(c, d_lo, d_hi);
+  if (st != LBM_OK) return st;
+  if (scheme < 0 || scheme > LBM_SCHEME_MRT) return fail(c, LBM_E_INVAL, "unknown scheme");
+  if (!(tau > 0.5) || !std::isfinite(tau)) return fail(c, LBM_E_INVAL, "tau must be > 1/2");
+  if (!std::isfinite(sigma)) return fail(c, LBM_E_INVAL, "sigma must be finite");
+  DeviceGuard guard(c->p.device);
+  if (!c->packed)
+    LBM_CUDA(c, cudaEventCreateWithFlags(&c->packed, cudaEventDisableTiming));
+  const StripLaunch L = step_launch(c, tau, sigma);
+  const int s = c->cur, d = 1 - c->cur;
+  const int r0 = c->row0, n = c->p.ny, g = kGhostRows;
+  // the rows the neighbours need first: the two lowest and two highest
+  // owned rows (all of them when the band is too thin to have an interior)
+  const bool thin = n < 2 * g + 1;
+  st = launch_rows(c, scheme, L, r0, thin ? r0 + n : r0 + g, s, d);
+  if (st == LBM_OK && !thin) st = launch_rows(c, scheme, L, r0 + n - g, r0 + n, s, d);
+  if (st != LBM_OK) return st;
+  c->cur = d;  // the packs read the new state
+  st = halo_copy(c, r0, d_lo, true);
+  if (st == LBM_OK) st = halo_copy(c, r0 + n - g, d_hi, true);
+  if (st != LBM_OK) return st;
+  LBM_CUDA(c, cudaEventRecord(c->packed, c->stream));
+  if (comm_stream)
+    LBM_CUDA(c, cudaStreamWaitEvent(static_cast<cudaStream_t>(comm_stream), c->packed, 0));
+  // the interior rows, while the messages travel
+  if (!thin) st = launch_rows(c, scheme, L, r0 + g, r0 + n - g, s, d);
+  if (st != LBM_OK) return st;
+  c->last_scheme = scheme;
+  return LBM_OK;
 }
 
 unsigned long long lbm_kernel_launch_count(void) { return g_launches.load(); }

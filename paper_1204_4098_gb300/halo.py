@@ -15,8 +15,13 @@ the undecomposed lattice evaluates there, so the result is bit-identical.
 * ``exchange`` -- one halo exchange over ``torch.distributed`` (point to
   point; gloo for host tensors, NCCL for device tensors), or the periodic
   self-exchange of a single rank.
+* ``window_reduce`` -- the window diagnostics of the whole lattice (mass
+  and the row means of the density, hence the coexistence densities) from
+  the bands' owned rows, in one FP64 all-reduce.
 * ``BandLattice`` -- a band of the CUDA library (``lbm_create_band``) with
-  its halo buffers; ``step`` is step, pack, exchange, unpack.
+  its halo buffers; ``step`` computes the boundary rows, packs them, sends
+  them on a second stream while the interior rows are computed, and unpacks
+  (or, without overlap, step, pack, exchange, unpack).
 * ``LocalBands`` -- several bands of one lattice on one GPU in one process,
   exchanging by device copies (each band's kernels run to completion before
   the copies; nothing waits on another kernel).
@@ -60,18 +65,19 @@ def neighbours(rank, world):
     return (rank - 1) % world, (rank + 1) % world
 
 
-def exchange(lo, hi, rank, world, group=None):
+def exchange(lo, hi, rank, world, group=None, out=None):
     """One halo exchange: send `hi` (this band's two highest rows) to the
     band above and `lo` to the band below; return (from_below, from_above),
-    the band below's `hi` and the band above's `lo`.  Tensors of equal shape
-    and type on the device the process group serves.  A single rank is its
-    own neighbour: (hi, lo)."""
+    the band below's `hi` and the band above's `lo` (received into `out`
+    when given).  Tensors of equal shape and type on the device the process
+    group serves.  A single rank is its own neighbour: (hi, lo)."""
     if world == 1:
         return hi, lo
     import torch
     import torch.distributed as dist
     below, above = neighbours(rank, world)
-    from_below, from_above = torch.empty_like(hi), torch.empty_like(lo)
+    from_below, from_above = out if out is not None else (torch.empty_like(hi),
+                                                          torch.empty_like(lo))
     ops = [dist.P2POp(dist.isend, hi, above, group, TAG_UP),
            dist.P2POp(dist.irecv, from_below, below, group, TAG_UP),
            dist.P2POp(dist.isend, lo, below, group, TAG_DOWN),
@@ -79,6 +85,35 @@ def exchange(lo, hi, rank, world, group=None):
     for w in dist.batch_isend_irecv(ops):
         w.wait()
     return from_below, from_above
+
+
+def window_reduce(rho_own, y0, ny, world, group=None, device=None):
+    """(mass, row means [ny]) of the whole lattice from this rank's owned
+    density rows `rho_own` [rows][nx] starting at row y0: every rank fills
+    its rows of an FP64 vector [mass, row sums ...] and one all-reduce (sum)
+    completes it.  The coexistence densities of a slab follow from the row
+    means (gas: rows 0 and ny - 1, liquid: rows ny/2 - 1 and ny/2)."""
+    import torch
+    rho_own = np.asarray(rho_own, dtype=np.float64)
+    rows, nx = rho_own.shape
+    v = np.zeros(ny + 1)
+    sums = rho_own.sum(1)
+    v[0] = sums.sum()
+    v[1 + y0:1 + y0 + rows] = sums
+    t = torch.from_numpy(v).to(device if device is not None else "cpu")
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    v = t.cpu().numpy()
+    return float(v[0]), v[1:] / nx
+
+
+def coexistence(row_means):
+    """(rho_g, rho_l) of a slab whose liquid fills the middle rows."""
+    ny = len(row_means)
+    lo = ny // 2 - 1 if ny >= 2 else 0
+    return (0.5 * (row_means[0] + row_means[-1]),
+            0.5 * (row_means[lo] + row_means[ny // 2]))
 
 
 class BandLattice:
@@ -91,6 +126,7 @@ class BandLattice:
         import torch
         self.torch = torch
         self.rank, self.world, self.group = rank, world, group
+        self.ny, self.device = ny, device
         self.y0, self.rows = band_partition(ny, world)[rank]
         self.stream = torch.cuda.Stream(device=device)
         self.lat = lbm.Lattice(nx, self.rows, T_over_Tc, precision=precision, device=device,
@@ -104,27 +140,59 @@ class BandLattice:
         dev = torch.device("cuda", device)
         self.lo = torch.empty(n, dtype=torch.uint8, device=dev)
         self.hi = torch.empty(n, dtype=torch.uint8, device=dev)
+        self.recv = (torch.empty(n, dtype=torch.uint8, device=dev),
+                     torch.empty(n, dtype=torch.uint8, device=dev))
+        self.comm = torch.cuda.Stream(device=device)
         self.exchange()  # ghost rows from the neighbours' exact boundary rows
 
     def exchange(self):
         """Pack, exchange and unpack the halo rows (on the band's stream)."""
         with self.torch.cuda.stream(self.stream):
             self.lat.halo_pack(self.lo.data_ptr(), self.hi.data_ptr())
-            below, above = exchange(self.lo, self.hi, self.rank, self.world, self.group)
+            below, above = exchange(self.lo, self.hi, self.rank, self.world, self.group,
+                                    self.recv)
             self.lat.halo_unpack(below.data_ptr(), above.data_ptr())
 
-    def step(self, n, scheme, tau, sigma=0.0):
+    def step(self, n, scheme, tau, sigma=0.0, overlap=None):
         """n steps, each followed by a halo exchange; returns the status of
-        the last step (lbm_sync_status)."""
-        with self.torch.cuda.stream(self.stream):
-            for _ in range(n):
-                self.lat.step_async(1, scheme, tau, sigma)
+        the last step (lbm_sync_status).  With `overlap` the boundary rows
+        are computed and packed first, and the exchange runs on a second
+        stream while the interior rows are computed (lbm_band_step_overlap);
+        the next step waits for the unpack.  By default overlap is on when
+        there is a transfer to hide (world > 1): a single band's
+        self-exchange copies nothing, and the split costs two small launches."""
+        torch = self.torch
+        if overlap is None:
+            overlap = self.world > 1
+        for _ in range(n):
+            if not overlap:
+                with torch.cuda.stream(self.stream):
+                    self.lat.step_async(1, scheme, tau, sigma)
                 self.exchange()
+                continue
+            with torch.cuda.stream(self.stream):
+                self.lat.step_overlap(scheme, tau, sigma, self.lo.data_ptr(), self.hi.data_ptr(),
+                                      self.comm.cuda_stream)
+            with torch.cuda.stream(self.comm):
+                below, above = exchange(self.lo, self.hi, self.rank, self.world, self.group,
+                                        self.recv)
+            self.stream.wait_stream(self.comm)
+            with torch.cuda.stream(self.stream):
+                self.lat.halo_unpack(below.data_ptr(), above.data_ptr())
         return self.lat.sync()
 
     def observe(self):
         """(rho, vx, vy) of the owned rows."""
         return self.lat.observe()
+
+    def window(self):
+        """(mass, rho_g, rho_l) of the whole lattice: one FP64 all-reduce over
+        the ranks (window_reduce), on the device the process group serves."""
+        self.lat.sync()
+        dev = self.torch.device("cuda", self.device) if self.world > 1 else None
+        mass, means = window_reduce(self.observe()[0], self.y0, self.ny, self.world,
+                                    self.group, dev)
+        return (mass, *coexistence(means))
 
     def close(self):
         self.lat.close()
@@ -171,10 +239,18 @@ class LocalBands:
             below, above = (b - 1) % self.k, (b + 1) % self.k
             lat.halo_unpack(self.hi[below].data_ptr(), self.lo[above].data_ptr())
 
-    def step(self, n, scheme, tau, sigma=0.0):
+    def step(self, n, scheme, tau, sigma=0.0, overlap=False):
         """n steps of every band with an exchange after each; returns the
-        worst band status."""
+        worst band status.  `overlap` takes the boundary-rows-first path
+        (lbm_band_step_overlap; on one stream the order only changes)."""
         for _ in range(n):
+            if overlap:
+                for lat, lo, hi in zip(self.lats, self.lo, self.hi):
+                    lat.step_overlap(scheme, tau, sigma, lo.data_ptr(), hi.data_ptr())
+                for b, lat in enumerate(self.lats):
+                    below, above = (b - 1) % self.k, (b + 1) % self.k
+                    lat.halo_unpack(self.hi[below].data_ptr(), self.lo[above].data_ptr())
+                continue
             for lat in self.lats:
                 lat.step_async(1, scheme, tau, sigma)
             self.exchange()

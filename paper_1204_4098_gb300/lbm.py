@@ -89,6 +89,7 @@ SIGNATURES = {
     "lbm_band_halo_bytes": (_I, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     "lbm_band_halo_pack": (_I, [_P, _P, _P]),
     "lbm_band_halo_unpack": (_I, [_P, _P, _P]),
+    "lbm_band_step_overlap": (_I, [_P, _I, _D, _D, _P, _P, _P]),
     "lbm_step": (_I, [_P, _I, _I, _D, _D]),
     "lbm_step_async": (_I, [_P, _I, _I, _D, _D]),
     "lbm_sync_status": (_I, [_P]),
@@ -253,6 +254,13 @@ class Lattice:
         device buffers at addresses d_lo, d_hi."""
         self._check(lib().lbm_band_halo_pack(self.ctx, _P(int(d_lo)), _P(int(d_hi))),
                     "lbm_band_halo_pack")
+
+    def step_overlap(self, scheme, tau, sigma, d_lo, d_hi, comm_stream=None):
+        """One band step with the boundary rows first, packed into d_lo /
+        d_hi, and comm_stream made to wait for the pack (lbm_band_step_overlap)."""
+        self._check(lib().lbm_band_step_overlap(
+            self.ctx, int(scheme), float(tau), float(sigma), _P(int(d_lo)), _P(int(d_hi)),
+            None if comm_stream is None else _P(int(comm_stream))), "lbm_band_step_overlap")
 
     def halo_unpack(self, d_below, d_above):
         self._check(lib().lbm_band_halo_unpack(self.ctx, _P(int(d_below)), _P(int(d_above))),

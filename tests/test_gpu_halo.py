@@ -22,13 +22,14 @@ def field(ny, seed=4):
     return rho
 
 
+@pytest.mark.parametrize("overlap", [False, True])
 @pytest.mark.parametrize("k", [1, 3, 4])
 @pytest.mark.parametrize("precision,variant", [(lbm.FP32, lbm.VARIANT_PAIR),
                                                (lbm.FP32, lbm.VARIANT_REGISTER),
                                                (lbm.FP64, lbm.VARIANT_REGISTER),
                                                (lbm.BF16DEV, lbm.VARIANT_PAIR)])
-def test_bands_match_whole_lattice_bitwise(k, precision, variant):
-    ny, steps = 45, 40
+def test_bands_match_whole_lattice_bitwise(k, precision, variant, overlap):
+    ny, steps = 45, 40  # bands of 45, 15 and 11-12 rows
     rho = field(ny)
     whole = lbm.Lattice(NX, ny, T, precision=precision)
     whole.set_variant(variant)
@@ -36,7 +37,7 @@ def test_bands_match_whole_lattice_bitwise(k, precision, variant):
     whole.step(steps, lbm.IMPROVED, 0.8, 0.1)
     bands = halo.LocalBands(NX, ny, T, rho, k, precision=precision, at_rest=True)
     bands.set_variant(variant)
-    assert bands.step(steps, lbm.IMPROVED, 0.8, 0.1) == lbm.LBM_OK
+    assert bands.step(steps, lbm.IMPROVED, 0.8, 0.1, overlap=overlap) == lbm.LBM_OK
     assert np.array_equal(bands.populations(), whole.populations())
     for a, b in zip(bands.observe(), whole.observe()):
         assert np.array_equal(a, b)
@@ -66,3 +67,23 @@ def test_band_contract():
     assert e.value.status == lbm.LBM_E_STATE
     with pytest.raises(lbm.LbmError):
         lbm.Lattice(NX, 1, T, band=True)  # a band owns at least two rows
+
+
+def test_band_runner_with_overlap_matches_whole_lattice():
+    """halo.BandLattice (the multi-rank runner) on one rank: the boundary
+    rows first, the exchange on its own stream (here the periodic
+    self-exchange) while the interior rows run, the unpack before the next
+    step -- bit-identical to the whole lattice, for a band thin enough to
+    have no interior as well."""
+    for ny in (45, 4):
+        rho = field(ny)
+        whole = lbm.Lattice(NX, ny, T, precision=lbm.FP32)
+        whole.set_variant(lbm.VARIANT_PAIR)
+        whole.init_density(rho)
+        whole.step(30, lbm.EDM, 0.7)
+        band = halo.BandLattice(NX, ny, T, rho)
+        band.lat.set_variant(lbm.VARIANT_PAIR)
+        assert band.step(30, lbm.EDM, 0.7, overlap=True) == lbm.LBM_OK
+        for a, b in zip(band.observe(), whole.observe()):
+            assert np.array_equal(a, b), ny
+        band.close()

@@ -39,7 +39,7 @@ def whole_run(ny, scheme, tau, sigma):
     return lat.f
 
 
-def band_run(rank, world, ny, scheme, tau, sigma):
+def band_run(rank, world, ny, scheme, tau, sigma, window=False):
     """This rank's band stepped by the oracle with halo exchanges; returns
     its owned rows [9][rows][nx]."""
     y0, rows = halo.band_partition(ny, world)[rank]
@@ -55,7 +55,10 @@ def band_run(rank, world, ny, scheme, tau, sigma):
         below, above = halo.exchange(lo, hi, rank, world)
         lat.f[:, 0:g] = below.numpy()
         lat.f[:, rows + g:rows + 2 * g] = above.numpy()
-    return lat.f[:, g:g + rows].copy()
+    own = lat.f[:, g:g + rows].copy()
+    if window:  # the window diagnostics in one FP64 all-reduce
+        return halo.window_reduce(own.sum(0), y0, ny, world)
+    return own
 
 
 def _free_port():
@@ -66,13 +69,16 @@ def _free_port():
     return port
 
 
-def _worker(rank, world, port, ny, case, q):
+def _worker(rank, world, port, ny, case, q, window=False):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        own = band_run(rank, world, ny, *case)
+        own = band_run(rank, world, ny, *case, window=window)
+        if window:
+            q.put((rank, own))
+            return
         parts = [None] * world
         dist.all_gather_object(parts, own)
         if rank == 0:
@@ -81,15 +87,15 @@ def _worker(rank, world, port, ny, case, q):
         dist.destroy_process_group()
 
 
-def _spawn(world, ny, case):
+def _spawn(world, ny, case, window=False):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, world, port, ny, case, q))
+    procs = [ctx.Process(target=_worker, args=(r, world, port, ny, case, q, window))
              for r in range(world)]
     for p in procs:
         p.start()
-    out = q.get(timeout=300)
+    out = [q.get(timeout=300) for _ in range(world)] if window else q.get(timeout=300)
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
@@ -123,3 +129,20 @@ def test_band_partition_and_halo_rows():
     h = halo.with_halo(field, 0, 2)  # rows 4, 5 | 0, 1 | 2, 3
     assert np.array_equal(h[:, 0], [12.0, 15.0, 0.0, 3.0, 6.0, 9.0])
     assert halo.neighbours(0, 4) == (3, 1) and halo.neighbours(3, 4) == (2, 0)
+
+
+def test_window_reduce_gives_every_rank_the_whole_lattice_diagnostics():
+    """One FP64 all-reduce per window: every rank gets the whole lattice's
+    mass and row means, equal to those of the undecomposed run (the mass to
+    rounding, the row means exactly: each row is summed by one rank)."""
+    ny, case = 31, (oracle.IMPROVED, 0.8, 0.1)
+    got = _spawn(4, ny, case, window=True)
+    rho = whole_run(ny, *case).sum(0)
+    for rank, (mass, means) in got:
+        assert mass == pytest.approx(rho.sum(), rel=1e-13)
+        assert np.array_equal(means, rho.sum(1) / NX)
+    g, l = halo.coexistence(rho.mean(1))
+    assert halo.coexistence(got[0][1][1]) == (g, l)
+    mass, means = halo.window_reduce(rho[3:9], 3, ny, 1)  # one rank: its rows only
+    assert mass == pytest.approx(rho[3:9].sum(), rel=1e-14)
+    assert np.array_equal(means[3:9], rho[3:9].sum(1) / NX) and not means[:3].any()
