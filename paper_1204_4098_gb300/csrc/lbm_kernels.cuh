@@ -225,14 +225,15 @@ __device__ __forceinline__ void strip_run(const StripArgs<S>& A, int strip, int 
 
   C PA[kQ], PB[kQ], PC[kQ];
   C hA = C(0), hB = C(0), hC = C(0);
-  // prologue: psi of rows y0 - 1 and y0, populations of y0 (PA) and y0 + 1 (PB)
+  // prologue: psi of rows y0 - 1 and y0, populations of y0 (PA) and y0 + 1
+  // (PB); the three rows are loaded together (one memory round trip)
   {
     C rdummy;
-    load_row(y0 == 0 ? ny - 1 : y0 - 1, PA, hA);
-    psi_row(PA, hA, Wm, Cm, Em, rdummy);
+    load_row(y0 == 0 ? ny - 1 : y0 - 1, PC, hC);
     load_row(y0, PA, hA);
-    psi_row(PA, hA, Wz, Cz, Ez, rho0);
     load_row(y0 + 1 == ny ? 0 : y0 + 1, PB, hB);
+    psi_row(PC, hC, Wm, Cm, Em, rdummy);
+    psi_row(PA, hA, Wz, Cz, Ez, rho0);
   }
 #if LBM_STRIP_UNROLL3
   int y = y0;
@@ -465,15 +466,21 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
   // psi ring: rows y-1 (m), y (z)
   P2 Wm = P2(C(0)), Cm = P2(C(0)), Em = P2(C(0)), Wz = P2(C(0)), Cz = P2(C(0)), Ez = P2(C(0));
   P2 r0;
-  {
-    P2 rd;
-    load_row(y0 == 0 ? ny - 1 : y0 - 1, P0, h1);
-    psi_row(P0, h1, Wm, Cm, Em, rd);
-    load_row(y0, P0, h1);
-    psi_row(P0, h1, Wz, Cz, Ez, r0);
-    load_row(y0 + 1 == ny ? 0 : y0 + 1, P1, h1);
-  }
   Raw next;
+  {
+    // the three rows before the first are fetched together: one memory
+    // round trip at the start of a band instead of three in sequence
+    Raw Rm, Rz;
+    P2 rd;
+    fetch_row(y0 == 0 ? ny - 1 : y0 - 1, Rm);
+    fetch_row(y0, Rz);
+    fetch_row(y0 + 1 == ny ? 0 : y0 + 1, next);
+    assemble(Rm, P0, h1);
+    psi_row(P0, h1, Wm, Cm, Em, rd);
+    assemble(Rz, P0, h1);
+    psi_row(P0, h1, Wz, Cz, Ez, r0);
+    assemble(next, P1, h1);
+  }
   for (int y = y0; y < y1; ++y) {
     const bool more = y + 2 <= y1;
     if (more) fetch_row(y + 2 >= ny ? y + 2 - ny : y + 2, next);
