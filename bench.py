@@ -69,6 +69,9 @@ MEASURED_TRAFFIC = {
     # batch body (single lattices unpadded): 4096^2 capture 615.3 MB read +
     # 555.6 MB written per launch, x4 cells
     ("8f05beea9b05b658", "fp32", 8192, "pair"): 4.6838e9,
+    # after the band prologue fetched its three rows together: 4096^2 capture
+    # 615.3 MB read + 555.6 MB written per launch, x4 cells
+    ("300215b053bb1d0a", "fp32", 8192, "pair"): 4.6836e9,
 }
 
 

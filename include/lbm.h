@@ -303,11 +303,14 @@ typedef struct {
  * WORKLIST_DYNAMIC: the same items handed out one at a time from a per-step
  * counter (a warp that finishes early takes more); PERSISTENT: one launch per
  * window and class, each CTA owning whole instances; COOPERATIVE: one
- * cooperative launch per window with a bounded grid barrier between steps.
- * AUTO times the candidates on live windows and keeps the fastest.  Every
- * mode gives the same results bit for bit. */
+ * cooperative launch per window with a bounded grid barrier between steps;
+ * BALANCED: per step and class, one wave of resident warps, each taking an
+ * equal share of all the class's rows (the rows of every strip laid end to
+ * end and cut into equal pieces, at least 8 rows each; rows_per_item does
+ * not apply).  AUTO times the candidates on live windows and keeps the
+ * fastest.  Every mode gives the same results bit for bit. */
 enum { LBM_BATCH_AUTO = 0, LBM_BATCH_WORKLIST = 1, LBM_BATCH_PERSISTENT = 2,
-       LBM_BATCH_COOPERATIVE = 3, LBM_BATCH_WORKLIST_DYNAMIC = 4 };
+       LBM_BATCH_COOPERATIVE = 3, LBM_BATCH_WORKLIST_DYNAMIC = 4, LBM_BATCH_BALANCED = 5 };
 /* Convergence rules.  CELL: every cell changed by less than
  * max(tol, 8 * 2^-23 * rho) over a window.  COEX: the coexistence densities
  * rho_g and rho_l (FP64 row means) each changed by less than
@@ -341,7 +344,8 @@ typedef struct {
   double tol;           /* density-change tolerance per window (1e-9)          */
   int max_steps;        /* step cap per instance (200000)                      */
   int mode;             /* LBM_BATCH_AUTO (window-level autotuning), _WORKLIST,
-                           _WORKLIST_DYNAMIC, _PERSISTENT, _COOPERATIVE        */
+                           _WORKLIST_DYNAMIC, _PERSISTENT, _COOPERATIVE,
+                           _BALANCED                                           */
   int rows_per_item;    /* band height of a work-list item; 0 = autotuned      */
   int conv;             /* LBM_CONV_COEX (default), _CELL, _NONE or _TREND      */
   int variant;          /* LBM_VARIANT_AUTO (default) or _PAIR: two columns per

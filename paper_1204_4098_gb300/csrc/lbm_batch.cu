@@ -200,6 +200,36 @@ batch_worklist_dyn_kernel(const BatchInst* __restrict__ inst, const int* __restr
   }
 }
 
+// One step of every active instance of one class on the balanced one-wave
+// schedule (balanced_schedule): warp w runs items[begin[w] .. begin[w + 1]),
+// each a row range of one strip, together an equal share of the class's rows.
+template <bool kPair>
+__global__ void __launch_bounds__(kWorklistThreads,
+                                  kPair ? LBM_BATCH_PAIR_MIN_BLOCKS : LBM_BATCH_ODD_MIN_BLOCKS)
+batch_balanced_kernel(const BatchInst* __restrict__ inst, const int4* __restrict__ items,
+                      const int* __restrict__ begin, const float* src, float* dst,
+                      unsigned* inst_status) {
+  __shared__ StripArgs<StoreF32> args[kWorklistThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int w = (blockIdx.x * kWorklistThreads + threadIdx.x) >> 5;
+  const int k1 = begin[w + 1];
+  for (int k = begin[w]; k < k1; ++k) {
+    const int4 it = items[k];  // instance, strip, first row, end row
+    const BatchInst I = inst[it.x];
+    __syncwarp();
+    if (lane == 0) {
+      StripArgs<StoreF32> A = inst_args(I, src, dst, inst_status + it.x, false);
+      A.y_begin = it.z;
+      A.y_end = it.w;
+      A.band_rows = it.w - it.z;
+      A.n_bands = 1;
+      args[warp] = A;
+    }
+    __syncwarp();
+    run_item<kPair, false>(args[warp], I.scheme, it.y, 0, lane);
+  }
+}
+
 // Grid barrier of the cooperative window: sync[0] counts arrivals, sync[1] is
 // the generation, sync[2] the error word.  Every CTA is resident (cooperative
 // launch), so the barrier completes; the wait is still bounded, and a CTA
@@ -514,6 +544,11 @@ struct lbm_batch {
   int* d_n_active = nullptr;     // {active two-column instances, all active}
   int* d_cta_begin = nullptr;
   int* d_cta_list = nullptr;
+  int4* d_bal_items = nullptr;   // balanced schedule: items of class 0, then class 1
+  int* d_bal_begin = nullptr;    // per class: wl_grid * 4 + 1 warp offsets
+  int4* h_bal_items = nullptr;
+  int* h_bal_begin = nullptr;
+  int bal_cap = 0;               // items per class table
   int* h_active = nullptr;
   int* h_prefix = nullptr;
   int* h_cta_begin = nullptr;
@@ -567,6 +602,11 @@ struct BDeviceGuard {
   }
 };
 
+// Warps of the larger class's resident work-list wave (balanced tables).
+int warps_max(const lbm_batch* b) {
+  return std::max(b->wl_grid[0], b->wl_grid[1]) * (kWorklistThreads / 32);
+}
+
 void set_geometry(BatchInst& d, int rows) {
   d.band_rows = std::max(1, std::min(rows, d.ny));
   d.n_bands = (d.ny + d.band_rows - 1) / d.band_rows;
@@ -576,9 +616,12 @@ void set_geometry(BatchInst& d, int rows) {
   d.pn_bands = (d.ny + d.pband_rows - 1) / d.pband_rows;
 }
 
+constexpr int kBalancedMinRows = 8;
+
 // Rebuild the active list (two-column instances first), the work-list prefix
-// and the persistent assignment of each class.
-lbm_status upload_tables(lbm_batch* b) {
+// and the persistent assignment of each class; for a balanced window also
+// each class's one-wave schedule.
+lbm_status upload_tables(lbm_batch* b, int mode) {
   const int na = int(b->active.size());
   std::vector<int> cls[2];  // [0] two columns per lane, [1] one
   for (int i : b->active) cls[b->desc[i].pair ? 0 : 1].push_back(i);
@@ -615,6 +658,22 @@ lbm_status upload_tables(lbm_batch* b) {
                                b->stream));
   LBM_BCUDA(b, cudaMemcpyAsync(b->d_cta_list, b->h_cta_list, std::max(pos, 1) * sizeof(int),
                                cudaMemcpyHostToDevice, b->stream));
+  if (mode == LBM_BATCH_BALANCED)
+    for (int c = 0; c < 2; ++c) {
+      std::vector<BalColumn> cols;
+      for (int i : cls[c]) cols.push_back(BalColumn{i, b->desc[i].n_strips, b->desc[i].ny});
+      const int warps = b->wl_grid[c] * (kWorklistThreads / 32);
+      int4* items = b->h_bal_items + size_t(c) * b->bal_cap;
+      int* begin = b->h_bal_begin + size_t(c) * (warps_max(b) + 1);
+      const int n = balanced_schedule(cols, warps, kBalancedMinRows,
+                                      reinterpret_cast<BalItem*>(items), begin);
+      LBM_BCUDA(b, cudaMemcpyAsync(b->d_bal_items + size_t(c) * b->bal_cap, items,
+                                   std::max(n, 1) * sizeof(int4), cudaMemcpyHostToDevice,
+                                   b->stream));
+      LBM_BCUDA(b, cudaMemcpyAsync(b->d_bal_begin + size_t(c) * (warps_max(b) + 1), begin,
+                                   (warps + 1) * sizeof(int), cudaMemcpyHostToDevice,
+                                   b->stream));
+    }
   return LBM_OK;
 }
 
@@ -623,6 +682,7 @@ lbm_status upload_tables(lbm_batch* b) {
 int class_grid(const lbm_batch* b, int mode, int cls) {
   if (b->class_items[cls] == 0) return 0;
   if (mode == LBM_BATCH_PERSISTENT) return b->pers_grid_max;
+  if (mode == LBM_BATCH_BALANCED) return b->wl_grid[cls];
   return worklist_grid(b->class_items[cls], kWorklistThreads / 32, b->wl_grid[cls]);
 }
 
@@ -712,6 +772,20 @@ lbm_status window_graph(lbm_batch* b, int mode, cudaGraphExec_t* out) {
             b->buf[(s + 1) & 1], b->d_status, b->d_counters + W + s);
       join();
     }
+  } else if (mode == LBM_BATCH_BALANCED) {
+    const int bspan = warps_max(b) + 1;
+    for (int s = 0; s < W; ++s) {
+      fork();
+      if (g0 > 0)
+        batch_balanced_kernel<true><<<g0, kWorklistThreads, 0, b->stream>>>(
+            b->d_inst, b->d_bal_items, b->d_bal_begin, b->buf[s & 1], b->buf[(s + 1) & 1],
+            b->d_status);
+      if (g1 > 0)
+        batch_balanced_kernel<false><<<g1, kWorklistThreads, 0, s1>>>(
+            b->d_inst, b->d_bal_items + b->bal_cap, b->d_bal_begin + bspan, b->buf[s & 1],
+            b->buf[(s + 1) & 1], b->d_status);
+      join();
+    }
   } else {
     fork();
     if (g0 > 0)
@@ -767,8 +841,9 @@ void choose_config(lbm_batch* b, int& mode, int& rows) {
   const auto eligible = [&](size_t k) {
     const auto& c = b->tuner.candidates[k];
     if (b->p.rows_per_item > 0 &&
-        (c.first == LBM_BATCH_WORKLIST || c.first == LBM_BATCH_WORKLIST_DYNAMIC) &&
-        c.second != b->p.rows_per_item)
+        (((c.first == LBM_BATCH_WORKLIST || c.first == LBM_BATCH_WORKLIST_DYNAMIC) &&
+          c.second != b->p.rows_per_item) ||
+         c.first == LBM_BATCH_BALANCED))
       return false;
     // a persistent window puts each instance on one SM: only worth trying
     // when the active populations are within a few times the L2 size and no
@@ -807,7 +882,7 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
   if (!p || !in || !out || count < 1) return LBM_E_INVAL;
   *out = nullptr;
   if (p->window < 2 || p->window % 2 || p->max_steps < 1 || !(p->tol >= 0) ||
-      p->mode < LBM_BATCH_AUTO || p->mode > LBM_BATCH_WORKLIST_DYNAMIC || p->rows_per_item < 0 ||
+      p->mode < LBM_BATCH_AUTO || p->mode > LBM_BATCH_BALANCED || p->rows_per_item < 0 ||
       p->conv < LBM_CONV_COEX || p->conv > LBM_CONV_TREND || !(p->conv_rel >= 0.0) ||
       !(p->trend_tol >= 0.0) ||
       !(p->variant == LBM_VARIANT_AUTO || p->variant == LBM_VARIANT_PAIR ||
@@ -918,6 +993,15 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
   ok &= cudaMalloc(&b->d_cta_begin, 2 * (b->pers_grid_max + 1) * sizeof(int)) == cudaSuccess;
   ok &= cudaMalloc(&b->d_cta_list, count * sizeof(int)) == cudaSuccess;
   ok &= cudaMalloc(&b->d_sync, 3 * sizeof(unsigned)) == cudaSuccess;
+  {
+    // balanced schedule: at most one item per warp plus one per strip boundary
+    long long strips = 0;
+    for (const BatchInst& d : b->desc) strips += d.n_strips;
+    b->bal_cap = int(warps_max(b) + strips + 1);
+    ok &= cudaMalloc(&b->d_bal_items, 2 * size_t(b->bal_cap) * sizeof(int4)) == cudaSuccess;
+    ok &= cudaMalloc(&b->d_bal_begin, 2 * size_t(warps_max(b) + 1) * sizeof(int)) ==
+          cudaSuccess;
+  }
   if (!ok) return bail(LBM_E_NOMEM, "cudaMalloc");
   ok &= cudaMallocHost(&b->h_active, count * sizeof(int)) == cudaSuccess;
   ok &= cudaMallocHost(&b->h_prefix, (count + 3) * sizeof(int)) == cudaSuccess;
@@ -926,6 +1010,9 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
   ok &= cudaMallocHost(&b->h_cta_list, count * sizeof(int)) == cudaSuccess;
   ok &= cudaMallocHost(&b->h_out, count * sizeof(BatchOut)) == cudaSuccess;
   ok &= cudaMallocHost(&b->h_status, count * sizeof(unsigned)) == cudaSuccess;
+  ok &= cudaMallocHost(&b->h_bal_items, 2 * size_t(b->bal_cap) * sizeof(int4)) == cudaSuccess;
+  ok &= cudaMallocHost(&b->h_bal_begin, 2 * size_t(warps_max(b) + 1) * sizeof(int)) ==
+        cudaSuccess;
   if (!ok) return bail(LBM_E_NOMEM, "cudaMallocHost");
   if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess)
@@ -939,6 +1026,7 @@ lbm_status lbm_batch_create(const lbm_batch_params* p, const lbm_instance* in, i
     return bail(LBM_E_CUDA, "memset");
   for (int rows : {8, 16, 32, 64, 128}) b->tuner.add(LBM_BATCH_WORKLIST, rows);
   for (int rows : {8, 16, 32, 64}) b->tuner.add(LBM_BATCH_WORKLIST_DYNAMIC, rows);
+  b->tuner.add(LBM_BATCH_BALANCED, 0);
   b->tuner.add(LBM_BATCH_PERSISTENT, 0);
   {
     // cooperative windows: every CTA resident, one launch per window
@@ -981,6 +1069,10 @@ lbm_status lbm_batch_destroy(lbm_batch* b) {
   cudaFree(b->d_cta_begin);
   cudaFree(b->d_cta_list);
   cudaFree(b->d_sync);
+  cudaFree(b->d_bal_items);
+  cudaFree(b->d_bal_begin);
+  if (b->h_bal_items) cudaFreeHost(b->h_bal_items);
+  if (b->h_bal_begin) cudaFreeHost(b->h_bal_begin);
   if (b->h_active) cudaFreeHost(b->h_active);
   if (b->h_prefix) cudaFreeHost(b->h_prefix);
   if (b->h_cta_begin) cudaFreeHost(b->h_cta_begin);
@@ -1120,8 +1212,8 @@ lbm_status lbm_batch_run(lbm_batch* b, int max_windows, int* n_active) {
   for (int w = 0; w < max_windows && !b->active.empty(); ++w) {
     int mode = LBM_BATCH_WORKLIST, rows = 32;
     choose_config(b, mode, rows);
-    for (auto& d : b->desc) set_geometry(d, rows);
-    lbm_status st = upload_tables(b);
+    for (auto& d : b->desc) set_geometry(d, rows > 0 ? rows : 32);
+    lbm_status st = upload_tables(b, mode);
     if (st != LBM_OK) return st;
     cudaGraphExec_t g = nullptr;
     st = window_graph(b, mode, &g);
@@ -1144,7 +1236,8 @@ lbm_status lbm_batch_run(lbm_batch* b, int max_windows, int* n_active) {
         mode == LBM_BATCH_COOPERATIVE
             ? 1
             : (class_grid(b, mode, 0) > 0 ? 1 : 0) + (class_grid(b, mode, 1) > 0 ? 1 : 0);
-    const bool per_step = mode == LBM_BATCH_WORKLIST || mode == LBM_BATCH_WORKLIST_DYNAMIC;
+    const bool per_step = mode == LBM_BATCH_WORKLIST || mode == LBM_BATCH_WORKLIST_DYNAMIC ||
+                          mode == LBM_BATCH_BALANCED;
     const unsigned long long nl = (per_step ? kernels * b->p.window : kernels) + 1;
     count_launches(nl);
     b->stats.launches += nl;

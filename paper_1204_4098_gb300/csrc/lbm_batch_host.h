@@ -60,6 +60,56 @@ void lpt_assign(std::vector<int> ids, const Cost& cost, int grid, int* begin, in
   }
 }
 
+// Balanced one-wave schedule of a work-list class.  The rows of every strip
+// of the class's instances, laid end to end (instance by instance, strip by
+// strip), are cut into `used` pieces of equal row count (to one row), one per
+// warp of a resident wave; a piece that crosses from one strip into the next
+// becomes one item per strip.  used = min(warps, max(1, total rows /
+// min_rows)): pieces stay at least min_rows long, since every item starts
+// by fetching the rows on either side of its first one.  Like the
+// single-lattice kernel's bands, every warp then does the same work and
+// the step ends with all of them, instead of with the last of many small
+// items.  Items go to items[] (instance, strip, first row, end row), warp
+// w's are items[begin[w] .. begin[w + 1]); begin gets warps + 1 entries.
+struct BalItem {
+  int inst, strip, y0, y1;
+};
+struct BalColumn {
+  int inst, n_strips, ny;
+};
+inline int balanced_schedule(const std::vector<BalColumn>& cols, int warps, int min_rows,
+                             BalItem* items, int* begin) {
+  long long total = 0;
+  for (const BalColumn& c : cols) total += (long long)c.n_strips * c.ny;
+  const long long used =
+      std::max(1LL, std::min<long long>(warps, total / std::max(1, min_rows)));
+  int n = 0;
+  size_t ci = 0;
+  int strip = 0, row = 0;  // the next row not yet assigned
+  for (int w = 0; w < warps; ++w) {
+    begin[w] = n;
+    if (w >= used || ci >= cols.size()) continue;
+    // rows [total w / used, total (w + 1) / used) of the concatenation
+    long long left = total * (w + 1) / used - total * w / used;
+    while (left > 0 && ci < cols.size()) {
+      const BalColumn& c = cols[ci];
+      const int take = int(std::min<long long>(left, c.ny - row));
+      items[n++] = BalItem{c.inst, strip, row, row + take};
+      left -= take;
+      row += take;
+      if (row == c.ny) {
+        row = 0;
+        if (++strip == c.n_strips) {
+          strip = 0;
+          ++ci;
+        }
+      }
+    }
+  }
+  begin[warps] = n;
+  return n;
+}
+
 // Window-level autotuner.  Each candidate (mode, rows) is timed on one live
 // window, the cheapest per cell update is kept, and tuning starts again once
 // the active work has halved or the chosen candidate has become 30 % dearer

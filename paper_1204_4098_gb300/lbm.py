@@ -62,7 +62,8 @@ class lbm_batch_stats(ctypes.Structure):
                 ("rows_per_item", ctypes.c_int), ("n_active", ctypes.c_int)]
 
 
-BATCH_AUTO, BATCH_WORKLIST, BATCH_PERSISTENT, BATCH_COOPERATIVE, BATCH_WORKLIST_DYNAMIC = range(5)
+(BATCH_AUTO, BATCH_WORKLIST, BATCH_PERSISTENT, BATCH_COOPERATIVE, BATCH_WORKLIST_DYNAMIC,
+ BATCH_BALANCED) = range(6)
 CONV_COEX, CONV_CELL, CONV_NONE, CONV_TREND = range(4)
 RUN_ACTIVE, RUN_CONVERGED, RUN_DIVERGED, RUN_CAPPED = range(4)
 

@@ -20,6 +20,13 @@ int shim_lpt(int n, const long long* cells, int grid, int* begin, int* list) {
   return pos;
 }
 
+// columns: 3 ints each (instance, strips, rows); items: 4 ints each.
+int shim_balanced(int ncols, const int* cols, int warps, int min_rows, int* items, int* begin) {
+  std::vector<lbm::BalColumn> c(ncols);
+  for (int k = 0; k < ncols; ++k) c[k] = lbm::BalColumn{cols[3 * k], cols[3 * k + 1], cols[3 * k + 2]};
+  return lbm::balanced_schedule(c, warps, min_rows, reinterpret_cast<lbm::BalItem*>(items), begin);
+}
+
 void* shim_tuner_new() { return new lbm::WindowTuner(); }
 void shim_tuner_free(void* t) { delete static_cast<lbm::WindowTuner*>(t); }
 void shim_tuner_add(void* t, int mode, int rows) {

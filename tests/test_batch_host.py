@@ -74,6 +74,64 @@ def test_lpt_assignment(S, n, grid, seed):
         assert max(loads) <= 4.0 / 3.0 * bound + 1e-9
 
 
+# --- balanced one-wave schedule ---------------------------------------------------
+
+def run_balanced(S, cols, warps, min_rows):
+    flat = [v for c in cols for v in c]
+    arr = (ctypes.c_int * max(len(flat), 1))(*flat)
+    cap = warps + sum(c[1] for c in cols) + 1
+    items = (ctypes.c_int * (4 * cap))()
+    begin = (ctypes.c_int * (warps + 1))()
+    n = S.shim_balanced(len(cols), arr, warps, min_rows, items, begin)
+    it = [tuple(items[4 * k:4 * k + 4]) for k in range(n)]
+    return it, list(begin)
+
+
+@pytest.mark.parametrize("warps,min_rows,seed", [(2432, 8, 1), (2432, 8, 2), (64, 8, 3),
+                                                 (2432, 200, 4), (7, 1, 5)])
+def test_balanced_schedule_covers_every_row_once_in_equal_pieces(S, warps, min_rows, seed):
+    rng = np.random.default_rng(seed)
+    cols = [(int(i), int(rng.integers(1, 9)), int(rng.integers(1, 520)))
+            for i in rng.permutation(40)[:int(rng.integers(1, 40))]]
+    items, begin = run_balanced(S, cols, warps, min_rows)
+    total = sum(ns * ny for _, ns, ny in cols)
+    used = max(1, min(warps, total // min_rows))
+    assert begin[0] == 0 and begin[warps] == len(items)
+    assert all(begin[w] <= begin[w + 1] for w in range(warps))
+    # every (instance, strip, row) exactly once, in order of the concatenation
+    seen = []
+    for inst, strip, y0, y1 in items:
+        assert 0 <= y0 < y1
+        seen += [(inst, strip, y) for y in range(y0, y1)]
+    want = [(i, s, y) for i, ns, ny in cols for s in range(ns) for y in range(ny)]
+    assert seen == want
+    # pieces of equal length to one row; warps past `used` idle
+    rows = [sum(y1 - y0 for _, _, y0, y1 in items[begin[w]:begin[w + 1]]) for w in range(warps)]
+    assert all(r == 0 for r in rows[used:])
+    assert max(rows[:used]) - min(rows[:used]) <= 1
+    # a piece is cut into items only at strip ends: every item of a warp but
+    # its first starts at row 0, every one but its last ends at the strip's end
+    ny = {i: n for i, _, n in cols}
+    for w in range(used):
+        mine = items[begin[w]:begin[w + 1]]
+        assert mine
+        assert all(it[2] == 0 for it in mine[1:])
+        assert all(it[3] == ny[it[0]] for it in mine[:-1])
+
+
+def test_balanced_schedule_small_sets(S):
+    # 3 strips x 10 rows over 8 warps with >= 8 rows each: 3 pieces of 10
+    items, begin = run_balanced(S, [(5, 3, 10)], 8, 8)
+    assert items == [(5, 0, 0, 10), (5, 1, 0, 10), (5, 2, 0, 10)]
+    assert begin == [0, 1, 2, 3, 3, 3, 3, 3, 3]
+    # one piece spanning two instances
+    items, begin = run_balanced(S, [(0, 1, 3), (1, 1, 4)], 1, 1)
+    assert items == [(0, 0, 0, 3), (1, 0, 0, 4)] and begin == [0, 2]
+    # nothing to do
+    items, begin = run_balanced(S, [], 4, 8)
+    assert items == [] and begin == [0, 0, 0, 0, 0]
+
+
 # --- window-level autotuner --------------------------------------------------------
 
 CANDS = [(WL, 8), (WL, 16), (WL, 32), (WL, 64), (WL, 128), (PERS, 0),

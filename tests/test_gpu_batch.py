@@ -32,7 +32,8 @@ def droplet(d, seed):
                                        (lbm.BATCH_WORKLIST_DYNAMIC, 8),
                                        (lbm.BATCH_WORKLIST_DYNAMIC, 32),
                                        (lbm.BATCH_PERSISTENT, 0), (lbm.BATCH_COOPERATIVE, 16),
-                                       (lbm.BATCH_COOPERATIVE, 64), (lbm.BATCH_AUTO, 0)])
+                                       (lbm.BATCH_COOPERATIVE, 64), (lbm.BATCH_BALANCED, 0),
+                                       (lbm.BATCH_AUTO, 0)])
 def test_batch_matches_single_domain_bitwise(mode, rows):
     windows, window = 3, 10
     b = lbm.Batch(MIXED, window=window, tol=0.0, max_steps=10 ** 6, mode=mode,
@@ -58,7 +59,7 @@ ODD = [dict(nx=nx, ny=ny, T_over_Tc=0.85, tau=0.8, sigma=0.1, scheme=lbm.IMPROVE
 
 
 @pytest.mark.parametrize("mode,rows", [(lbm.BATCH_WORKLIST, 8), (lbm.BATCH_WORKLIST_DYNAMIC, 16),
-                                       (lbm.BATCH_PERSISTENT, 0)])
+                                       (lbm.BATCH_PERSISTENT, 0), (lbm.BATCH_BALANCED, 0)])
 def test_batch_odd_widths_on_the_two_column_body_bitwise(mode, rows):
     """Odd nx >= 3 run on the two-column body with rows padded to nx + 3 and
     columns nx, nx + 1 copying columns 0, 1 (nx = 1 stays on one column per
