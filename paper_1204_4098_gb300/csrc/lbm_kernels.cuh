@@ -295,6 +295,58 @@ __device__ __forceinline__ V load2(const V* p) {
   else return __ldg(p);
 }
 
+// Asynchronous copies global -> shared (cp.async, completion tracked per
+// thread in commit groups): the row fetch of the deviation-storage kernels.
+template <int N>  // bytes: 4, 8 or 16, both addresses aligned to N
+__device__ __forceinline__ void cp_async(void* smem, const void* g) {
+  static_assert(N == 4 || N == 8 || N == 16, "cp.async copies 4, 8 or 16 bytes");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(
+                   unsigned(__cvta_generic_to_shared(smem))),
+               "l"(g), "n"(N)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// One fetched row of a warp in shared memory, lane-major (each lane writes
+// and reads only its own column of every array): the pairs of the 9 planes;
+// for deviation storage also the density pair of the row after the pulled
+// row (the two before it stay in registers); the lane's extra element (the
+// FP32 value, or the aligned 32-bit word holding the 16-bit deviation, plus
+// its density).
+template <class S>
+struct AsyncRow {
+  typename Vec2<typename S::T>::type d[kQ][32];
+  float2 rr[S::kDev ? 32 : 1];
+  unsigned hd[32];
+  float hr[S::kDev ? 32 : 1];
+};
+#ifndef LBM_ASYNC_F32
+#define LBM_ASYNC_F32 0
+#endif
+// Storage whose rows are fetched asynchronously (non-coherent loads only).
+template <class S>
+constexpr bool async_fetch() {
+  return S::kDev || (LBM_ASYNC_F32 && std::is_same<S, StoreF32>::value);
+}
+#ifndef LBM_ASYNC_STAGES
+#define LBM_ASYNC_STAGES 3
+#endif
+// stages per warp: kAsyncStages - 1 rows in flight (y + 2, y + 3, ...) while
+// row y is computed, plus the stage of row y + 1, already assembled
+constexpr int kAsyncStages = LBM_ASYNC_STAGES;
+
+template <class S>
+__device__ __forceinline__ AsyncRow<S>* async_rows() {
+  __shared__ AsyncRow<S> s_rows[kStripWarpsPerCta * kAsyncStages];
+  return s_rows + (threadIdx.x >> 5) * kAsyncStages;
+}
+
 // kPadded: rows may have the odd-nx layout (pitch nx + 3, see StripArgs);
 // the batch engine's body.  The single-lattice kernels have pitch = nx, even.
 template <class S, int SCHEME, int MODE, bool kCoherent = false, bool kPadded = false>
@@ -466,24 +518,9 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
   // psi ring: rows y-1 (m), y (z)
   P2 Wm = P2(C(0)), Cm = P2(C(0)), Em = P2(C(0)), Wz = P2(C(0)), Cz = P2(C(0)), Ez = P2(C(0));
   P2 r0;
-  Raw next;
-  {
-    // the three rows before the first are fetched together: one memory
-    // round trip at the start of a band instead of three in sequence
-    Raw Rm, Rz;
-    P2 rd;
-    fetch_row(y0 == 0 ? ny - 1 : y0 - 1, Rm);
-    fetch_row(y0, Rz);
-    fetch_row(y0 + 1 == ny ? 0 : y0 + 1, next);
-    assemble(Rm, P0, h1);
-    psi_row(P0, h1, Wm, Cm, Em, rd);
-    assemble(Rz, P0, h1);
-    psi_row(P0, h1, Wz, Cz, Ez, r0);
-    assemble(next, P1, h1);
-  }
-  for (int y = y0; y < y1; ++y) {
-    const bool more = y + 2 <= y1;
-    if (more) fetch_row(y + 2 >= ny ? y + 2 - ny : y + 2, next);
+  // Output row y from P0 (its pulled populations) and P1 (row y + 1's);
+  // afterwards P0 holds row y + 1 and the psi ring has advanced.
+  auto compute_row = [&](int y) {
     P2 Wp = P2(C(0)), Cp = P2(C(0)), Ep = P2(C(0)), r1;
     psi_row(P1, h1, Wp, Cp, Ep, r1);
     P2 Fx = P2(C(0)), Fy = P2(C(0));
@@ -562,7 +599,129 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
     r0 = r1;
 #pragma unroll
     for (int a = 0; a < kQ; ++a) P0[a] = P1[a];
-    if (more) assemble(next, P1, h1);  // warp-uniform
+  };
+  auto wrap = [ny](int y) { return y >= ny ? y - ny : y; };
+
+  if constexpr (async_fetch<S>() && !kCoherent) {
+    // Rows are copied into shared memory asynchronously (cp.async), so a row
+    // in flight holds no registers, and kAsyncStages - 1 rows (y + 2, ...)
+    // are in flight while row y is computed.  Each lane waits for its own
+    // copies only (cp.async.wait_group) and reads only its own slots.
+    AsyncRow<S>* st = async_rows<S>();
+    auto fetch_async = [&](int y, AsyncRow<S>& R) {
+      const int ym = y == 0 ? ny - 1 : y - 1;
+      const int yp = y == ny - 1 ? 0 : y + 1;
+      const int rows[3] = {ym, y, yp};
+      if (qlane) {
+        int qy = y - qey;
+        qy = qy < 0 ? qy + ny : (qy >= ny ? qy - ny : qy);
+        const size_t e = size_t(qa) * A.plane + size_t(qy) * pitch + qsx;
+        if constexpr (S::kDev) {
+          cp_async<4>(&R.hd[lane], A.src + (e & ~size_t(1)));  // pitch and plane are even
+          cp_async<4>(&R.hr[lane], A.rho_src + size_t(qy) * pitch + qsx);
+        } else {
+          cp_async<4>(&R.hd[lane], A.src + e);
+        }
+      }
+      if constexpr (S::kDev) {
+        if (!ring_ok) {  // the band's first row: the two density rows before it
+          ring0 =
+              __ldg(reinterpret_cast<const float2*>(A.rho_src + size_t(rows[0]) * pitch + ca));
+          ring1 =
+              __ldg(reinterpret_cast<const float2*>(A.rho_src + size_t(rows[1]) * pitch + ca));
+          ring_ok = true;
+        }
+        cp_async<8>(&R.rr[lane], A.rho_src + size_t(rows[2]) * pitch + ca);
+      }
+#pragma unroll
+      for (int a = 0; a < kQ; ++a)
+        cp_async<sizeof(V)>(&R.d[a][lane],
+                            A.src + a * A.plane + size_t(rows[1 - ey_of(a)]) * pitch + ca);
+      cp_async_commit();
+    };
+    auto assemble_async = [&](const AsyncRow<S>& R, P2 (&P)[kQ], C& h) {
+      Raw W;
+#pragma unroll
+      for (int a = 0; a < kQ; ++a) W.v[a] = R.d[a][lane];
+      W.h = C(0);
+      if constexpr (S::kDev) {
+        W.rr[0] = ring0;
+        W.rr[1] = ring1;
+        W.rr[2] = R.rr[lane];
+        ring0 = W.rr[1];
+        ring1 = W.rr[2];
+        if (qlane) {  // as pull_one: w_a rho + d at the extra element's cell
+          const unsigned u = R.hd[lane];
+          const unsigned short bits = (qsx & 1) ? (unsigned short)(u >> 16) : (unsigned short)u;
+          T t;
+          __builtin_memcpy(&t, &bits, sizeof(bits));
+          W.h = fma_rn(w_of<C>(qa), C(R.hr[lane]), S::to_c(t));
+        }
+      } else {
+        if (qlane) W.h = S::to_c(__uint_as_float(R.hd[lane]));
+      }
+      assemble(W, P, h);
+    };
+    // Row r goes to stage (r - y0 + 1) mod kAsyncStages, fetched in order
+    // from y0 - 1; every row fetch (or its absence) commits one group, so
+    // the groups still pending after row y's fetch are rows y + 2 .. y + D.
+    constexpr int D = kAsyncStages - 1;
+    {
+      P2 rd;
+      fetch_async(y0 == 0 ? ny - 1 : y0 - 1, st[0]);
+      fetch_async(y0, st[1]);
+      fetch_async(wrap(y0 + 1), st[2]);
+#pragma unroll
+      for (int k = 2; k < D; ++k) {
+        if (y0 + k <= y1) fetch_async(wrap(y0 + k), st[k + 1]);
+        else cp_async_commit();  // an empty group keeps the count per row
+      }
+      cp_async_wait<D>();
+      assemble_async(st[0], P0, h1);
+      psi_row(P0, h1, Wm, Cm, Em, rd);
+      if (y0 + D <= y1) fetch_async(wrap(y0 + D), st[0]);
+      else cp_async_commit();
+      cp_async_wait<D>();
+      assemble_async(st[1], P0, h1);
+      psi_row(P0, h1, Wz, Cz, Ez, r0);
+      cp_async_wait<D - 1>();
+      assemble_async(st[2], P1, h1);
+    }
+    int sn = 3 % kAsyncStages, sf = 1;  // stages of rows y + 2 (next) and y + 1 + D
+    for (int y = y0; y < y1; ++y) {
+      if (y + 1 + D <= y1) fetch_async(wrap(y + 1 + D), st[sf]);  // into row y's stage
+      else cp_async_commit();
+      compute_row(y);
+      if (y + 2 <= y1) {  // warp-uniform
+        cp_async_wait<D - 1>();
+        assemble_async(st[sn], P1, h1);
+      }
+      sn = sn == kAsyncStages - 1 ? 0 : sn + 1;
+      sf = sf == kAsyncStages - 1 ? 0 : sf + 1;
+    }
+    cp_async_wait<0>();
+  } else {
+    Raw next;
+    {
+      // the three rows before the first are fetched together: one memory
+      // round trip at the start of a band instead of three in sequence
+      Raw Rm, Rz;
+      P2 rd;
+      fetch_row(y0 == 0 ? ny - 1 : y0 - 1, Rm);
+      fetch_row(y0, Rz);
+      fetch_row(wrap(y0 + 1), next);
+      assemble(Rm, P0, h1);
+      psi_row(P0, h1, Wm, Cm, Em, rd);
+      assemble(Rz, P0, h1);
+      psi_row(P0, h1, Wz, Cz, Ez, r0);
+      assemble(next, P1, h1);
+    }
+    for (int y = y0; y < y1; ++y) {
+      const bool more = y + 2 <= y1;
+      if (more) fetch_row(wrap(y + 2), next);
+      compute_row(y);
+      if (more) assemble(next, P1, h1);  // warp-uniform
+    }
   }
   if (__any_sync(FULL, bad) && lane == 0) atomicOr(A.status, kStatusDiverged);
 }
@@ -570,9 +729,13 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
 #ifndef LBM_STRIP2_MIN_BLOCKS
 #define LBM_STRIP2_MIN_BLOCKS 4  // 128 registers: the fetched row and the two assembled rows
 #endif
+#ifndef LBM_STRIP2_DEV_MIN_BLOCKS
+#define LBM_STRIP2_DEV_MIN_BLOCKS 4  // deviation storage (rows in flight in shared memory)
+#endif
 
 template <class S, int SCHEME, int MODE>
-__global__ void __launch_bounds__(kStripThreads, LBM_STRIP2_MIN_BLOCKS)
+__global__ void __launch_bounds__(kStripThreads,
+                                  S::kDev ? LBM_STRIP2_DEV_MIN_BLOCKS : LBM_STRIP2_MIN_BLOCKS)
 strip2_kernel(const StripArgs<S> A) {
   const int lane = threadIdx.x & 31;
   const int gwarp = (blockIdx.x * kStripThreads + threadIdx.x) >> 5;
