@@ -72,6 +72,9 @@ MEASURED_TRAFFIC = {
     # after the band prologue fetched its three rows together: 4096^2 capture
     # 615.3 MB read + 555.6 MB written per launch, x4 cells
     ("300215b053bb1d0a", "fp32", 8192, "pair"): 4.6836e9,
+    # rows fetched into shared memory with cp.async: 4096^2 capture 616.7 MB
+    # read + 555.6 MB written per launch, x4 cells
+    ("1026352877ad7d4b", "fp32", 8192, "pair"): 4.6892e9,
 }
 
 

@@ -104,7 +104,7 @@ template <bool kPair, int SCHEME, bool kCoherent>
 __device__ __forceinline__ void run_scheme(const StripArgs<StoreF32>& A, int strip, int band,
                                            int lane) {
   if constexpr (kPair)
-    strip_run2<StoreF32, SCHEME, kModeStep, kCoherent, true>(A, strip, band, lane);
+    strip_run2<StoreF32, SCHEME, kModeStep, kCoherent, true, false>(A, strip, band, lane);
   else
     strip_run<StoreF32, SCHEME, kModeStep, kCoherent>(A, strip, band, lane);
 }

@@ -326,13 +326,11 @@ struct AsyncRow {
   unsigned hd[32];
   float hr[S::kDev ? 32 : 1];
 };
-#ifndef LBM_ASYNC_F32
-#define LBM_ASYNC_F32 0
-#endif
-// Storage whose rows are fetched asynchronously (non-coherent loads only).
+// Storage whose rows can be fetched asynchronously (FP32 and 16-bit: pairs
+// of 4 or 8 bytes; FP64 keeps its rows in registers).
 template <class S>
 constexpr bool async_fetch() {
-  return S::kDev || (LBM_ASYNC_F32 && std::is_same<S, StoreF32>::value);
+  return S::kDev || std::is_same<S, StoreF32>::value;
 }
 #ifndef LBM_ASYNC_STAGES
 #define LBM_ASYNC_STAGES 3
@@ -349,7 +347,13 @@ __device__ __forceinline__ AsyncRow<S>* async_rows() {
 
 // kPadded: rows may have the odd-nx layout (pitch nx + 3, see StripArgs);
 // the batch engine's body.  The single-lattice kernels have pitch = nx, even.
-template <class S, int SCHEME, int MODE, bool kCoherent = false, bool kPadded = false>
+// kAsync: fetch rows into shared memory with cp.async where the storage
+// allows (async_fetch; non-coherent loads only).  The batch body keeps its
+// rows in registers: its short items measured faster that way (59.7k
+// against 51.8k MLUPS on 128 slabs), while one lattice gains (FP32 8192^2
+// 84.5k -> 87.1k, BF16 82.1k -> 87.0k).
+template <class S, int SCHEME, int MODE, bool kCoherent = false, bool kPadded = false,
+          bool kAsync = true>
 __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int band,
                                            int lane) {
   using C = typename S::C;
@@ -602,7 +606,7 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
   };
   auto wrap = [ny](int y) { return y >= ny ? y - ny : y; };
 
-  if constexpr (async_fetch<S>() && !kCoherent) {
+  if constexpr (kAsync && async_fetch<S>() && !kCoherent) {
     // Rows are copied into shared memory asynchronously (cp.async), so a row
     // in flight holds no registers, and kAsyncStages - 1 rows (y + 2, ...)
     // are in flight while row y is computed.  Each lane waits for its own

@@ -47,8 +47,10 @@ BUDGETS = [
     ("strip2_kernelINS_9StoreBF16E", 128, 0),  # two columns, BF16 deviations
     ("strip2_kernelINS_8StoreF16E", 128, 0),   # two columns, FP16 deviations
     ("strip_kernelINS_8StoreF32E", 80, 0),     # one column per lane, FP32
-    ("batch_worklist_kernelILb0E", 80, 0),     # batch, one column (6 CTAs per SM)
-    ("batch_worklist_kernelILb1E", 128, 80),   # batch, two columns: 76 B measured
+    ("batch_worklist_kernelILb0E", 80, 8),     # batch, one column (6 CTAs per SM): 4 B
+    ("batch_worklist_kernelILb1E", 128, 16),   # batch, two columns: 8 B measured (76 B
+                                               # before the item prologue's rows were
+                                               # fetched together)
 ]
 
 
