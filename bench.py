@@ -75,6 +75,9 @@ MEASURED_TRAFFIC = {
     # rows fetched into shared memory with cp.async: 4096^2 capture 616.7 MB
     # read + 555.6 MB written per launch, x4 cells
     ("1026352877ad7d4b", "fp32", 8192, "pair"): 4.6892e9,
+    # the same FP32 kernel after the 16-bit unpack change (StoreBF16 only):
+    # 4096^2 capture 616.8 MB read + 555.5 MB written per launch, x4 cells
+    ("01946c2627dbfadb", "fp32", 8192, "pair"): 4.6893e9,
 }
 
 
