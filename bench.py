@@ -78,6 +78,10 @@ MEASURED_TRAFFIC = {
     # the same FP32 kernel after the 16-bit unpack change (StoreBF16 only):
     # 4096^2 capture 616.8 MB read + 555.5 MB written per launch, x4 cells
     ("01946c2627dbfadb", "fp32", 8192, "pair"): 4.6893e9,
+    # after the odd-nx store change of the batch body (single lattices
+    # unpadded) and narrower compiler barriers around the row copies: 4096^2
+    # capture 616.7 MB read + 555.8 MB written per launch, x4 cells
+    ("93fd099c0bd56bf9", "fp32", 8192, "pair"): 4.6899e9,
 }
 
 

@@ -4,9 +4,10 @@
 // (strip_run2, two columns per lane; strip_run, one column per lane, for
 // nx = 1 or when asked for; both in lbm_kernels.cuh) on its own slice of one
 // packed buffer pair.  An odd-nx instance on the two-column body has rows of
-// nx + 3 elements whose columns nx, nx + 1 copy columns 0 and 1 (the lane
-// holding columns 0 and 1 writes the copies every step), so pairs stay
-// aligned and the last column meets its periodic neighbour.  Instances fall
+// nx + 3 elements whose columns nx .. nx + 2 copy columns 0 .. 2 (refreshed
+// every step: column nx by the pair store of the lane holding the last
+// column, the other two by the lanes holding columns 1 and 2), so pairs stay
+// aligned and the last column meets its periodic neighbours.  Instances fall
 // in two classes by body, each with kernels of its own (separate register
 // budgets).  A window of `window` steps is one CUDA graph, in one of
 // three launch modes:
@@ -50,7 +51,7 @@ struct BatchInst {
   size_t coff;             // cell offset in the density snapshot
   int nx, ny, n_strips;     // strips of 64 columns (pair) or 32
   int pitch;               // row pitch of the population planes: nx, or nx + 3 for odd nx
-                           // on the two-column body (columns nx, nx + 1 copy columns 0, 1)
+                           // on the two-column body (columns nx .. nx + 2 copy columns 0 .. 2)
   int pair;                // two columns per lane (strip_run2): even nx, and odd nx >= 3
   int band_rows, n_bands;  // work-list geometry
   int pband_rows, pn_bands;  // persistent geometry

@@ -52,7 +52,7 @@ struct StripArgs {
   unsigned* status;           // device status word
   int nx, ny;                 // ny: rows of the buffers
   int pitch;                  // elements per row of a plane: nx, or nx + 3 for odd nx in the
-                              // two-column kernel (columns nx, nx + 1 copy columns 0, 1)
+                              // two-column kernel (columns nx .. nx + 2 copy columns 0 .. 2)
   int y_begin, y_end;         // rows computed (a domain band: the owned rows)
   int out_row0;               // observe mode: output row of buffer row out_row0 is 0
   int n_strips;               // ceil(nx / 32)
@@ -296,18 +296,21 @@ __device__ __forceinline__ V load2(const V* p) {
 }
 
 // Asynchronous copies global -> shared (cp.async, completion tracked per
-// thread in commit groups): the row fetch of the deviation-storage kernels.
+// thread in commit groups): the row fetch of the two-column kernels.  Only
+// the wait is a compiler memory barrier: reads of a stage cannot move above
+// the wait that completes it, nor below the next wait, which every reuse of
+// the stage follows (the prologue places its own barrier where a stage is
+// refetched without one).  Issuing and committing copies then does not
+// force values held in memory (the batch body's per-item arguments in
+// shared memory) to be read again.
 template <int N>  // bytes: 4, 8 or 16, both addresses aligned to N
 __device__ __forceinline__ void cp_async(void* smem, const void* g) {
   static_assert(N == 4 || N == 8 || N == 16, "cp.async copies 4, 8 or 16 bytes");
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(
                    unsigned(__cvta_generic_to_shared(smem))),
-               "l"(g), "n"(N)
-               : "memory");
+               "l"(g), "n"(N));
 }
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
@@ -349,9 +352,10 @@ __device__ __forceinline__ AsyncRow<S>* async_rows() {
 // the batch engine's body.  The single-lattice kernels have pitch = nx, even.
 // kAsync: fetch rows into shared memory with cp.async where the storage
 // allows (async_fetch; non-coherent loads only).  The batch body keeps its
-// rows in registers: its short items measured faster that way (59.7k
-// against 51.8k MLUPS on 128 slabs), while one lattice gains (FP32 8192^2
-// 84.5k -> 87.1k, BF16 82.1k -> 87.0k).
+// rows in registers: its short items measured faster that way (59.8k
+// against 51.9k MLUPS on 128 slabs, with or without the copies acting as
+// compiler memory barriers), while one lattice gains (FP32 8192^2 84.5k ->
+// 87.1k, BF16 82.1k -> 87.0k).
 template <class S, int SCHEME, int MODE, bool kCoherent = false, bool kPadded = false,
           bool kAsync = true>
 __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int band,
@@ -370,11 +374,11 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
   const int xa = x0 + 2 * lane;         // left column of this lane
   const bool active_a = xa < nx, active_b = xa + 1 < nx;
   // Even nx (pitch nx): lanes past the edge take the wrapped columns, which
-  // serve as the right neighbours.  Odd nx (pitch nx + 3): columns nx and
-  // nx + 1 of every row hold copies of columns 0 and 1, so the lane whose
-  // cell a is the last column nx - 1 has column 0 as its cell b, and the
-  // next lane columns 1 and an unused one -- the periodic neighbours, with
-  // aligned pairs; lanes further out read column 0 (their cells are unused).
+  // serve as the right neighbours.  Odd nx (pitch nx + 3): columns nx .. nx
+  // + 2 of every row hold copies of columns 0 .. 2, so the lane whose cell a
+  // is the last column nx - 1 has column 0 as its cell b, and the next lane
+  // columns 1 and 2 -- the periodic neighbours, with aligned pairs; lanes
+  // further out read column 0 (their cells are unused).
   const int ca = (!kPadded || pitch == nx) ? xa % nx : (xa < pitch ? xa : 0);
   // extra-element lanes: 0..8 halo pulls of column x0-1 (plane = lane),
   // 9..11 column x0-1 of planes 1, 5, 8 (e_x = +1), 16..24 halo pulls of
@@ -533,13 +537,15 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
     if constexpr (MODE == kModeStep) {
       collide<SCHEME>(P0, r0, Fx, Fy, Cz, A.P);
       if (active_a) {
-        // Both cells are stored as a pair, or, for the lane holding the last
-        // column of an odd nx, cell a alone (its cell b is the copy of
-        // column 0, which the lane holding columns 0 and 1 writes).  With odd
-        // nx that lane also stores its two cells into the copies.
-        const bool both = !kPadded || active_b;  // even nx: both cells are inside
-        const bool copies = kPadded && pitch != nx && xa == 0;
-        const size_t ghost = size_t(y) * pitch + nx;
+        // Every active lane stores its two cells as a pair.  With odd nx
+        // (pitch nx + 3, columns nx .. nx + 2 holding copies of columns
+        // 0 .. 2) the lane whose cell a is the last column has column nx as
+        // its cell b; all its inputs (pulls, and psi up to column nx + 1) are
+        // copies, so it computes column 0's values exactly and its pair store
+        // refreshes that copy.  Lanes 0 and 1 of strip 0 refresh the copies
+        // of columns 1 and 2.
+        const bool copies = kPadded && pitch != nx && xa < 4;
+        const size_t gidx = size_t(y) * pitch + (xa == 0 ? nx + 1 : nx + 2);
         if constexpr (S::kDev) {
           // the density plane absorbs the 16-bit rounding of the deviations
           P2 res = r0;
@@ -548,21 +554,13 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
             const P2 d = fma_rn(P2(-w_of<C>(a)), r0, P0[a]);
             const V v = S::from_c2(d.x(), d.y());
             T* plane = A.dst + a * A.plane;
-            if (both) *reinterpret_cast<V*>(plane + idx) = v;
-            else plane[idx] = v.x;
-            if (copies) {
-              plane[ghost] = v.x;
-              plane[ghost + 1] = v.y;
-            }
+            *reinterpret_cast<V*>(plane + idx) = v;
+            if (copies) plane[gidx] = xa == 0 ? v.y : v.x;
             res = sub_rn(res, P2(S::to_c2(v)));
           }
           const float2 rp = make_float2(float(res.x()), float(res.y()));
-          if (both) *reinterpret_cast<float2*>(A.rho_dst + idx) = rp;
-          else A.rho_dst[idx] = rp.x;
-          if (copies) {
-            A.rho_dst[ghost] = rp.x;
-            A.rho_dst[ghost + 1] = rp.y;
-          }
+          *reinterpret_cast<float2*>(A.rho_dst + idx) = rp;
+          if (copies) A.rho_dst[gidx] = xa == 0 ? rp.y : rp.x;
         } else {
 #pragma unroll
           for (int a = 0; a < kQ; ++a) {
@@ -570,12 +568,8 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
             v.x = S::from_c(P0[a].x());
             v.y = S::from_c(P0[a].y());
             T* plane = A.dst + a * A.plane;
-            if (both) *reinterpret_cast<V*>(plane + idx) = v;
-            else plane[idx] = v.x;
-            if (copies) {
-              plane[ghost] = v.x;
-              plane[ghost + 1] = v.y;
-            }
+            *reinterpret_cast<V*>(plane + idx) = v;
+            if (copies) plane[gidx] = xa == 0 ? v.y : v.x;
           }
         }
       }
@@ -683,6 +677,7 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
       cp_async_wait<D>();
       assemble_async(st[0], P0, h1);
       psi_row(P0, h1, Wm, Cm, Em, rd);
+      asm volatile("" ::: "memory");  // stage 0's reads stay before its refetch
       if (y0 + D <= y1) fetch_async(wrap(y0 + D), st[0]);
       else cp_async_commit();
       cp_async_wait<D>();
