@@ -438,7 +438,8 @@ def test_staged_kernel_fp32_parity_with_oracle():
                                    (66, 40), (100, 17), (130, 65)])
 def test_pair_kernel_matches_register_kernel_bitwise(precision, nx, ny):
     """Two columns per lane (vector loads, shuffled +-1 pulls, boundary and
-    halo elements from extra lanes, wrapped lanes in ragged strips) computes
+    halo elements from extra lanes, wrapped lanes in ragged strips, rows
+    copied into shared memory ahead of use, bands of one row) computes
     exactly what one column per lane does: steps of every scheme and the
     observed density and velocity, in every storage type (16-bit deviation
     storage included: deviations and density plane pairs)."""
@@ -448,7 +449,7 @@ def test_pair_kernel_matches_register_kernel_bitwise(precision, nx, ny):
                           (lbm.NOFORCE, 0.0)):
         out = []
         for variant, rows in ((lbm.VARIANT_REGISTER, 0), (lbm.VARIANT_PAIR, 0),
-                              (lbm.VARIANT_PAIR, 3)):
+                              (lbm.VARIANT_PAIR, 1), (lbm.VARIANT_PAIR, 3)):
             g = lbm.Lattice(nx, ny, t, precision=precision)
             g.set_variant(variant)
             g.set_band_rows(rows)
