@@ -82,6 +82,10 @@ MEASURED_TRAFFIC = {
     # unpadded) and narrower compiler barriers around the row copies: 4096^2
     # capture 616.7 MB read + 555.8 MB written per launch, x4 cells
     ("93fd099c0bd56bf9", "fp32", 8192, "pair"): 4.6899e9,
+    # buffer pointers held in registers on the row-copy path, copy stores
+    # addressed from the pair store: 4096^2 capture 616.7 MB read + 555.8 MB
+    # written per launch, x4 cells
+    ("078d563a4c56ea55", "fp32", 8192, "pair"): 4.6899e9,
 }
 
 

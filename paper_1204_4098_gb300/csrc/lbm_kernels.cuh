@@ -351,11 +351,12 @@ __device__ __forceinline__ AsyncRow<S>* async_rows() {
 // kPadded: rows may have the odd-nx layout (pitch nx + 3, see StripArgs);
 // the batch engine's body.  The single-lattice kernels have pitch = nx, even.
 // kAsync: fetch rows into shared memory with cp.async where the storage
-// allows (async_fetch; non-coherent loads only).  The batch body keeps its
-// rows in registers: its short items measured faster that way (59.8k
-// against 51.9k MLUPS on 128 slabs, with or without the copies acting as
-// compiler memory barriers), while one lattice gains (FP32 8192^2 84.5k ->
-// 87.1k, BF16 82.1k -> 87.0k).
+// allows (async_fetch; non-coherent loads only).  One lattice gains (FP32
+// 8192^2 84.5k -> 87.1k, BF16 82.1k -> 87.0k), and so do its short bands
+// (2048^2 with 16-row bands: 66.4k -> 73.1k).  The batch body keeps its rows
+// in registers: with its item loop and two scheme bodies the row-copy
+// variant spills 36-44 B and measured slower (whole default sweep 52.9k
+// against 54.6k MLUPS).
 template <class S, int SCHEME, int MODE, bool kCoherent = false, bool kPadded = false,
           bool kAsync = true>
 __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int band,
@@ -368,6 +369,22 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
                               (MODE == kModeStep && SCHEME == kNoForce));
   const unsigned FULL = 0xffffffffu;
   const int nx = A.nx, ny = A.ny, pitch = kPadded ? A.pitch : A.nx;
+  // With the rows fetched by cp.async, the buffer pointers and the plane
+  // size are held in registers: the batch body's arguments live in shared
+  // memory, and reading them there at every row copy measured 10-15 %
+  // slower.  On the register-fetch path they stay references to the
+  // arguments, which keeps registers free for the held rows.
+  constexpr bool kRowCopy = kAsync && async_fetch<S>() && !kCoherent;
+  using HoldSrc = std::conditional_t<kRowCopy, const T* const, const T* const&>;
+  using HoldDst = std::conditional_t<kRowCopy, T* const, T* const&>;
+  using HoldRSrc = std::conditional_t<kRowCopy, const float* const, const float* const&>;
+  using HoldRDst = std::conditional_t<kRowCopy, float* const, float* const&>;
+  using HoldPlane = std::conditional_t<kRowCopy, const size_t, const size_t&>;
+  HoldSrc f_src = A.src;
+  HoldDst f_dst = A.dst;
+  HoldRSrc r_src = A.rho_src;
+  HoldRDst r_dst = A.rho_dst;
+  HoldPlane f_plane = A.plane;
   const int y0 = A.y_begin + band * A.band_rows;
   const int y1 = min(y0 + A.band_rows, A.y_end);
   const int x0 = strip * 64;
@@ -431,7 +448,7 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
     if constexpr (S::kDev) {
       auto plane_row = [&](int r) {
         return load2<kCoherent>(
-            reinterpret_cast<const float2*>(A.rho_src + size_t(r) * pitch + ca));
+            reinterpret_cast<const float2*>(r_src + size_t(r) * pitch + ca));
       };
       if (ring_ok) {  // warp-uniform
         R.rr[0] = ring0;
@@ -449,7 +466,7 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
     for (int a = 0; a < kQ; ++a) {
       const int r = rows[1 - ey_of(a)];  // source row y - ey
       R.v[a] =
-          load2<kCoherent>(reinterpret_cast<const V*>(A.src + a * A.plane + size_t(r) * pitch + ca));
+          load2<kCoherent>(reinterpret_cast<const V*>(f_src + a * f_plane + size_t(r) * pitch + ca));
     }
   };
   // pulled populations of the lane's two cells (P[a].x at ca, .y at ca + 1)
@@ -545,7 +562,7 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
         // refreshes that copy.  Lanes 0 and 1 of strip 0 refresh the copies
         // of columns 1 and 2.
         const bool copies = kPadded && pitch != nx && xa < 4;
-        const size_t gidx = size_t(y) * pitch + (xa == 0 ? nx + 1 : nx + 2);
+        const int goff = xa == 0 ? nx + 1 : nx;  // from the lane's pair to its copy
         if constexpr (S::kDev) {
           // the density plane absorbs the 16-bit rounding of the deviations
           P2 res = r0;
@@ -553,23 +570,23 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
           for (int a = 0; a < kQ; ++a) {
             const P2 d = fma_rn(P2(-w_of<C>(a)), r0, P0[a]);
             const V v = S::from_c2(d.x(), d.y());
-            T* plane = A.dst + a * A.plane;
-            *reinterpret_cast<V*>(plane + idx) = v;
-            if (copies) plane[gidx] = xa == 0 ? v.y : v.x;
+            T* const at = f_dst + a * f_plane + idx;
+            *reinterpret_cast<V*>(at) = v;
+            if (copies) at[goff] = xa == 0 ? v.y : v.x;
             res = sub_rn(res, P2(S::to_c2(v)));
           }
           const float2 rp = make_float2(float(res.x()), float(res.y()));
-          *reinterpret_cast<float2*>(A.rho_dst + idx) = rp;
-          if (copies) A.rho_dst[gidx] = xa == 0 ? rp.y : rp.x;
+          *reinterpret_cast<float2*>(r_dst + idx) = rp;
+          if (copies) r_dst[idx + goff] = xa == 0 ? rp.y : rp.x;
         } else {
 #pragma unroll
           for (int a = 0; a < kQ; ++a) {
             V v;
             v.x = S::from_c(P0[a].x());
             v.y = S::from_c(P0[a].y());
-            T* plane = A.dst + a * A.plane;
-            *reinterpret_cast<V*>(plane + idx) = v;
-            if (copies) plane[gidx] = xa == 0 ? v.y : v.x;
+            T* const at = f_dst + a * f_plane + idx;
+            *reinterpret_cast<V*>(at) = v;
+            if (copies) at[goff] = xa == 0 ? v.y : v.x;
           }
         }
       }
@@ -600,7 +617,7 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
   };
   auto wrap = [ny](int y) { return y >= ny ? y - ny : y; };
 
-  if constexpr (kAsync && async_fetch<S>() && !kCoherent) {
+  if constexpr (kRowCopy) {
     // Rows are copied into shared memory asynchronously (cp.async), so a row
     // in flight holds no registers, and kAsyncStages - 1 rows (y + 2, ...)
     // are in flight while row y is computed.  Each lane waits for its own
@@ -613,28 +630,28 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
       if (qlane) {
         int qy = y - qey;
         qy = qy < 0 ? qy + ny : (qy >= ny ? qy - ny : qy);
-        const size_t e = size_t(qa) * A.plane + size_t(qy) * pitch + qsx;
+        const size_t e = size_t(qa) * f_plane + size_t(qy) * pitch + qsx;
         if constexpr (S::kDev) {
-          cp_async<4>(&R.hd[lane], A.src + (e & ~size_t(1)));  // pitch and plane are even
-          cp_async<4>(&R.hr[lane], A.rho_src + size_t(qy) * pitch + qsx);
+          cp_async<4>(&R.hd[lane], f_src + (e & ~size_t(1)));  // pitch and plane are even
+          cp_async<4>(&R.hr[lane], r_src + size_t(qy) * pitch + qsx);
         } else {
-          cp_async<4>(&R.hd[lane], A.src + e);
+          cp_async<4>(&R.hd[lane], f_src + e);
         }
       }
       if constexpr (S::kDev) {
         if (!ring_ok) {  // the band's first row: the two density rows before it
           ring0 =
-              __ldg(reinterpret_cast<const float2*>(A.rho_src + size_t(rows[0]) * pitch + ca));
+              __ldg(reinterpret_cast<const float2*>(r_src + size_t(rows[0]) * pitch + ca));
           ring1 =
-              __ldg(reinterpret_cast<const float2*>(A.rho_src + size_t(rows[1]) * pitch + ca));
+              __ldg(reinterpret_cast<const float2*>(r_src + size_t(rows[1]) * pitch + ca));
           ring_ok = true;
         }
-        cp_async<8>(&R.rr[lane], A.rho_src + size_t(rows[2]) * pitch + ca);
+        cp_async<8>(&R.rr[lane], r_src + size_t(rows[2]) * pitch + ca);
       }
 #pragma unroll
       for (int a = 0; a < kQ; ++a)
         cp_async<sizeof(V)>(&R.d[a][lane],
-                            A.src + a * A.plane + size_t(rows[1 - ey_of(a)]) * pitch + ca);
+                            f_src + a * f_plane + size_t(rows[1 - ey_of(a)]) * pitch + ca);
       cp_async_commit();
     };
     auto assemble_async = [&](const AsyncRow<S>& R, P2 (&P)[kQ], C& h) {
