@@ -384,6 +384,11 @@ def run_ours(args, world, rank, local):
         h_rho0 = pin()
         h_rho0[...] = rho0
         outs = (pin(), pin(), pin())
+        # one untimed pass through the same calls first (warm-up, like the
+        # device-timed steps): the page-locked buffers' first transfers
+        lat.init_density(h_rho0)
+        lat.step_async(1, lbm.IMPROVED, 0.8, 0.1)
+        lat.observe(out=outs)
         dist_barrier(world)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
