@@ -87,3 +87,20 @@ def test_band_runner_with_overlap_matches_whole_lattice():
         for a, b in zip(band.observe(), whole.observe()):
             assert np.array_equal(a, b), ny
         band.close()
+
+
+@pytest.mark.parametrize("precision", [lbm.FP32, lbm.BF16DEV])
+def test_bands_with_odd_width_match_whole_lattice_bitwise(precision):
+    """Odd nx runs on the one-column kernel; its bands carry the same two
+    ghost rows and exchange the same messages (width nx)."""
+    nx, ny, steps = 71, 38, 25
+    rg, rl, _ = th.maxwell(th.CarnahanStarling(th.temperature(T)))
+    rho = inputs.droplet(nx, ny, rg, rl, 11.0, W=4.0, x0=nx / 2.0, y0=ny - 2.0)
+    whole = lbm.Lattice(nx, ny, T, precision=precision)
+    whole.init_density_at_rest(rho)
+    whole.step(steps, lbm.EDM, 0.7)
+    for overlap in (False, True):
+        bands = halo.LocalBands(nx, ny, T, rho, 3, precision=precision, at_rest=True)
+        assert bands.step(steps, lbm.EDM, 0.7, overlap=overlap) == lbm.LBM_OK
+        assert np.array_equal(bands.populations(), whole.populations())
+        bands.close()
