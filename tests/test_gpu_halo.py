@@ -67,6 +67,23 @@ def test_band_contract():
     assert e.value.status == lbm.LBM_E_STATE
     with pytest.raises(lbm.LbmError):
         lbm.Lattice(NX, 1, T, band=True)  # a band owns at least two rows
+    import torch
+    buf = [torch.empty(b.halo_bytes(), dtype=torch.uint8, device="cuda") for _ in range(2)]
+    lo, hi = buf[0].data_ptr(), buf[1].data_ptr()
+    with pytest.raises(lbm.LbmError) as e:
+        whole.step_overlap(lbm.SC, 1.0, 0.0, lo, hi)  # not a band
+    assert e.value.status == lbm.LBM_E_STATE
+    for bad in ((lbm.SC, 0.5, 0.0), (99, 1.0, 0.0), (lbm.SC, 1.0, float("nan"))):
+        with pytest.raises(lbm.LbmError) as e:
+            b.step_overlap(*bad, lo, hi)
+        assert e.value.status == lbm.LBM_E_INVAL
+    with pytest.raises(lbm.LbmError) as e:
+        b.step_overlap(lbm.SC, 1.0, 0.0, 0, hi)  # no buffer
+    assert e.value.status == lbm.LBM_E_INVAL
+    fresh = lbm.Lattice(NX, 6, T, band=True)
+    with pytest.raises(lbm.LbmError) as e:
+        fresh.step_overlap(lbm.SC, 1.0, 0.0, lo, hi)  # not initialised
+    assert e.value.status == lbm.LBM_E_STATE
 
 
 def test_band_runner_with_overlap_matches_whole_lattice():
