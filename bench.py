@@ -17,6 +17,9 @@ are far larger than L2, so no flush is needed between steps.
                 memory: lbm_init_density (H2D), K steps, lbm_get_moments (D2H).
 * cpu_baseline -- the FP64 oracle (test infrastructure) on a bounded sample
                 of the same workload, on this host's cores.
+* storage_variants, batched_sweep (128 slabs, with the sequential plain runs
+  measured over all of them), batched_sweep_config4_512 (the 512-slab sweep,
+  batched), warm_start (a reduced config 5) -- the other workloads' legs.
 
 ``--impl reference`` times the oracle alone as the reference arm.
 Under torchrun every rank runs its own replica (weak scaling).
@@ -425,9 +428,10 @@ def run_ours(args, world, rank, local):
                               "frac": gbs / peak, "bytes_per_cell": BYTES_PER_CELL[name]}
             v.close()
 
-    sweep_line = None
+    sweep_line = sweep512 = None
     if rank == 0 and not args.no_sweep:
         sweep_line = sweep_measure(128, 128, seed=4, device=local)
+        sweep512 = sweep_batched_only(512, seed=4, device=local)
 
     warm_line = None
     if rank == 0 and not args.no_warmstart:
@@ -453,6 +457,8 @@ def run_ours(args, world, rank, local):
             line["storage_variants"] = variants
         if sweep_line:
             line["batched_sweep"] = sweep_line
+        if sweep512:
+            line["batched_sweep_config4_512"] = sweep512
         if warm_line:
             line["warm_start"] = warm_line
         print(json.dumps(line), flush=True)
@@ -508,6 +514,26 @@ def sweep_measure(n_inst, n_seq, seed=4, device=0):
             "coexistence_max_rel_diff_vs_sequential": agree, "converged_in_both": n_both,
             "convergence_rule": "COEX: rho_g, rho_l (FP64 row means) change < max(1e-9, 8 ulp) "
                                 "over two consecutive 1000-step windows; cap 2e5 steps",
+            "init": "cold: Maxwell densities, sharp slab (rows [ny/4, 3ny/4) liquid)"}
+
+
+def sweep_batched_only(n_inst, seed=4, device=0):
+    """Config 4 at its full size (512 instances), batched only: the
+    sequential baseline of this size is measured by --workload sweep (a
+    sample, scaled), the 128-instance sweep of the default line measures it
+    over every instance."""
+    import numpy as np
+
+    from paper_1204_4098_gb300 import inputs, sweep
+    inst = inputs.sweep_instances(n_inst, seed=seed)
+    g, l = sweep.cold_start_profiles(inst)
+    res, stats, wall = sweep.run_batched(inst, g, l, np.zeros(n_inst), device=device)
+    cells_steps = sum(d["nx"] * d["ny"] * r["steps"] for d, r in zip(inst, res))
+    return {"instances": n_inst, "batched_wall_s": wall, "batched_gpu_s": stats["gpu_ms"] / 1e3,
+            "instances_per_s": n_inst / wall,
+            "batched_MLUPS": cells_steps / (stats["gpu_ms"] * 1e-3) / 1e6,
+            "windows": stats["windows"], "status": _status_counts(res),
+            "convergence_rule": "COEX (as the 128-instance sweep); cap 2e5 steps",
             "init": "cold: Maxwell densities, sharp slab (rows [ny/4, 3ny/4) liquid)"}
 
 
