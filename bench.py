@@ -89,6 +89,9 @@ MEASURED_TRAFFIC = {
     # addressed from the pair store: 4096^2 capture 616.7 MB read + 555.8 MB
     # written per launch, x4 cells
     ("078d563a4c56ea55", "fp32", 8192, "pair"): 4.6899e9,
+    # the same FP32 kernel after the 16-bit decode / residual change (16-bit
+    # paths only): 4096^2 capture 616.8 MB read + 555.9 MB written, x4 cells
+    ("bab0aef77fdf5a50", "fp32", 8192, "pair"): 4.6906e9,
 }
 
 

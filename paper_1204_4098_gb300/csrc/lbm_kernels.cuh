@@ -71,15 +71,14 @@ enum { kModeStep = 0, kModeObserve = 1, kModeObserveNoForce = 2 };
 template <class S, bool kCoherent>
 __device__ __forceinline__ typename S::C pull_one(const StripArgs<S>& A, int a, int idx) {
   using C = typename S::C;
-  C v;
-  if constexpr (kCoherent) {
-    v = S::to_c(__ldcg(A.src + a * A.plane + idx));
-    if constexpr (S::kDev) v = fma_rn(w_of<C>(a), C(__ldcg(A.rho_src + idx)), v);
+  const typename S::T d = kCoherent ? __ldcg(A.src + a * A.plane + idx)
+                                     : __ldg(A.src + a * A.plane + idx);
+  if constexpr (S::kDev) {
+    const C r = C(kCoherent ? __ldcg(A.rho_src + idx) : __ldg(A.rho_src + idx));
+    return S::decode(mul_rn(w_of<C>(a), r), d);  // w_a rho + d
   } else {
-    v = S::to_c(__ldg(A.src + a * A.plane + idx));
-    if constexpr (S::kDev) v = fma_rn(w_of<C>(a), C(__ldg(A.rho_src + idx)), v);
+    return S::to_c(d);
   }
-  return v;
 }
 
 static __constant__ int c_ex[16] = {0, 1, 0, -1, 0, 1, -1, -1, 1, 0, 0, 0, 0, 0, 0, 0};
@@ -477,7 +476,7 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
       const int ex = ex_of(a), ey = ey_of(a);
       P2 v;  // the two values loaded at ca, ca + 1
       if constexpr (S::kDev) {
-        v = fma_rn(P2(w_of<C>(a)), P2(R.rr[1 - ey]), P2(S::to_c2(R.v[a])));
+        v = S::decode2(mul_rn(P2(w_of<C>(a)), P2(R.rr[1 - ey])), R.v[a]);
       } else {
         v = P2(S::to_c(R.v[a].x), S::to_c(R.v[a].y));
       }
@@ -573,7 +572,7 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
             T* const at = f_dst + a * f_plane + idx;
             *reinterpret_cast<V*>(at) = v;
             if (copies) at[goff] = xa == 0 ? v.y : v.x;
-            res = sub_rn(res, P2(S::to_c2(v)));
+            res = S::sub_from(res, v);
           }
           const float2 rp = make_float2(float(res.x()), float(res.y()));
           *reinterpret_cast<float2*>(r_dst + idx) = rp;
@@ -670,7 +669,7 @@ __device__ __forceinline__ void strip_run2(const StripArgs<S>& A, int strip, int
           const unsigned short bits = (qsx & 1) ? (unsigned short)(u >> 16) : (unsigned short)u;
           T t;
           __builtin_memcpy(&t, &bits, sizeof(bits));
-          W.h = fma_rn(w_of<C>(qa), C(R.hr[lane]), S::to_c(t));
+          W.h = S::decode(mul_rn(w_of<C>(qa), C(R.hr[lane])), t);
         }
       } else {
         if (qlane) W.h = S::to_c(__uint_as_float(R.hd[lane]));
