@@ -21,8 +21,11 @@
 // wrapped columns (serving as the right neighbour) and store nothing.
 // strip_run / strip_kernel below is this design with one column per lane;
 // strip_run2 / strip2_kernel gives each lane two adjacent columns of a
-// 64-column strip (even nx), and strip_tma_kernel stages the rows in shared
-// memory with bulk copies.  All three compute the same values bit for bit.
+// 64-column strip (even nx) and, for FP32 and 16-bit storage on single
+// lattices, copies the rows it fetches ahead into shared memory with
+// per-lane cp.async (two rows in flight, no registers held for them);
+// strip_tma_kernel stages the rows in shared memory with bulk copies.  All
+// three compute the same values bit for bit.
 #pragma once
 
 #include "lbm_device.cuh"
