@@ -424,7 +424,9 @@ def run_ours(args, world, rank, local):
     lat.close()
 
     variants = {}
-    if args.variants and rank == 0:
+    # the other workloads' legs are single-GPU measurements: N = 1 only, so
+    # that a scaling run times its replicas and nothing else
+    if args.variants and rank == 0 and world == 1:
         for name, p in (("bf16dev", lbm.BF16DEV), ("fp16dev", lbm.FP16DEV)):
             v = lbm.Lattice(n, n, 0.85, precision=p, device=local, stream=stream.cuda_stream)
             v.init_density(rho0)
@@ -444,12 +446,12 @@ def run_ours(args, world, rank, local):
             v.close()
 
     sweep_line = sweep512 = None
-    if rank == 0 and not args.no_sweep:
+    if rank == 0 and world == 1 and not args.no_sweep:
         sweep_line = sweep_measure(128, 128, seed=4, device=local)
         sweep512 = sweep_batched_only(512, seed=4, device=local)
 
     warm_line = None
-    if rank == 0 and not args.no_warmstart:
+    if rank == 0 and world == 1 and not args.no_warmstart:
         warm_line = {"label": "reduced config 5: 6,000 training draws (nx = 32 slabs, cap 6e4 "
                               "steps; config 5: 11,000), 3 x 1500 epochs, the 256 held-out "
                               "256x256 points; cold sequential measured over all 256",
