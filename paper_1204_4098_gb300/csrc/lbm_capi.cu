@@ -224,6 +224,14 @@ struct lbm_ctx {
   int ny_buf = 0;
   int row0 = 0;
   cudaEvent_t packed = nullptr;  // overlapped band step: boundary rows packed
+  // Step graphs of small lattices (queue_steps): one per buffer parity, with
+  // the launch arguments of its first step.
+  struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    StripLaunch L{};
+    int scheme = -1, variant = -1, grid = 0;
+  } graph[2];
+  cudaStream_t cap_stream = nullptr;  // private stream the graphs are captured on
   std::string err;
 };
 
@@ -363,6 +371,94 @@ lbm_status launch_rows(lbm_ctx* c, int scheme, StripLaunch L, int r0, int r1, in
   return LBM_OK;
 }
 
+// Steps per captured step graph (even: a replay leaves the state in the same
+// buffer) and the lattice size up to which steps go through graphs.  One
+// launch per step costs ~6 us of host-side launch overhead on this system,
+// which is most of a step below ~2048^2 cells (a 256^2 step computes in
+// ~2 us); a graph replays its kernels back to back.  Larger lattices launch
+// per step: the GPU time of a step hides the launch there.
+constexpr int kGraphSteps = 16;
+constexpr size_t kGraphMaxCells = size_t(2048) * 2048;
+
+// One step kernel from buffer c->cur on `stream`, flipping c->cur.
+cudaError_t launch_step(lbm_ctx* c, int scheme, StripLaunch& L, int grid, cudaStream_t stream) {
+  const int s = c->cur, d = 1 - c->cur;
+  L.src = c->f[s];
+  L.dst = c->f[d];
+  L.rho_src = c->rho[s];
+  L.rho_dst = c->rho[d];
+  const int variant = pick_variant(c, kStepMode);
+  const cudaError_t e =
+      variant == LBM_VARIANT_STAGED
+          ? strip_tma_launch(c->p.precision, scheme, L, grid, stream)
+          : variant == LBM_VARIANT_PAIR
+                ? strip2_launch(c->p.precision, scheme, kStepMode, L, grid, stream)
+                : strip_launch(c->p.precision, scheme, kStepMode, L, grid, stream);
+  if (e == cudaSuccess) c->cur = d;
+  return e;
+}
+
+// Every argument a step kernel reads, compared field by field.
+bool same_launch(const StripLaunch& x, const StripLaunch& y) {
+  return x.src == y.src && x.dst == y.dst && x.rho_src == y.rho_src && x.rho_dst == y.rho_dst &&
+         x.out_rho == y.out_rho && x.out_vx == y.out_vx && x.out_vy == y.out_vy &&
+         x.status == y.status && x.nx == y.nx && x.ny == y.ny && x.y_begin == y.y_begin &&
+         x.y_end == y.y_end && x.out_row0 == y.out_row0 && x.n_strips == y.n_strips &&
+         x.band_rows == y.band_rows && x.n_bands == y.n_bands && x.plane == y.plane &&
+         x.RT == y.RT && x.a == y.a && x.b4 == y.b4 && x.two_over_G == y.two_over_G &&
+         x.minus_G == y.minus_G && x.tau == y.tau && x.omega == y.omega &&
+         x.sigma_ups == y.sigma_ups && x.guo == y.guo && x.s_e == y.s_e && x.s_eps == y.s_eps &&
+         x.s_q == y.s_q;
+}
+
+// The cached graph of kGraphSteps steps from the current buffer, captured
+// again when any kernel argument, the scheme, the kernel variant or the grid
+// changed; nullptr when capture is unavailable (the caller then launches
+// step by step).
+cudaGraphExec_t step_graph(lbm_ctx* c, int scheme, StripLaunch L, int grid) {
+  lbm_ctx::StepGraph& g = c->graph[c->cur];
+  const int variant = pick_variant(c, kStepMode);
+  L.src = c->f[c->cur];
+  L.dst = c->f[1 - c->cur];
+  L.rho_src = c->rho[c->cur];
+  L.rho_dst = c->rho[1 - c->cur];
+  if (g.exec && g.scheme == scheme && g.variant == variant && g.grid == grid &&
+      same_launch(g.L, L))
+    return g.exec;
+  if (g.exec) {
+    cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+  }
+  if (!c->cap_stream &&
+      cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    c->cap_stream = nullptr;
+    return nullptr;
+  }
+  const int cur0 = c->cur;
+  cudaGraph_t graph = nullptr;
+  bool ok = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) ==
+            cudaSuccess;
+  for (int k = 0; ok && k < kGraphSteps; ++k)
+    ok = launch_step(c, scheme, L, grid, c->cap_stream) == cudaSuccess;
+  c->cur = cur0;  // capturing ran nothing
+  const bool ended = cudaStreamEndCapture(c->cap_stream, &graph) == cudaSuccess;
+  cudaGraphExec_t exec = nullptr;
+  if (ok && ended && graph && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+    exec = nullptr;
+  if (graph) cudaGraphDestroy(graph);
+  if (!exec) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  g.exec = exec;
+  g.L = L;
+  g.scheme = scheme;
+  g.variant = variant;
+  g.grid = grid;
+  return exec;
+}
+
 lbm_status queue_steps(lbm_ctx* c, int n, int scheme, double tau, double sigma) {
   if (!c) return LBM_E_INVAL;
   if (n < 0) return fail(c, LBM_E_INVAL, "n must be >= 0");
@@ -377,21 +473,16 @@ lbm_status queue_steps(lbm_ctx* c, int n, int scheme, double tau, double sigma) 
   int grid = 0;
   lbm_status st = geometry(c, scheme, kStepMode, L, grid);
   if (st != LBM_OK) return st;
-  for (int k = 0; k < n; ++k) {
-    const int s = c->cur, d = 1 - c->cur;
-    L.src = c->f[s];
-    L.dst = c->f[d];
-    L.rho_src = c->rho[s];
-    L.rho_dst = c->rho[d];
-    const int variant = pick_variant(c, kStepMode);
-    cudaError_t e =
-        variant == LBM_VARIANT_STAGED
-            ? strip_tma_launch(c->p.precision, scheme, L, grid, c->stream)
-            : variant == LBM_VARIANT_PAIR
-                  ? strip2_launch(c->p.precision, scheme, kStepMode, L, grid, c->stream)
-                  : strip_launch(c->p.precision, scheme, kStepMode, L, grid, c->stream);
+  int k = 0;
+  if (!c->band && n >= kGraphSteps && size_t(c->p.nx) * c->p.ny <= kGraphMaxCells) {
+    const cudaGraphExec_t g = step_graph(c, scheme, L, grid);
+    if (g)
+      for (; k + kGraphSteps <= n; k += kGraphSteps)
+        LBM_CUDA(c, cudaGraphLaunch(g, c->stream));  // the state returns to c->cur
+  }
+  for (; k < n; ++k) {
+    const cudaError_t e = launch_step(c, scheme, L, grid, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
-    c->cur = d;
   }
   count_launches((unsigned long long)n);
   c->last_scheme = scheme;
@@ -588,6 +679,9 @@ lbm_status lbm_destroy(lbm_ctx* c) {
   cudaFree(c->d_tmp);
   cudaFree(c->d_pop);
   if (c->packed) cudaEventDestroy(c->packed);
+  for (auto& g : c->graph)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->h_status) cudaFreeHost(c->h_status);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;

@@ -289,6 +289,38 @@ def test_band_rows_do_not_change_results(precision):
         assert np.array_equal(f, out[0])
 
 
+@pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP64, lbm.BF16DEV])
+def test_step_graphs_match_single_launches(precision):
+    """Runs of 16 steps or more on a small lattice replay a captured graph of
+    16 steps; the result equals one launch per step, from either buffer
+    parity, with a remainder, and after the scheme, tau, the band height or
+    the kernel variant changed (each change captures a new graph)."""
+    nx, ny, t = 66, 40, 0.85
+    rho, ux, uy = droplet_state(nx, ny, t)
+    runs = [(37, lbm.IMPROVED, 0.8, 0.1, 0, lbm.VARIANT_AUTO),
+            (4, lbm.IMPROVED, 0.8, 0.1, 0, lbm.VARIANT_AUTO),
+            (32, lbm.IMPROVED, 0.8, 0.1, 0, lbm.VARIANT_AUTO),
+            (16, lbm.IMPROVED, 0.9, 0.1, 0, lbm.VARIANT_AUTO),
+            (17, lbm.EDM, 0.9, 0.0, 0, lbm.VARIANT_AUTO),
+            (16, lbm.EDM, 0.9, 0.0, 3, lbm.VARIANT_AUTO),
+            (16, lbm.EDM, 0.9, 0.0, 3, lbm.VARIANT_REGISTER),
+            (48, lbm.IMPROVED, 0.8, 0.1, 0, lbm.VARIANT_AUTO)]
+    graph = lbm.Lattice(nx, ny, t, precision=precision)
+    single = lbm.Lattice(nx, ny, t, precision=precision)
+    for g in (graph, single):
+        g.init_density(rho, ux, uy)
+    for n, scheme, tau, sigma, rows, variant in runs:
+        for g in (graph, single):
+            g.set_band_rows(rows)
+            g.set_variant(variant)
+        graph.step(n, scheme, tau, sigma)
+        for _ in range(n):
+            single.step(1, scheme, tau, sigma)
+        assert np.array_equal(graph.populations(), single.populations()), (n, scheme, tau)
+    graph.close()
+    single.close()
+
+
 def test_checkpoint_roundtrip_is_bitwise():
     nx, ny, t = 64, 40, 0.85
     rho, ux, uy = droplet_state(nx, ny, t)
