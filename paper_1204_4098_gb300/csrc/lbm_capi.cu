@@ -372,11 +372,11 @@ lbm_status launch_rows(lbm_ctx* c, int scheme, StripLaunch L, int r0, int r1, in
 }
 
 // Steps per captured step graph (even: a replay leaves the state in the same
-// buffer) and the lattice size up to which steps go through graphs.  One
-// launch per step costs ~6 us of host-side launch overhead on this system,
-// which is most of a step below ~2048^2 cells (a 256^2 step computes in
-// ~2 us); a graph replays its kernels back to back.  Larger lattices launch
-// per step: the GPU time of a step hides the launch there.
+// buffer) and the lattice size up to which steps go through graphs.  With
+// one launch per step a small lattice (64^2 to 256^2) takes a flat ~6.2 us
+// per step however little it computes; a graph of the same kernels replays
+// them with shorter gaps (~4 us per step there, a few per cent faster up to
+// 2048^2).  From 4096^2 on the step's own time hides the gap.
 constexpr int kGraphSteps = 16;
 constexpr size_t kGraphMaxCells = size_t(2048) * 2048;
 
