@@ -427,10 +427,6 @@ struct StoreBF16 {
   static __device__ __forceinline__ __nv_bfloat162 from_c2(C a, C b) {
     return __floats2bfloat162_rn(a, b);
   }
-  // (r.x - v.x, r.y - v.y), each one rounding: a mixed-precision FMA with the
-  // 16-bit value times -1 (exact) plus the FP32 value, on the 16-bit halves
-  // of the pair's word as they are -- the same values as subtracting the
-  // unpacked pair.
   // wr + d with one rounding (mixed-precision FMA of the 16-bit deviation
   // times 1 plus the FP32 w_a rho): the value a stored deviation stands for.
   static __device__ __forceinline__ float decode(float wr, __nv_bfloat16 d) {
@@ -452,6 +448,10 @@ struct StoreBF16 {
         : "r"(u), "f"(wr.x()), "f"(wr.y()));
     return Pair<float>(x, y);
   }
+  // (r.x - v.x, r.y - v.y), each one rounding: a mixed-precision FMA with the
+  // 16-bit value times -1 (exact) plus the FP32 value, on the 16-bit halves
+  // of the pair's word as they are -- the same values as subtracting the
+  // unpacked pair.
   static __device__ __forceinline__ Pair<float> sub_from(Pair<float> r, __nv_bfloat162 v) {
     unsigned u;
     __builtin_memcpy(&u, &v, sizeof(u));
@@ -471,9 +471,7 @@ struct StoreF16 {
   static __device__ __forceinline__ T from_c(C v) { return __float2half_rn(v); }
   static __device__ __forceinline__ float2 to_c2(__half2 v) { return __half22float2(v); }
   static __device__ __forceinline__ __half2 from_c2(C a, C b) { return __floats2half2_rn(a, b); }
-  // as StoreBF16::sub_from, with -1 in FP16
-  // wr + d with one rounding (mixed-precision FMA of the 16-bit deviation
-  // times 1 plus the FP32 w_a rho): the value a stored deviation stands for.
+  // as StoreBF16::decode, with 1 in FP16
   static __device__ __forceinline__ float decode(float wr, __half d) {
     unsigned short b;
     __builtin_memcpy(&b, &d, sizeof(b));
@@ -493,6 +491,7 @@ struct StoreF16 {
         : "r"(u), "f"(wr.x()), "f"(wr.y()));
     return Pair<float>(x, y);
   }
+  // as StoreBF16::sub_from, with -1 in FP16
   static __device__ __forceinline__ Pair<float> sub_from(Pair<float> r, __half2 v) {
     unsigned u;
     __builtin_memcpy(&u, &v, sizeof(u));
