@@ -321,6 +321,40 @@ def test_step_graphs_match_single_launches(precision):
     single.close()
 
 
+@pytest.mark.parametrize("precision,rtol,vtol", [(lbm.FP64, 1e-11, 1e-12),
+                                                 (lbm.FP32, 2e-6, 2e-5)])
+def test_moments_of_a_large_lattice_in_row_chunks(precision, rtol, vtol):
+    """From 2048^2 cells on, lbm_get_moments computes and copies the rows in
+    chunks (each chunk copied while the next is computed).  Every row, the
+    chunk boundaries included, equals the oracle's observation (Table I:
+    v = u + F / (2 rho)) of the same populations; pinned and pageable
+    outputs agree bitwise."""
+    torch = pytest.importorskip("torch")
+    nx, ny, t = 2048, 2050, 0.85  # ny not a multiple of the chunk count
+    rg, rl = maxwell(t)
+    rho = inputs.droplet(nx, ny, rg, rl, 300.0, W=4.0)
+    gpu = lbm.Lattice(nx, ny, t, precision=precision)
+    gpu.init_density(rho)
+    gpu.step(3, lbm.IMPROVED, 0.8, 0.1)
+    ref = oracle.Lattice(nx, ny, t)
+    ref.f = gpu.populations()
+    ref.last_scheme = oracle.IMPROVED
+    want = ref.observe()
+    pin = [torch.empty((ny, nx), dtype=torch.float64, pin_memory=True).numpy() for _ in range(3)]
+    got = gpu.observe(out=tuple(pin))
+    pageable = gpu.observe()
+    for a, b in zip(got, pageable):
+        assert np.array_equal(a, b)
+    assert np.max(np.abs(got[0] - want[0]) / want[0]) < rtol
+    for k in (1, 2):
+        assert np.max(np.abs(got[k] - want[k])) < vtol, k
+    # the outputs are written independently: rho alone equals rho of all three
+    rho_only = np.empty((ny, nx))
+    assert lbm.lib().lbm_get_moments(gpu.ctx, lbm._dptr(rho_only), None, None) == lbm.LBM_OK
+    assert np.array_equal(rho_only, got[0])
+    gpu.close()
+
+
 def test_checkpoint_roundtrip_is_bitwise():
     nx, ny, t = 64, 40, 0.85
     rho, ux, uy = droplet_state(nx, ny, t)
