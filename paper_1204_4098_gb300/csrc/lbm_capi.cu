@@ -480,7 +480,16 @@ lbm_status queue_steps(lbm_ctx* c, int n, int scheme, double tau, double sigma) 
   lbm_status st = geometry(c, scheme, kStepMode, L, grid);
   if (st != LBM_OK) return st;
   int k = 0;
-  if (!c->band && n >= kGraphSteps && size_t(c->p.nx) * c->p.ny <= kGraphMaxCells) {
+  // (not while the caller captures the context stream into a graph of its
+  // own: the steps are then recorded one launch at a time)
+  cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+  if (!c->band && n >= kGraphSteps && size_t(c->p.nx) * c->p.ny <= kGraphMaxCells &&
+      cudaStreamIsCapturing(c->stream, &capturing) != cudaSuccess) {
+    cudaGetLastError();  // treated as capturing: plain launches
+    capturing = cudaStreamCaptureStatusActive;
+  }
+  if (!c->band && n >= kGraphSteps && size_t(c->p.nx) * c->p.ny <= kGraphMaxCells &&
+      capturing == cudaStreamCaptureStatusNone) {
     const cudaGraphExec_t g = step_graph(c, scheme, L, grid);
     if (g)
       for (; k + kGraphSteps <= n; k += kGraphSteps)

@@ -321,6 +321,48 @@ def test_step_graphs_match_single_launches(precision):
     single.close()
 
 
+def test_step_graphs_of_the_staged_kernel_match_single_launches():
+    """The same for the bulk-copy staged kernel (its tensor maps are kernel
+    arguments captured with the graph)."""
+    nx, ny, t = 64, 40, 0.85
+    rho, ux, uy = droplet_state(nx, ny, t)
+    out = []
+    for chunk in (40, 1):
+        g = lbm.Lattice(nx, ny, t, precision=lbm.FP32)
+        g.set_variant(lbm.VARIANT_STAGED)
+        g.init_density(rho, ux, uy)
+        for _ in range(40 // chunk):
+            g.step(chunk, lbm.IMPROVED, 0.8, 0.1)
+        out.append(g.populations())
+        g.close()
+    assert np.array_equal(out[0], out[1])
+
+
+def test_steps_captured_into_a_caller_graph_replay_exactly():
+    """lbm_step_async on a stream the caller is capturing records one launch
+    per step into the caller's graph (no graph of its own); two replays of 32
+    captured steps equal 64 steps run directly."""
+    torch = pytest.importorskip("torch")
+    nx, ny, t = 66, 40, 0.85
+    rho, ux, uy = droplet_state(nx, ny, t)
+    s = torch.cuda.Stream()
+    a = lbm.Lattice(nx, ny, t, stream=s.cuda_stream)
+    b = lbm.Lattice(nx, ny, t)
+    a.init_density(rho, ux, uy)
+    b.init_density(rho, ux, uy)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+        a.step_async(32, lbm.IMPROVED, 0.8, 0.1)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    b.step(64, lbm.IMPROVED, 0.8, 0.1)
+    assert np.array_equal(a.populations(), b.populations())
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("precision,rtol,vtol", [(lbm.FP64, 1e-11, 1e-12),
                                                  (lbm.FP32, 2e-6, 2e-5)])
 def test_moments_of_a_large_lattice_in_row_chunks(precision, rtol, vtol):
