@@ -182,8 +182,10 @@ lbm_status lbm_init_density_at_rest(lbm_ctx *ctx, const double *rho);
  * on the context stream, one per step; on lattices of at most 2048^2 cells
  * runs of 16 steps go through a CUDA graph of 16 step kernels, captured on
  * first use for the current buffer and launch arguments and kept until the
- * context is destroyed (bit-identical to single launches).  The call then
- * waits for the kernels and reads the device status word once.  LBM_E_DIVERGED if psi became undefined in any step
+ * context is destroyed (bit-identical to single launches); while the caller
+ * captures the context stream into a graph of its own, lbm_step_async records
+ * one launch per step instead.  The call then waits for the kernels and
+ * reads the device status word once (so lbm_step itself cannot be captured).  LBM_E_DIVERGED if psi became undefined in any step
  * (the state is then unspecified but the context stays usable and
  * destroyable); LBM_E_STATE before lbm_init_density / lbm_set_populations. */
 lbm_status lbm_step(lbm_ctx *ctx, int n, int scheme, double tau, double sigma);
