@@ -398,7 +398,7 @@ def run_ours(args, world, rank, local):
     # ---- end to end through the C ABI with pinned host buffers ----
     e2e = None
     if not args.no_e2e:
-        pin = lambda: torch.empty((n, n), dtype=torch.float64, pin_memory=True).numpy()
+        pin = lambda: lbm.host_array((n, n))  # page-locked, huge pages where available
         h_rho0 = pin()
         h_rho0[...] = rho0
         outs = (pin(), pin(), pin())
@@ -426,8 +426,8 @@ def run_ours(args, world, rank, local):
                "h2d_bytes_per_step": 8 * cells / args.steps,
                "d2h_bytes_per_step": 24 * cells / args.steps,
                "note": "lbm_init_density (8 B/cell H2D) + K x lbm_step + lbm_get_moments "
-                       "(24 B/cell D2H), pinned host memory, wall clock; median of three "
-                       "timed passes"}
+                       "(24 B/cell D2H), host arrays from lbm_host_alloc (page-locked), "
+                       "wall clock; median of three timed passes"}
     lat.close()
 
     variants = {}

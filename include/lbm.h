@@ -540,6 +540,29 @@ lbm_status lbm_selftest_grid_barrier_timeout(int device, int *result);
 lbm_status lbm_mass_f32_noalloc(const float *d_values, size_t n, double *d_out,
                                 void *cuda_stream);
 
+/* ---- page-locked host buffers ------------------------------------------ */
+
+/* Host memory for the arrays passed to lbm_init_density, lbm_get_moments,
+ * lbm_get/set_populations and their batch counterparts, which DMA copies
+ * move at the rate of the CPU-GPU link.  *out receives at least `bytes` of
+ * zeroed, page-locked memory: an anonymous mapping registered with the CUDA
+ * driver (cudaHostRegister); from one transparent huge page up (2 MiB with
+ * 4 KiB base pages, 512 MiB with 64 KiB ones) it is aligned to and rounded
+ * up to whole huge pages and advised for them (MADV_HUGEPAGE, used where the
+ * kernel provides them).  Buffers from
+ * cudaHostAlloc work as well; on a virtualised host whose memory had been
+ * used and released by an earlier job, 537 MB copies into them were measured
+ * 5-8x slower than the link rate, while copies into these buffers stayed at
+ * it.  The paper has no counterpart: a deployment helper.  Errors:
+ * LBM_E_INVAL for a NULL out or bytes = 0, LBM_E_NOMEM when the mapping
+ * fails, LBM_E_CUDA when the registration fails (nothing is then held).
+ * Thread-safe. */
+lbm_status lbm_host_alloc(size_t bytes, void **out);
+
+/* Unregister and unmap a buffer from lbm_host_alloc.  NULL is accepted;
+ * LBM_E_INVAL for any other pointer that lbm_host_alloc did not return. */
+lbm_status lbm_host_free(void *p);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,7 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
 SOURCES = [
     "lbm_step_f32.cu", "lbm_step_f64.cu", "lbm_step_bf16.cu", "lbm_step_f16.cu",
     "lbm_capi.cu", "lbm_eos_host.cpp", "lbm_noalloc.cu", "lbm_batch.cu", "lbm_mlp.cu",
-    "lbm_selftest.cu",
+    "lbm_selftest.cu", "lbm_host_mem.cpp",
 ]
 
 

@@ -12,6 +12,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -112,6 +113,8 @@ SIGNATURES = {
     "lbm_selftest_wait_timeout": (_I, [_I, ctypes.c_longlong, _IP]),
     "lbm_selftest_grid_barrier_timeout": (_I, [_I, _IP]),
     "lbm_mass_f32_noalloc": (_I, [_P, ctypes.c_size_t, _P, _P]),
+    "lbm_host_alloc": (_I, [ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)]),
+    "lbm_host_free": (_I, [_P]),
     "lbm_batch_default_params": (None, [ctypes.POINTER(lbm_batch_params)]),
     "lbm_batch_create": (_I, [ctypes.POINTER(lbm_batch_params), ctypes.POINTER(lbm_instance),
                               _I, ctypes.POINTER(_P)]),
@@ -174,6 +177,24 @@ def _dptr(a):
         assert a.dtype == np.float64 and a.flags.c_contiguous
         return a.ctypes.data_as(ctypes.c_void_p)
     return ctypes.c_void_p(int(a))  # a raw pointer (e.g. pinned torch memory)
+
+
+def host_array(shape, dtype=np.float64):
+    """Zeroed numpy array in page-locked host memory from lbm_host_alloc (huge
+    pages where the kernel provides them), for the host arrays the C ABI
+    copies; the memory goes back through lbm_host_free when the array (and
+    every view of it) is collected."""
+    dtype = np.dtype(dtype)
+    count = int(np.prod(shape))
+    nbytes = max(count * dtype.itemsize, 1)
+    p = ctypes.c_void_p()
+    st = lib().lbm_host_alloc(nbytes, ctypes.byref(p))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_host_alloc failed")
+    buf = (ctypes.c_char * nbytes).from_address(p.value)
+    arr = np.frombuffer(buf, dtype=dtype, count=count).reshape(shape)
+    weakref.finalize(buf, lib().lbm_host_free, ctypes.c_void_p(p.value))
+    return arr
 
 
 def critical_point(a=1.0, b=4.0, R=1.0):

@@ -3,6 +3,8 @@ inputs.  Tolerances: FP64 storage agrees to rounding (1e-13 per step, 1e-11
 after 1e4 steps); FP32 to 1e-4 relative density after 1e4 steps (and 2e-6 of
 the population scale per step); 16-bit deviation storage is reported and
 gated loosely."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -646,6 +648,46 @@ def test_uniform_density_stays_uniform_at_rest(precision):
             assert not np.any(vx) and not np.any(vy), (nx, scheme)
             assert np.max(np.abs(r / 0.2 - 1)) < tol, (nx, scheme)
             g.close()
+
+
+def test_host_alloc_buffers_carry_the_same_values():
+    """lbm_host_alloc / lbm_host_free: zeroed page-locked buffers (aligned to
+    a huge page from one huge page up) that init and moments read and write
+    with the same values as pageable arrays; the argument errors."""
+    L = lbm.lib()
+    p = ctypes.c_void_p()
+    assert L.lbm_host_alloc(0, ctypes.byref(p)) == lbm.LBM_E_INVAL
+    assert L.lbm_host_alloc(16, None) == lbm.LBM_E_INVAL
+    assert L.lbm_host_free(None) == lbm.LBM_OK
+    assert L.lbm_host_alloc(40, ctypes.byref(p)) == lbm.LBM_OK
+    assert L.lbm_host_free(ctypes.c_void_p(p.value + 8)) == lbm.LBM_E_INVAL
+    assert L.lbm_host_free(p) == lbm.LBM_OK
+    assert L.lbm_host_free(p) == lbm.LBM_E_INVAL  # already freed
+    hp = 2 << 20
+    try:
+        hp = int(open("/sys/kernel/mm/transparent_hugepage/hpage_pmd_size").read())
+    except OSError:
+        pass
+    big = lbm.host_array((hp // 8 + 3,))
+    assert big.ctypes.data % hp == 0 and not big[::4096].any() and big[-1] == 0.0
+    del big
+    nx, ny, t = 70, 50, 0.85
+    rho, ux, uy = droplet_state(nx, ny, t)
+    h = [lbm.host_array((ny, nx)) for _ in range(6)]
+    h[0][...] = rho
+    h[1][...] = ux
+    h[2][...] = uy
+    a = lbm.Lattice(nx, ny, t)
+    b = lbm.Lattice(nx, ny, t)
+    a.init_density(h[0], h[1], h[2])
+    b.init_density(rho, ux, uy)
+    a.step(20, lbm.IMPROVED, 0.8, 0.1)
+    b.step(20, lbm.IMPROVED, 0.8, 0.1)
+    got = a.observe(out=tuple(h[3:]))
+    for x, y in zip(got, b.observe()):
+        assert np.array_equal(x, y)
+    a.close()
+    b.close()
 
 
 def test_pinned_host_arrays_are_used_in_place():
