@@ -441,6 +441,7 @@ cudaGraphExec_t step_graph(lbm_ctx* c, int scheme, StripLaunch L, int grid) {
     c->cap_stream = nullptr;
     return nullptr;
   }
+  const StripLaunch first = L;  // the key: launch_step overwrites the buffers
   const int cur0 = c->cur;
   cudaGraph_t graph = nullptr;
   bool ok = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) ==
@@ -458,7 +459,7 @@ cudaGraphExec_t step_graph(lbm_ctx* c, int scheme, StripLaunch L, int grid) {
     return nullptr;
   }
   g.exec = exec;
-  g.L = L;
+  g.L = first;
   g.scheme = scheme;
   g.variant = variant;
   g.grid = grid;
