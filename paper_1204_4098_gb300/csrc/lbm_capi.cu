@@ -800,6 +800,7 @@ lbm_status lbm_get_moments(lbm_ctx* c, double* rho, double* vx, double* vy) {
   const bool pair = pick_variant(c, mode) == LBM_VARIANT_PAIR;
   for (int k = 0; k < chunks; ++k) {
     const int r0 = int(size_t(ny) * k / chunks), r1 = int(size_t(ny) * (k + 1) / chunks);
+    if (r1 == r0) continue;  // fewer rows than chunks
     L.y_begin = c->row0 + r0;
     L.y_end = c->row0 + r1;
     int grid = 0;
