@@ -4,6 +4,7 @@ after 1e4 steps); FP32 to 1e-4 relative density after 1e4 steps (and 2e-6 of
 the population scale per step); 16-bit deviation storage is reported and
 gated loosely."""
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -691,7 +692,15 @@ def test_host_alloc_buffers_carry_the_same_values():
         pass
     big = lbm.host_array((hp // 8 + 3,))
     assert big.ctypes.data % hp == 0 and not big[::4096].any() and big[-1] == 0.0
+    addr = big.ctypes.data
+    view = big[1:]
     del big
+    gc.collect()
+    assert view[-1] == 0.0  # a view keeps the buffer
+    del view
+    gc.collect()
+    # collected: the binding returned it through lbm_host_free already
+    assert L.lbm_host_free(ctypes.c_void_p(addr)) == lbm.LBM_E_INVAL
     nx, ny, t = 70, 50, 0.85
     rho, ux, uy = droplet_state(nx, ny, t)
     h = [lbm.host_array((ny, nx)) for _ in range(6)]
