@@ -17,7 +17,8 @@ are far larger than L2, so no flush is needed between steps.
                 memory: lbm_init_density (H2D), K steps, lbm_get_moments (D2H).
 * cpu_baseline -- the FP64 oracle (test infrastructure) on a bounded sample
                 of the same workload, on this host's cores.
-* storage_variants, batched_sweep (128 slabs, with the sequential plain runs
+* storage_variants, schemes_fp32 (every forcing scheme and the MRT form on
+  the same workload), batched_sweep (128 slabs, with the sequential plain runs
   measured over all of them), batched_sweep_config4_512 (the 512-slab sweep,
   batched), warm_start (a reduced config 5) -- the other workloads' legs.
 
@@ -452,6 +453,40 @@ def run_ours(args, world, rank, local):
                               "frac": gbs / peak, "bytes_per_cell": BYTES_PER_CELL[name]}
             v.close()
 
+    # every forcing scheme of Table I and the MRT form, FP32, on a liquid slab
+    # at the Maxwell densities of T = 0.9 Tc (Ladd's forcing diverges from
+    # the 0.85 Tc spinodal start and from 0.85 Tc slabs); the headline is the
+    # improved scheme
+    schemes = {}
+    if args.variants and rank == 0 and world == 1 and args.precision == "fp32":
+        from paper_1204_4098_gb300 import inputs
+        rg, rl, _ = lbm.maxwell(lbm.temperature(0.9))
+        slab = inputs.slab_step(n, n, rg, rl)
+        for name, sch, sigma in (("SC", lbm.SC, 0.0), ("EDM", lbm.EDM, 0.0),
+                                 ("improved", lbm.IMPROVED, 0.1), ("noforce", lbm.NOFORCE, 0.0),
+                                 ("EDM_Ce_1_over_tau", lbm.EDM_MOD, 0.0), ("Ladd", lbm.LADD, 0.0),
+                                 ("MRT_improved", lbm.MRT, 0.1)):
+            v = lbm.Lattice(n, n, 0.9, precision=lbm.FP32, device=local,
+                            stream=stream.cuda_stream)
+            if sch == lbm.MRT:
+                v.set_mrt_rates(0.8, 1.1, 1.3)
+            v.init_density(slab)
+            v.step_async(args.warmup, sch, 0.8, sigma)
+            torch.cuda.synchronize()
+            k = max(args.steps // 2, 1)
+            s2, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s2.record(stream)
+            v.step_async(k, sch, 0.8, sigma)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            st = v.sync()
+            t_ms = s2.elapsed_time(e2)
+            gbs = BYTES_PER_CELL["fp32"] * cells / (t_ms * 1e-3 / k) / 1e9
+            schemes[name] = {"MLUPS": round(cells * k / (t_ms * 1e-3) / 1e6, 1),
+                             "frac": round(gbs / peak, 4),
+                             "status": lbm.STATUS_NAMES.get(st, st)}
+            v.close()
+
     sweep_line = sweep512 = None
     if rank == 0 and world == 1 and not args.no_sweep:
         sweep_line = sweep_measure(128, 128, seed=4, device=local)
@@ -479,6 +514,9 @@ def run_ours(args, world, rank, local):
                 "gpu_launches": launches}
         if variants:
             line["storage_variants"] = variants
+        if schemes:
+            line["schemes_fp32"] = {"workload": f"{n}x{n} slab at the Maxwell densities, "
+                                                "T = 0.9 Tc, tau = 0.8", **schemes}
         if sweep_line:
             line["batched_sweep"] = sweep_line
         if sweep512:
