@@ -137,3 +137,21 @@ def test_every_entry_point_is_documented():
         if m and not any("*/" in prev for prev in lines[max(0, i - 3):i]):
             undocumented.append(m.group(1))
     assert not undocumented, undocumented
+
+
+def test_host_alloc_argument_checks_without_a_gpu(L):
+    p = ctypes.c_void_p()
+    assert L.lbm_host_alloc(0, ctypes.byref(p)) == lbm.LBM_E_INVAL
+    assert L.lbm_host_alloc(64, None) == lbm.LBM_E_INVAL
+    assert L.lbm_host_alloc(1 << 63, ctypes.byref(p)) == lbm.LBM_E_INVAL
+    assert L.lbm_host_free(None) == lbm.LBM_OK
+    scratch = ctypes.create_string_buffer(64)
+    assert L.lbm_host_free(ctypes.cast(scratch, ctypes.c_void_p)) == lbm.LBM_E_INVAL
+    # registration needs the CUDA driver: without a GPU the mapping is
+    # returned and the status says so; with one, the buffer is usable
+    st = L.lbm_host_alloc(4096, ctypes.byref(p))
+    assert st in (lbm.LBM_OK, lbm.LBM_E_CUDA)
+    if st == lbm.LBM_OK:
+        assert L.lbm_host_free(p) == lbm.LBM_OK
+    else:
+        assert not p.value
