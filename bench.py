@@ -13,8 +13,9 @@ are far larger than L2, so no flush is needed between steps.
 * roofline   -- the step kernel: algorithmic bytes per launch (9 reads + 9
                 writes per cell) / average launch time, against the measured
                 HBM copy bandwidth.
-* e2e        -- the same metric through the public C ABI from pinned host
-                memory: lbm_init_density (H2D), K steps, lbm_get_moments (D2H).
+* e2e        -- the same metric through the public C ABI from page-locked
+                host buffers (lbm_host_alloc): lbm_init_density (H2D), K
+                steps, lbm_get_moments (D2H); median of three passes.
 * cpu_baseline -- the FP64 oracle (test infrastructure) on a bounded sample
                 of the same workload, on this host's cores.
 * storage_variants, schemes_fp32 (every forcing scheme and the MRT form on
@@ -396,7 +397,7 @@ def run_ours(args, world, rank, local):
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s"}
 
-    # ---- end to end through the C ABI with pinned host buffers ----
+    # ---- end to end through the C ABI with page-locked host buffers ----
     e2e = None
     if not args.no_e2e:
         pin = lambda: lbm.host_array((n, n))  # page-locked, huge pages where available

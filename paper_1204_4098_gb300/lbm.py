@@ -345,7 +345,7 @@ class Lattice:
 
     def observe(self, out=None):
         """(rho, vx, vy) as FP64 arrays; `out` may supply the three arrays
-        (e.g. views of pinned host memory for fast copies)."""
+        (host_array buffers keep the copies at the link rate)."""
         if out is None:
             out = tuple(np.empty((self.ny, self.nx)) for _ in range(3))
         rho, vx, vy = out
