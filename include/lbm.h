@@ -185,9 +185,10 @@ lbm_status lbm_init_density_at_rest(lbm_ctx *ctx, const double *rho);
  * context is destroyed (bit-identical to single launches); while the caller
  * captures the context stream into a graph of its own, lbm_step_async records
  * one launch per step instead.  The call then waits for the kernels and
- * reads the device status word once (so lbm_step itself cannot be captured).  LBM_E_DIVERGED if psi became undefined in any step
- * (the state is then unspecified but the context stays usable and
- * destroyable); LBM_E_STATE before lbm_init_density / lbm_set_populations. */
+ * reads the device status word once (so lbm_step itself cannot be
+ * captured).  LBM_E_DIVERGED if psi became undefined in any step (the state
+ * is then unspecified but the context stays usable and destroyable);
+ * LBM_E_STATE before lbm_init_density / lbm_set_populations. */
 lbm_status lbm_step(lbm_ctx *ctx, int n, int scheme, double tau, double sigma);
 
 /* Queue n steps without waiting and without reading the status (for timing
@@ -199,7 +200,11 @@ lbm_status lbm_sync_status(lbm_ctx *ctx);
 /* Density and the actual fluid velocity v = u + F / (2 rho) (Table I, every
  * scheme) of the current state, as host FP64 arrays of ny*nx; any pointer
  * may be NULL.  F = 0 (and psi is not evaluated) when the most recent
- * lbm_step used LBM_SCHEME_NOFORCE.  LBM_E_DIVERGED if psi is undefined. */
+ * lbm_step used LBM_SCHEME_NOFORCE.  LBM_E_DIVERGED if psi is undefined.
+ * The values go through device staging and DMA copies; from 2048^2 cells
+ * on, rows are computed and copied in four chunks, each copied while the
+ * next is computed (page-locked outputs, e.g. from lbm_host_alloc, let the
+ * copies run asynchronously at the link rate). */
 lbm_status lbm_get_moments(lbm_ctx *ctx, double *rho, double *vx, double *vy);
 
 /* Total mass sum_x rho(x), reduced on the device in FP64. */
