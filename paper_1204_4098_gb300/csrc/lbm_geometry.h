@@ -10,8 +10,21 @@
 namespace lbm {
 
 // Shortest band of the automatic geometry: each band reloads the two rows
-// around it, so bands stay at least this tall even below one full wave.
+// around it, so on lattices above 256^2 cells bands stay at least this tall
+// even below one full wave.
 constexpr int kMinBandRows = 4;
+
+// Shortest automatic band of an nx x ny lattice.  A small lattice's step is
+// one short wave (replayed from a graph in runs of steps), whose length is
+// the rows each warp walks through, so there the shortest bands win
+// (measured, improved scheme, one column per lane: 64^2 and 128^2 2.69 us
+// per step with 1-row bands against 4.1-4.2 with 4-row ones; 256^2 3.83 us
+// with 2-row bands against 4.36 with 1 or 4; from 512^2 on the 4-row rule
+// is as fast or faster).
+inline int min_band_rows(int nx, int ny) {
+  const long long cells = (long long)nx * ny;
+  return cells <= 128LL * 128 ? 1 : (cells <= 256LL * 256 ? 2 : kMinBandRows);
+}
 
 // Variant for an nx x ny lattice of `precision` on a GPU of `sm_count` SMs,
 // given the requested one; `step` is false for the observe (moments)
@@ -49,7 +62,7 @@ struct StripGeometry {
 
 // Strips of 32 columns (64 for PAIR) and as many row bands as fill the
 // `resident_warps` warp slots once (one wave: every warp of a band runs at the
-// same time as its neighbours), at least kMinBandRows rows each; a positive
+// same time as its neighbours), at least min_band_rows rows each; a positive
 // band_rows_override fixes the band height instead.
 inline StripGeometry strip_geometry(int nx, int ny, int variant, long long resident_warps,
                                     int warps_per_cta, int band_rows_override) {
@@ -60,7 +73,7 @@ inline StripGeometry strip_geometry(int nx, int ny, int variant, long long resid
     g.band_rows = std::min(band_rows_override, ny);
   } else {
     long long n_bands = std::max<long long>(1, resident_warps / g.n_strips);
-    n_bands = std::min<long long>(n_bands, std::max(1, ny / kMinBandRows));
+    n_bands = std::min<long long>(n_bands, std::max(1, ny / min_band_rows(nx, ny)));
     g.band_rows = int((ny + n_bands - 1) / n_bands);
   }
   g.n_bands = (ny + g.band_rows - 1) / g.band_rows;

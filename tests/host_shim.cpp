@@ -125,6 +125,6 @@ void shim_strip_geometry(int nx, int ny, int variant, long long resident_warps,
   out[3] = g.grid;
 }
 
-int shim_min_band_rows() { return lbm::kMinBandRows; }
+int shim_min_band_rows(int nx, int ny) { return lbm::min_band_rows(nx, ny); }
 
 }  // extern "C"

@@ -73,7 +73,6 @@ def test_bench_geometry_is_one_wave(host_shim):
 @pytest.mark.parametrize("seed", range(5))
 def test_geometry_covers_the_lattice_in_one_wave(host_shim, seed):
     rng = np.random.default_rng(seed)
-    kmin = host_shim.shim_min_band_rows()
     for _ in range(200):
         nx, ny = (int(v) for v in rng.integers(1, 5000, 2))
         var = PAIR if rng.random() < 0.5 else REG
@@ -83,12 +82,24 @@ def test_geometry_covers_the_lattice_in_one_wave(host_shim, seed):
         assert g["n_strips"] == (nx + w - 1) // w
         # the bands tile the rows exactly once
         assert g["n_bands"] * g["band_rows"] >= ny > (g["n_bands"] - 1) * g["band_rows"]
-        assert g["band_rows"] >= min(kmin, ny)
+        assert g["band_rows"] >= min(host_shim.shim_min_band_rows(nx, ny), ny)
         # one wave, unless the strips alone exceed it
         items = g["n_strips"] * g["n_bands"]
         assert items <= max(resident, g["n_strips"])
         # one warp per item
         assert (g["grid"] - 1) * 4 < items <= g["grid"] * 4
+
+
+def test_small_lattices_take_the_shortest_bands(host_shim):
+    # the step of a small lattice is one short wave: 1-row bands up to 128^2
+    # cells, 2-row bands up to 256^2, then at least 4 rows
+    assert [host_shim.shim_min_band_rows(n, n) for n in (64, 128, 129, 256, 257, 512)] == \
+        [1, 1, 2, 2, 4, 4]
+    for n, rows in ((64, 1), (128, 1), (256, 2), (512, 4)):
+        g = geometry(host_shim, n, n, REG, SMS * 6 * 4)
+        assert g["band_rows"] == rows and g["n_bands"] == n // rows, n
+    g = geometry(host_shim, 4096, 4096, PAIR, SMS * 4 * 4)  # one wave, taller bands
+    assert g["band_rows"] > 4
 
 
 def test_band_height_override(host_shim):
